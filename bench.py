@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark: SU(3) Landau gauge fixing by steepest descent with Fourier
+acceleration on GB300, in site-iterations per second.
+
+Workload (default): one 32^4 configuration (links of scale 0.5 behind a random
+gauge of scale 1.0, seed 0), FP32 links (18 reals, structure of arrays) with
+FP64 F/theta sums, alpha = 0.08.  A step is one full iteration of the method
+(gradient, F/theta reduction, forward 4D FFT, p2_max/p2 scaling, inverse FFT,
+gauge step g, link update, gauge accumulation); ``value`` = lattice sites x
+timed steps / device time.  Then the same configuration is fixed to
+theta < 1e-15 (FP32 phase + FP64 tail): ``time_to_theta``.  ``e2e`` repeats the
+fix through the public API from pinned host links, with the host<->device
+copies inside the timed region.
+
+--impl reference times the CPU oracle (numpy FP64, naive DFT) instead.
+One JSON line on stdout (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "site-iterations/s"
+WORKLOADS = {
+    "32^4-f32": dict(dims=(32, 32, 32, 32), dtype="f32", link_scale=0.5, gauge_scale=1.0, seed=0, alpha=0.08,
+                     tol=1e-15, max_iter=5000,
+                     desc="32^4 single config, FP32 links (18 reals, SoA), FP64 F/theta sums, FP64 tail to "
+                          "theta<1e-15, link scale 0.5, gauge scale 1.0, alpha 0.08"),
+    "48^3x8-f32r12": dict(dims=(48, 48, 48, 8), dtype="f32_r12", link_scale=0.6, gauge_scale=1.0, seed=0,
+                          alpha=0.08, tol=1e-15, max_iter=5000,
+                          desc="48^3x8 single config, FP32 12-real links, FP64 tail to theta<1e-15, "
+                               "link scale 0.6"),
+    "8^4-f64": dict(dims=(8, 8, 8, 8), dtype="f64", link_scale=0.3, gauge_scale=1.0, seed=0, alpha=0.08,
+                    tol=1e-12, max_iter=2000,
+                    desc="8^4 single config, plain FP64, theta<1e-12, link scale 0.3"),
+}
+DEFAULT_WORKLOAD = "32^4-f32"
+KERNEL_SOURCES = {"update": "k_links.cu", "gradient": "k_links.cu", "build_g": "k_links.cu",
+                  "accumulate": "k_links.cu", "fft_xy": "k_fft.cu", "fft_zt": "k_fft.cu"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per site of each kernel (unique HBM bytes a launch must
+# move: neighbour links and neighbour g count once, via the caches)
+# ---------------------------------------------------------------------------
+def bytes_per_site(kernel: str, prec: int, r: int) -> float:
+    table = {
+        "gradient": 4 * r + 8,   # own links in, packed gradient out
+        "fft_xy": 16,            # 4 complex in, 4 complex out
+        "fft_zt": 16,
+        "build_g": 8 + r,        # packed gradient in, g out
+        "update": 9 * r,         # links in and out, g in
+        "accumulate": 3 * r,     # g in, G in and out
+        "reduce": 0,
+    }
+    return table.get(kernel, 0) * prec
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.path = tempfile.mktemp(prefix="lgf_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", gpu_id], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception as e:  # nvidia-smi missing
+            log("clock sampling unavailable:", e)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, t0: float, t1: float):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    ts = _dt.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(p[1]), float(p[2]), p[5:9]))
+                except ValueError:
+                    continue
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15]
+        note = None
+        if not inside:
+            inside = rows
+            note = "timed region shorter than the 100 ms sampling period: samples from the whole run"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        out = {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+               "reasons": reasons, "samples": len(inside)}
+        if note:
+            out["note"] = note
+        return out
+
+
+def gpu_id_for_smi(torch) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis or "0"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+_ORACLE_CHILD = r"""
+import os, sys, time, json
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from oracle import lgf_oracle as O
+U = np.load(sys.argv[2])
+n = int(sys.argv[3]); alpha = float(sys.argv[4])
+t = time.perf_counter()
+O.iterate(U, n, alpha)
+print(json.dumps({"seconds": time.perf_counter() - t, "iterations": n}))
+"""
+
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+              "NUMEXPR_NUM_THREADS": "1"}
+
+
+def time_oracle(U, n: int, alpha: float) -> float:
+    """Seconds for n oracle iterations on U, in a 1-thread child process."""
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "U.npy")
+        np.save(path, U)
+        env = dict(os.environ, **ONE_THREAD)
+        r = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path, str(n), str(alpha)],
+                           capture_output=True, text=True, env=env, timeout=1800)
+        if r.returncode != 0:
+            raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
+        return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+
+
+# ---------------------------------------------------------------------------
+def profile_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))[workload][kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1208_1186_gb300", "csrc", KERNEL_SOURCES.get(kernel, ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec.get("dram_bytes_per_launch") if rec.get("source_sha256_16") == h else None
+
+
+def run_ours(args, W):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import lgf_inputs
+    import paper_1208_1186_gb300 as lgf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    dims = W["dims"]
+    V = int(np.prod(dims))
+    seed = W["seed"] + rank  # independent configurations per rank (replicas)
+    t = time.time()
+    U = lgf_inputs.synthetic_config(dims, seed=seed, link_scale=W["link_scale"], gauge_scale=W["gauge_scale"])
+    log(f"[rank {rank}] generated {dims} config in {time.time() - t:.1f}s")
+    Ud = torch.from_numpy(U).to("cuda")
+    stream = torch.cuda.Stream()
+    gf = lgf.GaugeFixer(dims, W["dtype"], stream=stream, alpha=W["alpha"])
+    gf.load_links(Ud)
+    smi = ClockSampler(gpu_id_for_smi(torch)) if rank == 0 else None
+    try:
+        gf.iterate(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        launches0 = gf.launch_count()
+        gf.profile(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        ev0.record(stream)
+        gf.iterate(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        prof = gf.profile_read()
+        gf.profile(False)
+        launches = gf.launch_count() - launches0
+        ms_max = max_over_ranks(ms)
+
+        # time to theta < tol from device-resident links
+        gf.load_links(Ud)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iters, conv = gf.fix(W["tol"], W["max_iter"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fix_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        split = gf.fix_split()
+        F, theta = gf.functional()
+
+        # end to end through the public API from pinned host memory
+        pinned = torch.empty(U.shape + (2,), dtype=torch.float64, pin_memory=True)
+        hostU = pinned.numpy().view(np.complex128).reshape(U.shape)
+        hostU[...] = U
+        hostOut = torch.empty_like(pinned).numpy().view(np.complex128).reshape(U.shape)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        gf.load_links(hostU)
+        iters_e2e, _ = gf.fix(W["tol"], W["max_iter"])
+        gf.store_links(hostOut)
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+    finally:
+        if smi:
+            smi.stop()
+    clocks = smi.summary(w0, w1) if smi else None
+    gf.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    prec = 4 if W["dtype"].startswith("f32") else 8
+    r = 12 if W["dtype"].endswith("r12") else 18
+    pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    kernels = {}
+    for name, (kms, n) in prof.items():
+        if n == 0 or name in ("other",):
+            continue
+        per_launch_ms = kms / n
+        b = bytes_per_site(name, prec, r) * V
+        kernels[name] = {"launches": n, "ms_per_launch": round(per_launch_ms, 5),
+                         "share": round(kms / sum(v[0] for v in prof.values()), 4),
+                         "algorithmic_gbs": round(b / (per_launch_ms * 1e-3) / 1e9, 1) if b else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
+    ach = kernels[dom]["algorithmic_gbs"]
+    step_bytes = sum(bytes_per_site(k, prec, r) for k in kernels) * V
+    value = world * V * args.steps / (ms_max / 1e3)
+    h2d = V * 576
+    d2h = V * 576
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": METRIC,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == 4 else "f64",
+        "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
+        "config": {"workload": W["desc"], "lattice": list(dims), "storage": W["dtype"], "alpha": W["alpha"],
+                   "link_scale": W["link_scale"], "gauge_scale": W["gauge_scale"], "seed": W["seed"],
+                   "l2": f"inputs larger than L2: links {4 * r * prec * V / 1e6:.0f} MB per sweep",
+                   "parallelism": f"replicas x{world} (independent configs, no collective on the data path)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(ach / hbm_peak, 4) if ach else None,
+                     "traffic": profile_traffic(dom, args.workload),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
+        "step_roofline": {"algorithmic_bytes_per_site": step_bytes / V,
+                          "achieved_gbs": round(step_bytes / (ms_max / args.steps * 1e-3) / 1e9, 1),
+                          "frac": round(step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / hbm_peak, 4)},
+        "kernels": kernels,
+        "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 4), "iterations": iters,
+                          "fp32_iterations": split[0], "fp64_iterations": split[1], "converged": conv,
+                          "F": F, "theta": theta},
+        "e2e": {"value": round(V * iters_e2e * world / e2e_s, 1), "unit": METRIC, "seconds": round(e2e_s, 4),
+                "what": "lgf_load_links(pinned host) + lgf_fix(theta<tol) + lgf_store_links(pinned host)",
+                "h2d_bytes_per_step": round(h2d / max(iters_e2e, 1), 1),
+                "d2h_bytes_per_step": round(d2h / max(iters_e2e, 1), 1)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        n = args.cpu_iters
+        log(f"timing {n} oracle iteration(s) on the same {dims} input, 1 thread ...")
+        secs = time_oracle(U, n, W["alpha"])
+        line["cpu_baseline"] = {"value": round(V * n / secs, 1), "unit": METRIC, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} iteration(s) of the numpy FP64 oracle on the same {dims} input "
+                                          f"({secs:.1f} s, 1 thread)"}
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def run_reference(args, W):
+    """The oracle as it stands, on host cores, each step a bounded sample."""
+    import numpy as np
+
+    import lgf_inputs
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    budget = 150.0 / max(args.steps + args.warmup, 1)  # seconds per step
+    # per-site cost model from two small lattices
+    probe = {}
+    for L in (8, 12):
+        U = lgf_inputs.synthetic_config((L,) * 4, seed=W["seed"], link_scale=W["link_scale"])
+        probe[L] = time_oracle(U, 2, W["alpha"]) / 2 / L ** 4
+    slope = (probe[12] - probe[8]) / 4
+
+    def est(dims):
+        return int(np.prod(dims)) * max(probe[8] + slope * (max(dims) - 8), probe[8])
+
+    cands = [W["dims"]] + [(L,) * 4 for L in (24, 20, 16, 12, 8)]
+    dims = next((d for d in cands if est(d) <= budget), (8, 8, 8, 8))
+    U = lgf_inputs.synthetic_config(dims, seed=W["seed"], link_scale=W["link_scale"],
+                                    gauge_scale=W["gauge_scale"])
+    V = int(np.prod(dims))
+    time_oracle(U, args.warmup, W["alpha"]) if args.warmup else None
+    secs = time_oracle(U, args.steps, W["alpha"])
+    value = V * args.steps / secs
+    sample = (f"{args.steps} oracle iteration(s) on a {dims} lattice of the same recipe"
+              + ("" if tuple(dims) == tuple(W["dims"]) else f" (full {W['dims']} does not fit the time budget)")
+              + ", 1 thread")
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["desc"], "lattice": list(W["dims"]), "sample_lattice": list(dims)},
+        "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("warm-up raised to 3 steps (minimum)")
+        args.warmup = 3
+    W = WORKLOADS[args.workload]
+    line = run_reference(args, W) if args.impl == "reference" else run_ours(args, W)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * lgf.h -- C ABI of liblgf: SU(3) lattice Landau gauge fixing by steepest
+ * descent with Fourier acceleration on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one the paper uses (Cardoso, Bicudo, Silva, Oliveira,
+ * "Landau Gauge Fixing on GPUs and String Tension", Sec. 1: steepest descent
+ * with Fourier acceleration after Davies et al.; Sec. 2.2: one thread per
+ * site, structure-of-arrays lattice, 4D FFT built from 2D plus 2D
+ * transforms).  The paper prints no formula of the iteration; the library
+ * computes, per iteration and on a periodic lattice L = (Lx, Ly, Lz, Lt) of
+ * V sites:
+ *
+ *   A(x)      = sum_mu [U_mu(x - mu) - U_mu(x)]
+ *   Delta(x)  = A - A^dagger - (1/3) Tr(A - A^dagger)          (gradient)
+ *   F         = 1/(4*3*V) sum_{x,mu} Re Tr U_mu(x)              (functional)
+ *   theta     = 1/(3*V)   sum_x Tr Delta Delta^dagger           (convergence)
+ *   Delta~    = FFT^-1[ p2_max / p2(k) * FFT[Delta] ], 0 at k = 0,
+ *               p2(k) = sum_mu 4 sin^2(pi k_mu / L_mu)
+ *   g(x)      = reunitarised (1 + alpha/2 Delta~(x))             (gauge step)
+ *   U_mu(x)  <- g(x) U_mu(x) g(x + mu)^dagger                    (update)
+ *
+ * theta and F always describe the links *before* an update; an iteration is
+ * one applied update.
+ *
+ * Conventions for every entry point:
+ *   - Return value: LGF_OK (0) or a negative lgf_status.  No exception,
+ *     abort or device trap leaves the library; lgf_last_error() gives text.
+ *   - Host link arrays are complex128 "array of structures" in the order
+ *     [s][mu][i][j] (re, im interleaved), s = x + Lx*(y + Ly*(z + Lz*t)),
+ *     mu = 0..3 = x, y, z, t: V*4*18 doubles.  They are caller-owned and
+ *     copied; the library keeps no pointer to them.
+ *   - Device memory is library-owned, obtained through the allocator set
+ *     with lgf_set_allocator() (cudaMalloc by default) on the device that was
+ *     current at lgf_create().  All work runs on the handle's stream (the
+ *     legacy default stream until lgf_set_stream()).  Every call that
+ *     computes returns after its work on that stream has finished.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgf_ctx* lgf_handle;
+
+/* Storage / arithmetic of the working links (paper Sec. 3.1 compares single
+ * and double precision and the 18-real and 12-real forms). */
+enum lgf_dtype {
+  LGF_F64 = 0,      /* FP64 links, 18 reals, FP64 everywhere                  */
+  LGF_F32 = 1,      /* FP32 links/FFT/update, 18 reals; FP64 F, theta sums     */
+  LGF_F32_R12 = 2,  /* as LGF_F32, links stored as rows 1-2 (12 reals), row 3
+                       rebuilt as conj(row1 x row2) on load (paper Sec. 2.2)  */
+  LGF_F64_R12 = 3   /* FP64, 12-real storage                                  */
+};
+
+enum lgf_status {
+  LGF_OK = 0,
+  LGF_ERR_ARG = -1,            /* bad argument / unsupported lattice           */
+  LGF_ERR_CUDA = -2,           /* a CUDA runtime call failed                    */
+  LGF_ERR_OOM = -3,            /* the allocator returned NULL                   */
+  LGF_ERR_NOT_CONVERGED = -4,  /* lgf_fix used max_iter updates, theta >= tol   */
+  LGF_ERR_NONFINITE = -5,      /* F or theta became NaN/Inf (bad input links)   */
+  LGF_ERR_TIMEOUT = -6         /* a bounded device wait gave up                 */
+};
+
+enum lgf_param {
+  LGF_ALPHA = 0,        /* step size alpha (default 0.08)                       */
+  LGF_CHECK_EVERY = 1,  /* lgf_fix: iterations queued between host checks (32)  */
+  LGF_TAIL_THETA = 2,   /* mixed precision: theta at which the FP32 phase hands
+                           over to the FP64 tail (default 1e-11)                */
+  LGF_TAIL_MAX_FP32 = 3 /* mixed precision: cap on FP32 iterations (default: all) */
+};
+
+/* Device allocator hooks.  alloc returns a device pointer (NULL on failure);
+ * free releases it.  Passing NULL for both restores cudaMalloc/cudaFree.
+ * Process-wide; affects handles created afterwards. */
+typedef void* (*lgf_alloc_fn)(size_t bytes, int device, void* stream, void* user);
+typedef void (*lgf_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
+int lgf_set_allocator(lgf_alloc_fn alloc, lgf_free_fn free_fn, void* user);
+
+/* Create a context for an Lx x Ly x Lz x Lt periodic lattice (Sec. 2.2 keeps
+ * lattice constants in constant memory; here they live in the handle and are
+ * passed by value to every kernel).  Each extent must be in [2, 64] and a
+ * product of 2, 3 and 5 (the radices of the on-chip FFT); dtype is an
+ * lgf_dtype.  Allocates all device buffers.  On failure *out is NULL and
+ * lgf_last_error(NULL) describes the cause. */
+int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out);
+
+/* Release every device buffer (after synchronising the handle's stream). */
+int lgf_destroy(lgf_handle h);
+
+/* Run subsequent work on this cudaStream_t (e.g. torch's current stream). */
+int lgf_set_stream(lgf_handle h, void* cuda_stream);
+
+/* Set a numeric parameter (lgf_param).  alpha must lie in (0, 0.125]: the
+ * accelerated step contracts every mode by (1 - 16 alpha), which is stable
+ * only for alpha < 1/8. */
+int lgf_set_param(lgf_handle h, int key, double value);
+
+/* Copy V*4*18 doubles of host links in (layout above), converting to the
+ * handle's storage; links must be SU(3) to rounding.  Mixed-precision
+ * handles also keep the FP64 input for the FP64 tail. */
+int lgf_load_links(lgf_handle h, const double* host_aos);
+
+/* As lgf_load_links, from device memory (e.g. a torch tensor's data_ptr)
+ * on the handle's device. */
+int lgf_load_links_device(lgf_handle h, const double* dev_aos);
+
+/* Copy the current links out, as V*4*18 host doubles (layout above).  12-real
+ * storage rebuilds row 3. */
+int lgf_store_links(lgf_handle h, double* host_aos);
+
+/* Apply exactly n iterations (no convergence test).  Mixed-precision handles
+ * iterate in their FP32 storage. */
+int lgf_iterate(lgf_handle h, int n);
+
+/* Iterate until theta < theta_tol or max_iter updates have been applied.
+ * *iters_out (may be NULL) receives the number of updates.  Returns LGF_OK,
+ * LGF_ERR_NOT_CONVERGED or an error.  Mixed-precision handles run the FP32
+ * phase down to LGF_TAIL_THETA, then rebuild the links in FP64 from the
+ * loaded input and the accumulated gauge transformation and finish in FP64;
+ * the links are FP64 from then on until the next load. */
+int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out);
+
+/* F and theta of the current links (either pointer may be NULL). */
+int lgf_functional(lgf_handle h, double* F, double* theta);
+
+/* Intermediates of one iteration on the current links, without updating
+ * them, for step-by-step checks.  Each non-NULL output receives V*8 doubles
+ * (V complex pairs x 4): the gradient packed as (Delta01, Delta02, Delta12,
+ * Im Delta00 + i Im Delta11) per site, and the accelerated gradient Delta~ in
+ * the same packing; g receives V*18 doubles ([s][i][j] complex). */
+int lgf_probe(lgf_handle h, double* delta_packed, double* delta_tilde_packed, double* g);
+
+/* Updates of the last lgf_fix done in FP32 storage and in FP64 (a plain FP64
+ * handle reports all of them as FP64; a mixed handle's FP32 phase and tail). */
+int lgf_fix_split(lgf_handle h, int* fp32_iters, int* fp64_iters);
+
+/* The theta history (theta before each update) of the last precision phase
+ * of the last lgf_fix, up to cap entries; *n_out receives the count. */
+int lgf_history(lgf_handle h, double* theta_out, int cap, int* n_out);
+
+/* Text of the last error on h (or of the last failed lgf_create if h is NULL). */
+const char* lgf_last_error(lgf_handle h);
+
+/* Kernel launches this handle has issued since creation (for accounting). */
+long long lgf_launch_count(lgf_handle h);
+
+/* Kernel kinds of one iteration, for lgf_profile_read(). */
+enum lgf_kernel {
+  LGF_K_GRADIENT = 0,   /* gradient Delta + block partials of F, theta     */
+  LGF_K_REDUCE = 1,     /* final FP64 sums and the stop decision            */
+  LGF_K_FFT_XY = 2,     /* x-y plane FFT (forward and inverse)              */
+  LGF_K_FFT_ZT = 3,     /* z-t plane FFT, forward + p2_max/p2 + inverse     */
+  LGF_K_BUILD_G = 4,    /* g = reunitarised (1 + alpha/2 Delta~)            */
+  LGF_K_UPDATE = 5,     /* U_mu(x) <- g(x) U_mu(x) g(x+mu)^dagger          */
+  LGF_K_ACCUMULATE = 6, /* mixed precision: G <- g G                        */
+  LGF_K_OTHER = 7,      /* layout conversions, copies                       */
+  LGF_NUM_KERNELS = 8
+};
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream right
+ * before and after every launch (not part of the method; it measures it).
+ * enable = 1 clears the totals and starts recording, 0 stops. */
+int lgf_profile(lgf_handle h, int enable);
+
+/* Accumulated device milliseconds and launch counts per lgf_kernel kind
+ * since lgf_profile(h, 1): ms[k], launches[k] for k < n (either may be NULL). */
+int lgf_profile_read(lgf_handle h, double* ms, long long* launches, int n);
+
+/* Short name of a kernel kind ("update", ...), "" if out of range. */
+const char* lgf_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGF_H */

@@ -1,0 +1,147 @@
+"""GB300-native Landau gauge fixing (steepest descent with Fourier
+acceleration) for SU(3) lattice gauge fields.
+
+The work runs in ``liblgf.so`` (hand-written sm_103a CUDA kernels behind the C
+ABI of ``include/lgf.h``).  This package is its thin Python face:
+``GaugeFixer`` wraps one library handle; the raw entry points are in
+``paper_1208_1186_gb300._lib`` under their C names.
+
+Host link arrays are complex128 of shape (Lt, Lz, Ly, Lx, 4, 3, 3) (x fastest,
+mu = x, y, z, t), the layout ``lgf_load_links`` takes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import LgfError
+
+__all__ = ["GaugeFixer", "LgfError"]
+
+def _as_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class GaugeFixer:
+    """One liblgf handle for an (Lx, Ly, Lz, Lt) lattice.
+
+    dtype: 'f64' (FP64, 18 reals), 'f64_r12', 'f32' (FP32 bulk with FP64 F/theta
+    sums and an FP64 tail in ``fix``), 'f32_r12' (the same with 12-real links).
+    """
+
+    def __init__(self, dims, dtype: str = "f64", stream=None, torch_allocator: bool = True,
+                 alpha: float = 0.08):
+        self.lib = _lib.load()
+        if torch_allocator:
+            _lib.use_torch_allocator()
+        self.dims = tuple(int(v) for v in dims)
+        self.shape = (self.dims[3], self.dims[2], self.dims[1], self.dims[0])
+        self.V = int(np.prod(self.dims))
+        self.dtype = dtype
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.lgf_create(*self.dims, _lib.DTYPES[dtype], ctypes.byref(h)), "lgf_create")
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+        self.set_param(_lib.LGF_ALPHA, alpha)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lgf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration ----------------------------------------------------
+    def set_stream(self, stream):
+        ptr = stream if isinstance(stream, int) else stream.cuda_stream
+        _lib.check(self.lib.lgf_set_stream(self.h, ctypes.c_void_p(ptr)), "lgf_set_stream", self.h)
+
+    def set_param(self, key: int, value: float):
+        _lib.check(self.lib.lgf_set_param(self.h, key, float(value)), "lgf_set_param", self.h)
+
+    # -- links --------------------------------------------------------------
+    def load_links(self, U):
+        """Host complex128 array (numpy) or a CUDA complex128/float64 torch tensor."""
+        if isinstance(U, np.ndarray):
+            a = np.ascontiguousarray(U, dtype=np.complex128)
+            if a.size != self.V * 36:
+                raise ValueError(f"expected {self.V * 36} complex entries, got {a.size}")
+            _lib.check(self.lib.lgf_load_links(self.h, _as_ptr(a)), "lgf_load_links", self.h)
+        else:  # torch tensor on the device
+            if not U.is_cuda or not U.is_contiguous() or U.numel() * U.element_size() != self.V * 576:
+                raise ValueError("expected a contiguous CUDA tensor of V*4*3*3 complex128")
+            _lib.check(self.lib.lgf_load_links_device(self.h, ctypes.c_void_p(U.data_ptr())),
+                       "lgf_load_links_device", self.h)
+
+    def store_links(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape + (4, 3, 3), dtype=np.complex128)
+        _lib.check(self.lib.lgf_store_links(self.h, _as_ptr(out)), "lgf_store_links", self.h)
+        return out
+
+    # -- the method -----------------------------------------------------------
+    def iterate(self, n: int):
+        _lib.check(self.lib.lgf_iterate(self.h, int(n)), "lgf_iterate", self.h)
+
+    def fix(self, theta_tol: float, max_iter: int, raise_on_fail: bool = False):
+        """Returns (iterations, converged)."""
+        it = ctypes.c_int(0)
+        st = self.lib.lgf_fix(self.h, float(theta_tol), int(max_iter), ctypes.byref(it))
+        if st == _lib.LGF_ERR_NOT_CONVERGED and not raise_on_fail:
+            return it.value, False
+        _lib.check(st, "lgf_fix", self.h)
+        return it.value, True
+
+    def functional(self):
+        F, th = ctypes.c_double(), ctypes.c_double()
+        _lib.check(self.lib.lgf_functional(self.h, ctypes.byref(F), ctypes.byref(th)), "lgf_functional", self.h)
+        return F.value, th.value
+
+    def probe(self):
+        """Gradient, accelerated gradient (both packed, (.., 4) complex) and g
+        of the current links; the links are not changed."""
+        d = np.empty(self.shape + (4,), dtype=np.complex128)
+        dt = np.empty(self.shape + (4,), dtype=np.complex128)
+        g = np.empty(self.shape + (3, 3), dtype=np.complex128)
+        _lib.check(self.lib.lgf_probe(self.h, _as_ptr(d), _as_ptr(dt), _as_ptr(g)), "lgf_probe", self.h)
+        return {"delta": d, "delta_tilde": dt, "g": g}
+
+    def fix_split(self):
+        """(FP32 updates, FP64 updates) of the last fix."""
+        a, b = ctypes.c_int(0), ctypes.c_int(0)
+        _lib.check(self.lib.lgf_fix_split(self.h, ctypes.byref(a), ctypes.byref(b)), "lgf_fix_split", self.h)
+        return a.value, b.value
+
+    def history(self, cap: int = 1 << 16) -> np.ndarray:
+        buf = np.empty(cap, dtype=np.float64)
+        n = ctypes.c_int(0)
+        _lib.check(self.lib.lgf_history(self.h, _as_ptr(buf), cap, ctypes.byref(n)), "lgf_history", self.h)
+        return buf[: n.value].copy()
+
+    def launch_count(self) -> int:
+        return int(self.lib.lgf_launch_count(self.h))
+
+    def profile(self, enable: bool):
+        _lib.check(self.lib.lgf_profile(self.h, int(bool(enable))), "lgf_profile", self.h)
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since profile(True)."""
+        n = _lib.LGF_NUM_KERNELS
+        ms = np.zeros(n, dtype=np.float64)
+        cnt = np.zeros(n, dtype=np.int64)
+        _lib.check(self.lib.lgf_profile_read(self.h, _as_ptr(ms), _as_ptr(cnt), n), "lgf_profile_read", self.h)
+        return {self.lib.lgf_kernel_name(k).decode(): (float(ms[k]), int(cnt[k])) for k in range(n)}

@@ -1,0 +1,353 @@
+// Site-local kernels of one gauge-fixing iteration (one thread per lattice
+// site, as in the paper's Sec. 2.2, on structure-of-arrays links):
+//
+//   k_gradient  A(x) = sum_mu [U_mu(x-mu) - U_mu(x)], Delta = A - A^dag -
+//               (1/3) Tr(A - A^dag), stored packed as four complex fields
+//               (Delta01, Delta02, Delta12, Im Delta00 + i Im Delta11); block
+//               partial sums of Re Tr U and Tr Delta Delta^dag in FP64 with
+//               warp shuffles.
+//   k_reduce    fixed-order FP64 sum of the block partials -> F, theta, and
+//               the stop decision of the iteration queue.
+//   k_build_g   g(x) = reunitarised (1 + alpha/2 Delta~(x)), FP64 arithmetic.
+//   k_update    U_mu(x) <- g(x) U_mu(x) g(x+mu)^dag.
+//
+// Links of direction mu occupy NC complex planes of V elements:
+// U[(mu*NC + c)*V + s]; NC = 9 stores every entry, NC = 6 rows 1-2 only.
+#include "lgf_kernels.cuh"
+
+namespace lgf {
+
+namespace {
+
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+    a = l < nw ? sa[l] : 0.0;
+    b = l < nw ? sb[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
+template <class T, int NC>
+__device__ __forceinline__ M3<T> load_m3_rw(const cx<T>* base, int64_t V, int64_t s) {
+  M3<T> m;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m.e[c / 3][c % 3] = base[c * V + s];
+  if (NC == 6) complete_row3(m);
+  return m;
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restrict__ U, cx<T>* __restrict__ D,
+                                                           double2* __restrict__ partial, const Geom geo,
+                                                           const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int64_t V = geo.V;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double fsum = 0.0, tsum = 0.0;
+  if (s < V) {
+    int c[4];
+    site_coords(geo, s, c);
+    M3<T> A;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) A.e[i][j] = mk<T>(0, 0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const cx<T>* base = U + (int64_t)mu * NC * V;
+      const M3<T> own = load_m3<T, NC>(base, V, s);
+      const M3<T> back = load_m3<T, NC>(base, V, site_back(geo, s, c, mu));
+      fsum += (double)own.e[0][0].re + (double)own.e[1][1].re + (double)own.e[2][2].re;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A.e[i][j] = A.e[i][j] + (back.e[i][j] - own.e[i][j]);
+    }
+    const cx<T> d01 = A.e[0][1] - conj(A.e[1][0]);
+    const cx<T> d02 = A.e[0][2] - conj(A.e[2][0]);
+    const cx<T> d12 = A.e[1][2] - conj(A.e[2][1]);
+    const T a0 = 2 * A.e[0][0].im, a1 = 2 * A.e[1][1].im, a2 = 2 * A.e[2][2].im;
+    const T tr = (a0 + a1 + a2) / (T)3;
+    const T i0 = a0 - tr, i1 = a1 - tr;
+    D[s] = d01;
+    D[V + s] = d02;
+    D[2 * V + s] = d12;
+    D[3 * V + s] = mk<T>(i0, i1);
+    const double di0 = i0, di1 = i1, di2 = -(di0 + di1);
+    tsum = 2.0 * ((double)norm2(cvt<double>(d01)) + (double)norm2(cvt<double>(d02)) +
+                  (double)norm2(cvt<double>(d12))) +
+           di0 * di0 + di1 * di1 + di2 * di2;
+  }
+  block_sum2(fsum, tsum);
+  if (threadIdx.x == 0) partial[blockIdx.x] = make_double2(fsum, tsum);
+}
+
+// mode 0: F and theta only.  mode 1: also the iteration decision (history,
+// stop at theta < tol or at max_iter updates, count the update otherwise).
+__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, int n, DevState* st,
+                                                 double normF, double normT, int mode) {
+  if (mode == 1 && st->done) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 p = partial[i];
+    a += p.x;
+    b += p.y;
+  }
+  block_sum2(a, b);
+  if (threadIdx.x != 0) return;
+  const double F = a * normF, th = b * normT;
+  st->F = F;
+  st->theta = th;
+  const bool bad = !isfinite(F) || !isfinite(th);
+  if (bad) st->nonfinite = 1;
+  if (mode != 1) return;
+  if (st->hist != nullptr && st->iters < st->hist_cap) st->hist[st->iters] = th;
+  if (bad || (st->tol >= 0.0 && th < st->tol) || st->iters >= st->max_iter) {
+    st->done = 1;
+  } else {
+    st->iters += 1;
+  }
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_build_g(const cx<T>* __restrict__ D, cx<T>* __restrict__ g, int64_t V,
+                                                 double h, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const cx<double> c0 = cvt<double>(ldg(D + s));
+  const cx<double> c1 = cvt<double>(ldg(D + V + s));
+  const cx<double> c2 = cvt<double>(ldg(D + 2 * V + s));
+  const cx<double> c3 = cvt<double>(ldg(D + 3 * V + s));
+  // rows 1-2 of 1 + h Delta~; Delta~10 = -conj(Delta~01), Delta~_ii = i Im
+  M3<double> m;
+  m.e[0][0] = mk<double>(1.0, h * c3.re);
+  m.e[0][1] = scale(c0, h);
+  m.e[0][2] = scale(c1, h);
+  m.e[1][0] = mk<double>(-h * c0.re, h * c0.im);
+  m.e[1][1] = mk<double>(1.0, h * c3.im);
+  m.e[1][2] = scale(c2, h);
+  reunitarize(m);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) g[c * V + s] = cvt<T>(m.e[c / 3][c % 3]);
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_update(cx<T>* U, const cx<T>* __restrict__ g, const Geom geo,
+                                                const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int64_t V = geo.V;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  int c[4];
+  site_coords(geo, s, c);
+  const M3<T> gx = load_m3<T, NC>(g, V, s);
+  constexpr int ROWS = NC / 3;
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    cx<T>* base = U + (int64_t)mu * NC * V;
+    const M3<T> u = load_m3_rw<T, NC>(base, V, s);
+    const M3<T> gf = load_m3<T, NC>(g, V, site_fwd(geo, s, c, mu));
+    M3<T> w, r;
+    mm<T, ROWS>(w, gx, u);
+    mm_dag<T, ROWS>(r, w, gf);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) base[q * V + s] = r.e[q / 3][q % 3];
+  }
+}
+
+// one thread per (site, matrix): 18 doubles in, NC complex out; nmu matrices
+// per site (4 for links, 1 for a gauge field)
+template <class T, int NC>
+__global__ void k_aos_to_soa(const double* __restrict__ aos, cx<T>* __restrict__ U, int64_t V, int nmu) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nmu * V) return;
+  const int64_t s = i / nmu;
+  const int mu = (int)(i - s * nmu);
+  const double* src = aos + i * 18;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) U[((int64_t)mu * NC + c) * V + s] = mk<T>((T)src[2 * c], (T)src[2 * c + 1]);
+}
+
+template <class T, int NC>
+__global__ void k_soa_to_aos(const cx<T>* __restrict__ U, double* __restrict__ aos, int64_t V, int nmu) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nmu * V) return;
+  const int64_t s = i / nmu;
+  const int mu = (int)(i - s * nmu);
+  const M3<T> m = load_m3<T, NC>(U + (int64_t)mu * NC * V, V, s);
+  double* dst = aos + i * 18;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    dst[2 * c] = (double)m.e[c / 3][c % 3].re;
+    dst[2 * c + 1] = (double)m.e[c / 3][c % 3].im;
+  }
+}
+
+// G(x) <- reunitarised g(x) G(x), in the storage precision
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_accumulate(cx<T>* G, const cx<T>* __restrict__ g, int64_t V,
+                                                    const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const M3<T> a = load_m3<T, NC>(g, V, s);
+  const M3<T> b = load_m3_rw<T, NC>(G, V, s);
+  M3<T> r;
+  mm<T, 2>(r, a, b);
+  reunitarize(r);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) G[c * V + s] = r.e[c / 3][c % 3];
+}
+
+// FP64 copy of a stored gauge field, reunitarised in FP64: out has 9 planes
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_promote_gauge(const cx<T>* __restrict__ G, cx<double>* __restrict__ out,
+                                                       int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const M3<T> a = load_m3<T, NC>(G, V, s);
+  M3<double> m;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m.e[i][j] = cvt<double>(a.e[i][j]);
+  reunitarize(m);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) out[c * V + s] = m.e[c / 3][c % 3];
+}
+
+template <class T, int NC>
+__global__ void k_set_identity(cx<T>* __restrict__ G, int64_t V) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) G[c * V + s] = mk<T>((c % 4 == 0) ? (T)1 : (T)0, (T)0);
+}
+
+template <class T>
+__global__ void k_unpack_fields(const cx<T>* __restrict__ D, double* __restrict__ out, int64_t V) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * V) return;
+  const int64_t s = i >> 2;
+  const int f = (int)(i & 3);
+  const cx<T> v = D[(int64_t)f * V + s];
+  out[2 * i] = (double)v.re;
+  out[2 * i + 1] = (double)v.im;
+}
+
+inline unsigned blocks_for(int64_t n, int thr) { return (unsigned)((n + thr - 1) / thr); }
+
+}  // namespace
+
+#define LGF_DISPATCH(prec, nc, KERNEL_CALL)         \
+  do {                                              \
+    if ((prec) == 8 && (nc) == 9) {                 \
+      using T = double;                             \
+      constexpr int NC = 9;                         \
+      KERNEL_CALL;                                  \
+    } else if ((prec) == 8) {                       \
+      using T = double;                             \
+      constexpr int NC = 6;                         \
+      KERNEL_CALL;                                  \
+    } else if ((nc) == 9) {                         \
+      using T = float;                              \
+      constexpr int NC = 9;                         \
+      KERNEL_CALL;                                  \
+    } else {                                        \
+      using T = float;                              \
+      constexpr int NC = 6;                         \
+      KERNEL_CALL;                                  \
+    }                                               \
+  } while (0)
+
+cudaError_t launch_gradient(int prec, int nc, const void* U, void* D, double2* partial, const Geom& geo,
+                            const DevState* st, cudaStream_t s) {
+  const unsigned nb = (unsigned)gradient_blocks(geo.V);
+  LGF_DISPATCH(prec, nc,
+               (k_gradient<T, NC><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<T>*>(U),
+                                                              static_cast<cx<T>*>(D), partial, geo, st)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_reduce(const double2* partial, int n, DevState* st, double normF, double normT, int mode,
+                          cudaStream_t s) {
+  k_reduce<<<1, 1024, 0, s>>>(partial, n, st, normF, normT, mode);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
+                           const DevState* st, cudaStream_t s) {
+  LGF_DISPATCH(prec, nc,
+               (k_build_g<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<T>*>(D),
+                                                                    static_cast<cx<T>*>(g), V, half_alpha, st)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& geo, const DevState* st,
+                          cudaStream_t s) {
+  LGF_DISPATCH(prec, nc,
+               (k_update<T, NC><<<blocks_for(geo.V, 256), 256, 0, s>>>(static_cast<cx<T>*>(U),
+                                                                       static_cast<const cx<T>*>(g), geo, st)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_aos_to_soa(int prec, int nc, const double* aos, void* U, int64_t V, int nmu, cudaStream_t s) {
+  LGF_DISPATCH(prec, nc,
+               (k_aos_to_soa<T, NC><<<blocks_for(nmu * V, 256), 256, 0, s>>>(aos, static_cast<cx<T>*>(U), V, nmu)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_soa_to_aos(int prec, int nc, const void* U, double* aos, int64_t V, int nmu, cudaStream_t s) {
+  LGF_DISPATCH(prec, nc,
+               (k_soa_to_aos<T, NC><<<blocks_for(nmu * V, 256), 256, 0, s>>>(static_cast<const cx<T>*>(U), aos, V,
+                                                                             nmu)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_accumulate(int prec, int nc, void* G, const void* g, int64_t V, const DevState* st,
+                              cudaStream_t s) {
+  LGF_DISPATCH(prec, nc,
+               (k_accumulate<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<cx<T>*>(G),
+                                                                       static_cast<const cx<T>*>(g), V, st)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, int64_t V, cudaStream_t s) {
+  LGF_DISPATCH(prec, nc,
+               (k_promote_gauge<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<T>*>(G),
+                                                                          static_cast<cx<double>*>(out64), V)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_set_identity(int prec, int nc, void* G, int64_t V, cudaStream_t s) {
+  LGF_DISPATCH(prec, nc, (k_set_identity<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<cx<T>*>(G), V)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_unpack_fields(int prec, const void* D, double* out, int64_t V, cudaStream_t s) {
+  if (prec == 8)
+    k_unpack_fields<double><<<blocks_for(4 * V, 256), 256, 0, s>>>(static_cast<const cx<double>*>(D), out, V);
+  else
+    k_unpack_fields<float><<<blocks_for(4 * V, 256), 256, 0, s>>>(static_cast<const cx<float>*>(D), out, V);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace lgf

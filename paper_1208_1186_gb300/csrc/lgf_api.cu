@@ -1,0 +1,689 @@
+// C ABI of liblgf (declared in include/lgf.h): handle management, device
+// buffers, and the host-side queueing of gauge-fixing iterations.
+//
+// One iteration (Sec. 1 of the paper: steepest descent with Fourier
+// acceleration; Sec. 2.2: one thread per site, 2D plus 2D FFT) is the kernel
+// chain
+//   gradient -> reduce -> fft_xy(fwd) -> fft_zt(fwd, scale, inv)
+//            -> fft_xy(inv) -> build_g -> update [-> accumulate G]
+// on the handle's stream.  The reduce kernel decides on the device whether
+// the update of its iteration is applied (theta < tol or max_iter reached
+// stop the queue); every later kernel reads that decision first, so lgf_fix
+// queues LGF_CHECK_EVERY iterations between host synchronisations and still
+// stops at exactly the first iteration with theta < tol.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lgf.h"
+#include "lgf_kernels.cuh"
+
+using namespace lgf;
+
+namespace {
+
+thread_local std::string g_last_create_error;
+
+struct Allocator {
+  lgf_alloc_fn alloc = nullptr;
+  lgf_free_fn free_fn = nullptr;
+  void* user = nullptr;
+};
+Allocator g_alloc;
+
+// Buffers of one working precision: links, packed gradient, gauge step,
+// twiddle factors.
+struct Engine {
+  int prec = 8;  // bytes per real: 8 (FP64) or 4 (FP32)
+  int nc = 9;    // complex entries stored per matrix
+  void* U = nullptr;
+  void* D = nullptr;
+  void* g = nullptr;
+  void* tw = nullptr;
+  FftGeom fg{};  // FFT tiling for this precision
+  size_t cbytes() const { return 2 * (size_t)prec; }
+};
+
+}  // namespace
+
+struct lgf_ctx {
+  int L[4] = {0, 0, 0, 0};
+  int64_t V = 0;
+  int dtype = 0;
+  bool mixed = false;  // FP32 bulk + FP64 tail
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double alpha = 0.08;
+  int check_every = 32;
+  double tail_theta = 1e-11;
+  long long tail_max32 = -1;
+
+  Geom geo{};
+  Engine e64, e32;
+  Engine* cur = nullptr;     // engine that holds the current links
+  void* G = nullptr;         // mixed: accumulated gauge transformation (e32 storage)
+  double* Uorig = nullptr;   // mixed: FP64 SoA copy of the loaded links (9 planes)
+  double* sin2 = nullptr;    // [4][kMaxL] 4 sin^2(pi k / L)
+  double2* partial = nullptr;
+  int nblk = 0;
+  DevState* st = nullptr;    // device
+  DevState* st_host = nullptr;  // pinned mirror
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int hist_n = 0;
+  double* staging = nullptr;  // device FP64 AoS link buffer (V*72 doubles), lazily
+  size_t staging_bytes = 0;
+  bool loaded = false;
+  long long launches = 0;
+  long long total_updates = 0;
+  int last_n32 = 0, last_n64 = 0;  // split of the last lgf_fix
+  std::string err;
+  // per-kernel timing (lgf_profile): an event before and after each launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // kernel kind of event pair i (events 2i, 2i+1)
+  double prof_ms[LGF_NUM_KERNELS] = {};
+  long long prof_n[LGF_NUM_KERNELS] = {};
+  struct Alloc {
+    void* p;
+    size_t n;
+  };
+  std::vector<Alloc> allocs;
+};
+
+namespace {
+
+int fail(lgf_handle h, int code, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_last_create_error = msg;
+  return code;
+}
+
+int cuda_fail(lgf_handle h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(h, LGF_ERR_CUDA, m);
+}
+
+#define LGF_CUDA(h, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+// event slot for the next profiled launch (grows the pool on demand)
+cudaError_t prof_begin(lgf_handle h, int kind) {
+  const size_t i = h->ev_kind.size();
+  while (h->ev_pool.size() < 2 * i + 2) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    h->ev_pool.push_back(ev);
+  }
+  h->ev_kind.push_back(kind);
+  return cudaEventRecord(h->ev_pool[2 * i], h->stream);
+}
+
+cudaError_t prof_end(lgf_handle h) {
+  return cudaEventRecord(h->ev_pool[2 * (h->ev_kind.size() - 1) + 1], h->stream);
+}
+
+// Launch one kernel of the given kind, counting it and, when profiling,
+// bracketing it with events on the handle's stream.
+#define LGF_LAUNCH(h, kind, call)                             \
+  do {                                                        \
+    if ((h)->profiling) LGF_CUDA(h, prof_begin((h), (kind))); \
+    LGF_CUDA(h, call);                                        \
+    if ((h)->profiling) LGF_CUDA(h, prof_end(h));             \
+    (h)->launches += 1;                                       \
+  } while (0)
+
+void* dev_alloc(lgf_handle h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (g_alloc.alloc) {
+    p = g_alloc.alloc(bytes, h->device, (void*)h->stream, g_alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->allocs.push_back({p, bytes});
+  return p;
+}
+
+void dev_free_all(lgf_handle h) {
+  for (auto& a : h->allocs) {
+    if (g_alloc.free_fn)
+      g_alloc.free_fn(a.p, a.n, h->device, (void*)h->stream, g_alloc.user);
+    else
+      cudaFree(a.p);
+  }
+  h->allocs.clear();
+}
+
+int alloc_engine(lgf_handle h, Engine& e) {
+  const int64_t V = h->V;
+  e.U = dev_alloc(h, (size_t)4 * e.nc * V * e.cbytes());
+  e.D = dev_alloc(h, (size_t)4 * V * e.cbytes());
+  e.g = dev_alloc(h, (size_t)9 * V * e.cbytes());
+  e.tw = dev_alloc(h, (size_t)4 * kMaxL * e.cbytes());
+  if (!e.U || !e.D || !e.g || !e.tw) return fail(h, LGF_ERR_OOM, "device allocation failed");
+  // twiddle factors e^{-2 pi i m / L} per axis, computed in long double
+  std::vector<double> tw64(8 * kMaxL, 0.0);
+  std::vector<float> tw32(8 * kMaxL, 0.0f);
+  for (int a = 0; a < 4; ++a) {
+    const int L = h->L[a];
+    for (int m = 0; m < L; ++m) {
+      const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)L;
+      const double c = (double)cosl(ang), s = (double)-sinl(ang);
+      tw64[2 * (a * kMaxL + m)] = c;
+      tw64[2 * (a * kMaxL + m) + 1] = s;
+      tw32[2 * (a * kMaxL + m)] = (float)c;
+      tw32[2 * (a * kMaxL + m) + 1] = (float)s;
+    }
+  }
+  if (e.prec == 8)
+    LGF_CUDA(h, cudaMemcpy(e.tw, tw64.data(), tw64.size() * sizeof(double), cudaMemcpyHostToDevice));
+  else
+    LGF_CUDA(h, cudaMemcpy(e.tw, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return LGF_OK;
+}
+
+int ensure_staging(lgf_handle h) {
+  const size_t need = (size_t)h->V * 72 * sizeof(double);
+  if (h->staging && h->staging_bytes >= need) return LGF_OK;
+  h->staging = static_cast<double*>(dev_alloc(h, need));
+  if (!h->staging) return fail(h, LGF_ERR_OOM, "device allocation of the link staging buffer failed");
+  h->staging_bytes = need;
+  return LGF_OK;
+}
+
+int sync_state(lgf_handle h) {
+  LGF_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+int reset_state(lgf_handle h, double tol, int max_iter, bool with_hist) {
+  DevState s{};
+  s.F = 0.0;
+  s.theta = 0.0;
+  s.done = 0;
+  s.iters = 0;
+  s.nonfinite = 0;
+  s.max_iter = max_iter;
+  s.tol = tol;
+  s.hist = with_hist ? h->hist : nullptr;
+  s.hist_cap = with_hist ? h->hist_cap : 0;
+  *h->st_host = s;
+  LGF_CUDA(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  return LGF_OK;
+}
+
+// Steps a1-a6 of one iteration (gradient through g) on engine e.  st may be
+// null (no stop logic).
+int queue_to_gauge(lgf_handle h, Engine& e, const DevState* st, int reduce_mode) {
+  cudaStream_t s = h->stream;
+  LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, st, s));
+  LGF_LAUNCH(h, LGF_K_REDUCE,
+             launch_reduce(h->partial, h->nblk, h->st, 1.0 / (12.0 * (double)h->V), 1.0 / (3.0 * (double)h->V),
+                           reduce_mode, s));
+  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 0, st, s));
+  LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_fft_zt(e.prec, e.D, e.fg, e.tw, h->sin2, st, s));
+  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 1, st, s));
+  LGF_LAUNCH(h, LGF_K_BUILD_G, launch_build_g(e.prec, e.nc, e.D, e.g, h->V, 0.5 * h->alpha, st, s));
+  return LGF_OK;
+}
+
+// One full iteration.  On the FP32 engine of a mixed handle the gauge
+// transformation accumulated since the last load is kept up to date, so that
+// the FP32 links always equal G U_loaded G^dagger up to FP32 rounding.
+int queue_iteration(lgf_handle h, Engine& e) {
+  const bool track_gauge = h->mixed && &e == &h->e32;
+  int rc = queue_to_gauge(h, e, h->st, 1);
+  if (rc) return rc;
+  LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(e.prec, e.nc, e.U, e.g, h->geo, h->st, h->stream));
+  if (track_gauge)
+    LGF_LAUNCH(h, LGF_K_ACCUMULATE, launch_accumulate(e.prec, e.nc, h->G, e.g, h->V, h->st, h->stream));
+  return LGF_OK;
+}
+
+// Run engine e until theta < tol, max_iter updates, or (if stall_check) theta
+// stops falling between host checks.  Returns LGF_OK / NOT_CONVERGED / error
+// and the number of updates through *done_iters.
+int run_fix(lgf_handle h, Engine& e, double tol, int max_iter, bool stall_check,
+            int* done_iters, bool* converged) {
+  int rc = reset_state(h, tol, max_iter, true);
+  if (rc) return rc;
+  long long queued = 0;
+  double last_theta = INFINITY;
+  int stalls = 0;
+  *converged = false;
+  for (;;) {
+    const long long room = (long long)max_iter + 1 - queued;
+    const int k = (int)(room < h->check_every ? room : h->check_every);
+    for (int i = 0; i < k; ++i) {
+      rc = queue_iteration(h, e);
+      if (rc) return rc;
+    }
+    queued += k;
+    rc = sync_state(h);
+    if (rc) return rc;
+    const DevState& s = *h->st_host;
+    if (s.nonfinite) return fail(h, LGF_ERR_NONFINITE, "F or theta is not finite (non-SU(3) or NaN input links?)");
+    if (s.done || queued >= (long long)max_iter + 1) break;
+    if (stall_check) {
+      if (s.theta > 0.5 * last_theta) {
+        if (++stalls >= 2) {
+          // hand over: stop the FP32 phase at the next reduce
+          break;
+        }
+      } else {
+        stalls = 0;
+      }
+      last_theta = s.theta;
+    }
+  }
+  const DevState& s = *h->st_host;
+  *done_iters = s.iters;
+  h->hist_n = s.iters + 1 < h->hist_cap ? s.iters + 1 : h->hist_cap;
+  *converged = s.theta < tol;
+  return LGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lgf_set_allocator(lgf_alloc_fn alloc, lgf_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return LGF_ERR_ARG;
+  g_alloc.alloc = alloc;
+  g_alloc.free_fn = free_fn;
+  g_alloc.user = user;
+  return LGF_OK;
+}
+
+int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out) {
+  if (!out) return fail(nullptr, LGF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  const int Ls[4] = {Lx, Ly, Lz, Lt};
+  if (dtype < LGF_F64 || dtype > LGF_F64_R12) return fail(nullptr, LGF_ERR_ARG, "unknown dtype");
+  FftGeom fg{};
+  for (int a = 0; a < 4; ++a) {
+    if (!make_axis_plan(Ls[a], &fg.ax[a]))
+      return fail(nullptr, LGF_ERR_ARG,
+                  "each lattice extent must be in [2, 64] and a product of 2, 3 and 5; got " +
+                      std::to_string(Ls[a]));
+    fg.L[a] = Ls[a];
+  }
+  lgf_ctx* h = new (std::nothrow) lgf_ctx();
+  if (!h) return fail(nullptr, LGF_ERR_OOM, "host allocation failed");
+  h->dtype = dtype;
+  h->mixed = (dtype == LGF_F32 || dtype == LGF_F32_R12);
+  int64_t V = 1;
+  for (int a = 0; a < 4; ++a) {
+    h->L[a] = Ls[a];
+    h->geo.L[a] = Ls[a];
+    h->geo.stride[a] = V;
+    V *= Ls[a];
+  }
+  h->V = V;
+  h->geo.V = V;
+  fg.V = V;
+  double p2max = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    double m = 0.0;
+    for (int k = 0; k < Ls[a]; ++k) {
+      const double sk = sin(M_PI * (double)k / (double)Ls[a]);
+      m = fmax(m, 4.0 * sk * sk);
+    }
+    p2max += m;
+  }
+  fg.p2max = p2max;
+  auto bail = [&](int code) {
+    std::string msg = h->err;
+    dev_free_all(h);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    delete h;
+    g_last_create_error = msg;
+    return code;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    h->err = "no CUDA device";
+    return bail(LGF_ERR_CUDA);
+  }
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+
+  // engines: FP64 always (working engine of FP64 handles, tail of mixed ones)
+  h->e64.prec = 8;
+  h->e64.nc = (dtype == LGF_F64_R12) ? 6 : 9;
+  if (h->mixed) {
+    h->e64.nc = 9;
+    h->e32.prec = 4;
+    h->e32.nc = (dtype == LGF_F32_R12) ? 6 : 9;
+  }
+  // FFT tiling: Bx consecutive x (>= 32 bytes of complex data when Lx allows)
+  auto pick = [&](Engine& e) -> bool {
+    FftGeom g = fg;
+    const int want = e.prec == 8 ? 2 : 4;
+    int bx = 1;
+    for (int b = want; b >= 1; b >>= 1)
+      if (Lx % b == 0) {
+        bx = b;
+        break;
+      }
+    g.Bx = bx;
+    g.Pxy = Lx + 1;
+    g.Pt = bx * (Lz + 1);
+    e.fg = g;
+    return fft_xy_smem(g, e.prec) <= (size_t)smem_optin && fft_zt_smem(g, e.prec) <= (size_t)smem_optin;
+  };
+  if (!pick(h->e64) || (h->mixed && !pick(h->e32))) {
+    h->err = "lattice planes too large for the shared-memory FFT";
+    return bail(LGF_ERR_ARG);
+  }
+  // the opt-in limit is process-wide per kernel: always raise it to the device maximum
+  cudaError_t e = fft_set_smem_limits(8, smem_optin, smem_optin);
+  if (e == cudaSuccess) e = fft_set_smem_limits(4, smem_optin, smem_optin);
+  if (e != cudaSuccess) {
+    cuda_fail(h, e, "cudaFuncSetAttribute");
+    return bail(LGF_ERR_CUDA);
+  }
+
+  int rc = alloc_engine(h, h->e64);
+  if (!rc && h->mixed) rc = alloc_engine(h, h->e32);
+  if (rc) return bail(rc);
+  h->cur = h->mixed ? &h->e32 : &h->e64;
+  if (h->mixed) {
+    h->G = dev_alloc(h, (size_t)h->e32.nc * V * h->e32.cbytes());
+    h->Uorig = static_cast<double*>(dev_alloc(h, (size_t)4 * 9 * V * 16));
+    if (!h->G || !h->Uorig) {
+      h->err = "device allocation failed";
+      return bail(LGF_ERR_OOM);
+    }
+  }
+  h->nblk = gradient_blocks(V);
+  h->partial = static_cast<double2*>(dev_alloc(h, (size_t)h->nblk * sizeof(double2)));
+  h->st = static_cast<DevState*>(dev_alloc(h, sizeof(DevState)));
+  h->sin2 = static_cast<double*>(dev_alloc(h, 4 * kMaxL * sizeof(double)));
+  h->hist_cap = 1 << 16;
+  h->hist = static_cast<double*>(dev_alloc(h, (size_t)h->hist_cap * sizeof(double)));
+  if (!h->partial || !h->st || !h->sin2 || !h->hist) {
+    h->err = "device allocation failed";
+    return bail(LGF_ERR_OOM);
+  }
+  if (cudaMallocHost(&h->st_host, sizeof(DevState)) != cudaSuccess) {
+    h->st_host = nullptr;
+    h->err = "pinned host allocation failed";
+    return bail(LGF_ERR_OOM);
+  }
+  std::vector<double> s2(4 * kMaxL, 0.0);
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < Ls[a]; ++k) {
+      const long double sk = sinl(3.14159265358979323846264338327950288L * (long double)k / (long double)Ls[a]);
+      s2[a * kMaxL + k] = (double)(4.0L * sk * sk);
+    }
+  if (cudaMemcpy(h->sin2, s2.data(), s2.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    h->err = "copy of the momentum table failed";
+    return bail(LGF_ERR_CUDA);
+  }
+  if (reset_state(h, -1.0, 0, false) || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    h->err = "state initialisation failed";
+    return bail(LGF_ERR_CUDA);
+  }
+  *out = h;
+  return LGF_OK;
+}
+
+int lgf_destroy(lgf_handle h) {
+  if (!h) return LGF_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+  dev_free_all(h);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  delete h;
+  return LGF_OK;
+}
+
+int lgf_set_stream(lgf_handle h, void* cuda_stream) {
+  if (!h) return LGF_ERR_ARG;
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return LGF_OK;
+}
+
+int lgf_set_param(lgf_handle h, int key, double value) {
+  if (!h) return LGF_ERR_ARG;
+  switch (key) {
+    case LGF_ALPHA:
+      if (!(value > 0.0 && value <= 0.125)) return fail(h, LGF_ERR_ARG, "alpha must lie in (0, 0.125]");
+      h->alpha = value;
+      return LGF_OK;
+    case LGF_CHECK_EVERY:
+      if (!(value >= 1 && value <= 4096)) return fail(h, LGF_ERR_ARG, "check_every must lie in [1, 4096]");
+      h->check_every = (int)value;
+      return LGF_OK;
+    case LGF_TAIL_THETA:
+      if (!(value > 0.0)) return fail(h, LGF_ERR_ARG, "tail theta must be positive");
+      h->tail_theta = value;
+      return LGF_OK;
+    case LGF_TAIL_MAX_FP32:
+      h->tail_max32 = (long long)value;
+      return LGF_OK;
+    default:
+      return fail(h, LGF_ERR_ARG, "unknown parameter key");
+  }
+}
+
+static int load_from_device_aos(lgf_handle h, const double* aos) {
+  const int64_t V = h->V;
+  if (h->mixed) {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, 9, aos, h->Uorig, V, 4, h->stream));
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(4, h->e32.nc, aos, h->e32.U, V, 4, h->stream));
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_set_identity(4, h->e32.nc, h->G, V, h->stream));
+    h->cur = &h->e32;
+  } else {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
+  }
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->loaded = true;
+  h->total_updates = 0;
+  return LGF_OK;
+}
+
+int lgf_load_links(lgf_handle h, const double* host_aos) {
+  if (!h || !host_aos) return LGF_ERR_ARG;
+  int rc = ensure_staging(h);
+  if (rc) return rc;
+  LGF_CUDA(h, cudaMemcpyAsync(h->staging, host_aos, (size_t)h->V * 72 * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+  return load_from_device_aos(h, h->staging);
+}
+
+int lgf_load_links_device(lgf_handle h, const double* dev_aos) {
+  if (!h || !dev_aos) return LGF_ERR_ARG;
+  return load_from_device_aos(h, dev_aos);
+}
+
+int lgf_store_links(lgf_handle h, double* host_aos) {
+  if (!h || !host_aos) return LGF_ERR_ARG;
+  if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
+  int rc = ensure_staging(h);
+  if (rc) return rc;
+  Engine& e = *h->cur;
+  LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(e.prec, e.nc, e.U, h->staging, h->V, 4, h->stream));
+  LGF_CUDA(h, cudaMemcpyAsync(host_aos, h->staging, (size_t)h->V * 72 * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+int lgf_iterate(lgf_handle h, int n) {
+  if (!h || n < 0) return LGF_ERR_ARG;
+  if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
+  int rc = reset_state(h, -1.0, n, false);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    rc = queue_iteration(h, *h->cur);
+    if (rc) return rc;
+  }
+  rc = sync_state(h);
+  if (rc) return rc;
+  if (h->st_host->nonfinite) return fail(h, LGF_ERR_NONFINITE, "F or theta is not finite");
+  h->total_updates += h->st_host->iters;
+  return LGF_OK;
+}
+
+int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out) {
+  if (!h || max_iter < 0 || !(theta_tol > 0.0)) return LGF_ERR_ARG;
+  if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
+  if (iters_out) *iters_out = 0;
+  h->last_n32 = h->last_n64 = 0;
+  int n1 = 0, n2 = 0;
+  bool conv = false;
+  int rc;
+  if (h->mixed && h->cur == &h->e32) {
+    // FP32 phase; G has been accumulated since the load
+    const int64_t V = h->V;
+    const double tol32 = theta_tol > h->tail_theta ? theta_tol : h->tail_theta;
+    int cap32 = max_iter;
+    if (h->tail_max32 >= 0 && h->tail_max32 < cap32) cap32 = (int)h->tail_max32;
+    rc = run_fix(h, h->e32, tol32, cap32, true, &n1, &conv);
+    if (rc) return rc;
+    h->total_updates += n1;
+    h->last_n32 = n1;
+    if (conv && h->st_host->theta < theta_tol) {
+      if (iters_out) *iters_out = n1;
+      return LGF_OK;
+    }
+    // FP64 tail from the loaded links and the reunitarised accumulated G
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
+    LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
+    h->cur = &h->e64;
+  }
+  const int left = max_iter - n1;
+  rc = run_fix(h, *h->cur, theta_tol, left, false, &n2, &conv);
+  if (rc) return rc;
+  h->total_updates += n2;
+  if (h->cur == &h->e64)
+    h->last_n64 = n2;
+  else
+    h->last_n32 += n2;
+  if (iters_out) *iters_out = n1 + n2;
+  return conv ? LGF_OK : fail(h, LGF_ERR_NOT_CONVERGED, "max_iter reached with theta >= tol");
+}
+
+int lgf_functional(lgf_handle h, double* F, double* theta) {
+  if (!h) return LGF_ERR_ARG;
+  if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
+  Engine& e = *h->cur;
+  LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, nullptr, h->stream));
+  LGF_LAUNCH(h, LGF_K_REDUCE,
+             launch_reduce(h->partial, h->nblk, h->st, 1.0 / (12.0 * (double)h->V), 1.0 / (3.0 * (double)h->V), 0,
+                           h->stream));
+  int rc = sync_state(h);
+  if (rc) return rc;
+  if (F) *F = h->st_host->F;
+  if (theta) *theta = h->st_host->theta;
+  if (h->st_host->nonfinite) return fail(h, LGF_ERR_NONFINITE, "F or theta is not finite");
+  return LGF_OK;
+}
+
+int lgf_probe(lgf_handle h, double* delta_packed, double* delta_tilde_packed, double* g) {
+  if (!h) return LGF_ERR_ARG;
+  if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
+  int rc = ensure_staging(h);
+  if (rc) return rc;
+  Engine& e = *h->cur;
+  const int64_t V = h->V;
+  cudaStream_t s = h->stream;
+  LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, nullptr, s));
+  LGF_LAUNCH(h, LGF_K_REDUCE,
+             launch_reduce(h->partial, h->nblk, h->st, 1.0 / (12.0 * (double)V), 1.0 / (3.0 * (double)V), 0, s));
+  if (delta_packed) {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_unpack_fields(e.prec, e.D, h->staging, V, s));
+    LGF_CUDA(h, cudaMemcpyAsync(delta_packed, h->staging, (size_t)V * 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LGF_CUDA(h, cudaStreamSynchronize(s));
+  }
+  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 0, nullptr, s));
+  LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_fft_zt(e.prec, e.D, e.fg, e.tw, h->sin2, nullptr, s));
+  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 1, nullptr, s));
+  LGF_LAUNCH(h, LGF_K_BUILD_G, launch_build_g(e.prec, e.nc, e.D, e.g, V, 0.5 * h->alpha, nullptr, s));
+  if (delta_tilde_packed) {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_unpack_fields(e.prec, e.D, h->staging, V, s));
+    LGF_CUDA(h, cudaMemcpyAsync(delta_tilde_packed, h->staging, (size_t)V * 8 * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    LGF_CUDA(h, cudaStreamSynchronize(s));
+  }
+  if (g) {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(e.prec, e.nc, e.g, h->staging, V, 1, s));
+    LGF_CUDA(h, cudaMemcpyAsync(g, h->staging, (size_t)V * 18 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  LGF_CUDA(h, cudaStreamSynchronize(s));
+  return LGF_OK;
+}
+
+int lgf_fix_split(lgf_handle h, int* fp32_iters, int* fp64_iters) {
+  if (!h) return LGF_ERR_ARG;
+  if (fp32_iters) *fp32_iters = h->last_n32;
+  if (fp64_iters) *fp64_iters = h->last_n64;
+  return LGF_OK;
+}
+
+int lgf_history(lgf_handle h, double* theta_out, int cap, int* n_out) {
+  if (!h) return LGF_ERR_ARG;
+  const int n = h->hist_n < cap ? h->hist_n : cap;
+  if (theta_out && n > 0) LGF_CUDA(h, cudaMemcpy(theta_out, h->hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = n;
+  return LGF_OK;
+}
+
+int lgf_profile(lgf_handle h, int enable) {
+  if (!h) return LGF_ERR_ARG;
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (enable) {
+    h->ev_kind.clear();
+    for (int k = 0; k < LGF_NUM_KERNELS; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_n[k] = 0;
+    }
+  }
+  h->profiling = enable != 0;
+  return LGF_OK;
+}
+
+int lgf_profile_read(lgf_handle h, double* ms, long long* launches, int n) {
+  if (!h || n < 0) return LGF_ERR_ARG;
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+    float t = 0.0f;
+    LGF_CUDA(h, cudaEventElapsedTime(&t, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+    h->prof_ms[h->ev_kind[i]] += t;
+    h->prof_n[h->ev_kind[i]] += 1;
+  }
+  h->ev_kind.clear();
+  for (int k = 0; k < n && k < LGF_NUM_KERNELS; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_n[k];
+  }
+  return LGF_OK;
+}
+
+const char* lgf_kernel_name(int kind) {
+  static const char* names[LGF_NUM_KERNELS] = {"gradient", "reduce", "fft_xy", "fft_zt",
+                                               "build_g",  "update", "accumulate", "other"};
+  return (kind >= 0 && kind < LGF_NUM_KERNELS) ? names[kind] : "";
+}
+
+const char* lgf_last_error(lgf_handle h) { return h ? h->err.c_str() : g_last_create_error.c_str(); }
+
+long long lgf_launch_count(lgf_handle h) { return h ? h->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// Shared device definitions for liblgf: complex arithmetic, SU(3) matrices in
+// structure-of-arrays storage, lattice geometry and the state that lets a
+// queue of iterations stop on the device once theta is below tolerance.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lgf {
+
+// ---------------------------------------------------------------------------
+// complex numbers
+// ---------------------------------------------------------------------------
+template <class T>
+struct alignas(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+template <class T>
+__host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> c;
+  c.re = r;
+  c.im = i;
+  return c;
+}
+template <class T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.re + b.re, a.im + b.im); }
+template <class T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.re - b.re, a.im - b.im); }
+template <class T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+  return mk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class T>
+__device__ __forceinline__ cx<T> conj(cx<T> a) { return mk<T>(a.re, -a.im); }
+// a * conj(b)
+template <class T>
+__device__ __forceinline__ cx<T> mul_cj(cx<T> a, cx<T> b) {
+  return mk<T>(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+template <class T>
+__device__ __forceinline__ cx<T> scale(cx<T> a, T s) { return mk<T>(a.re * s, a.im * s); }
+template <class T>
+__device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+
+template <class D, class S>
+__device__ __forceinline__ cx<D> cvt(cx<S> a) { return mk<D>((D)a.re, (D)a.im); }
+
+// read-only, cached load of one complex element
+template <class T>
+__device__ __forceinline__ cx<T> ldg(const cx<T>* p);
+template <>
+__device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 complex matrices
+// ---------------------------------------------------------------------------
+template <class T>
+struct M3 {
+  cx<T> e[3][3];
+};
+
+// row 3 of an SU(3) matrix from rows 1 and 2: conj(r1 x r2)
+template <class T>
+__device__ __forceinline__ void complete_row3(M3<T>& m) {
+  m.e[2][0] = conj(m.e[0][1] * m.e[1][2] - m.e[0][2] * m.e[1][1]);
+  m.e[2][1] = conj(m.e[0][2] * m.e[1][0] - m.e[0][0] * m.e[1][2]);
+  m.e[2][2] = conj(m.e[0][0] * m.e[1][1] - m.e[0][1] * m.e[1][0]);
+}
+
+// Load a matrix stored as NC complex planes of V elements each (NC = 9: all
+// entries row-major; NC = 6: rows 1-2, row 3 rebuilt).
+template <class T, int NC>
+__device__ __forceinline__ M3<T> load_m3(const cx<T>* __restrict__ base, int64_t V, int64_t s) {
+  M3<T> m;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m.e[c / 3][c % 3] = ldg(base + c * V + s);
+  if (NC == 6) complete_row3(m);
+  return m;
+}
+
+template <class T, int NC>
+__device__ __forceinline__ void store_m3(cx<T>* __restrict__ base, int64_t V, int64_t s, const M3<T>& m) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) base[c * V + s] = m.e[c / 3][c % 3];
+}
+
+// c = a * b for the first ROWS rows of c
+template <class T, int ROWS = 3>
+__device__ __forceinline__ void mm(M3<T>& c, const M3<T>& a, const M3<T>& b) {
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> acc = a.e[i][0] * b.e[0][j];
+      acc = acc + a.e[i][1] * b.e[1][j];
+      acc = acc + a.e[i][2] * b.e[2][j];
+      c.e[i][j] = acc;
+    }
+}
+
+// c = a * b^dagger for the first ROWS rows of c
+template <class T, int ROWS = 3>
+__device__ __forceinline__ void mm_dag(M3<T>& c, const M3<T>& a, const M3<T>& b) {
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> acc = mul_cj(a.e[i][0], b.e[j][0]);
+      acc = acc + mul_cj(a.e[i][1], b.e[j][1]);
+      acc = acc + mul_cj(a.e[i][2], b.e[j][2]);
+      c.e[i][j] = acc;
+    }
+}
+
+// Project onto SU(3): Gram-Schmidt on rows 1 and 2, row 3 = conj(r1 x r2).
+template <class T>
+__device__ __forceinline__ void reunitarize(M3<T>& m) {
+  T n1 = norm2(m.e[0][0]) + norm2(m.e[0][1]) + norm2(m.e[0][2]);
+  T inv1 = rsqrt(n1);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) m.e[0][j] = scale(m.e[0][j], inv1);
+  // <r1, r2> = sum conj(r1_j) r2_j
+  cx<T> ip = mul_cj(m.e[1][0], m.e[0][0]);
+  ip = ip + mul_cj(m.e[1][1], m.e[0][1]);
+  ip = ip + mul_cj(m.e[1][2], m.e[0][2]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) m.e[1][j] = m.e[1][j] - ip * m.e[0][j];
+  T n2 = norm2(m.e[1][0]) + norm2(m.e[1][1]) + norm2(m.e[1][2]);
+  T inv2 = rsqrt(n2);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) m.e[1][j] = scale(m.e[1][j], inv2);
+  complete_row3(m);
+}
+
+// ---------------------------------------------------------------------------
+// lattice geometry, passed by value to every kernel
+// ---------------------------------------------------------------------------
+struct Geom {
+  int L[4];         // Lx, Ly, Lz, Lt
+  int64_t stride[4];  // 1, Lx, Lx*Ly, Lx*Ly*Lz
+  int64_t V;
+};
+
+__device__ __forceinline__ void site_coords(const Geom& g, int64_t s, int c[4]) {
+  int64_t r = s;
+  c[0] = (int)(r % g.L[0]);
+  r /= g.L[0];
+  c[1] = (int)(r % g.L[1]);
+  r /= g.L[1];
+  c[2] = (int)(r % g.L[2]);
+  c[3] = (int)(r / g.L[2]);
+}
+
+// site index of x - mu (periodic)
+__device__ __forceinline__ int64_t site_back(const Geom& g, int64_t s, const int c[4], int mu) {
+  return c[mu] > 0 ? s - g.stride[mu] : s + (int64_t)(g.L[mu] - 1) * g.stride[mu];
+}
+// site index of x + mu (periodic)
+__device__ __forceinline__ int64_t site_fwd(const Geom& g, int64_t s, const int c[4], int mu) {
+  return c[mu] < g.L[mu] - 1 ? s + g.stride[mu] : s - (int64_t)(g.L[mu] - 1) * g.stride[mu];
+}
+
+// ---------------------------------------------------------------------------
+// device-side iteration state
+// ---------------------------------------------------------------------------
+// The final reduction of every iteration writes F and theta here and decides
+// whether the update of that iteration goes ahead.  Every later kernel of the
+// queue reads `done` first and returns at once when it is set, so a host can
+// queue many iterations and still stop exactly at the first theta < tol.
+struct DevState {
+  double F;          // F of the links before the latest update
+  double theta;      // theta of the same links
+  int done;          // 1: no further update is applied
+  int iters;         // updates applied since the last reset
+  int nonfinite;     // F or theta was NaN/Inf
+  int max_iter;      // stop once iters reaches this (fix mode)
+  double tol;        // stop once theta < tol (fix mode; < 0 disables)
+  int hist_cap;
+  int pad_;
+  double* hist;      // theta before update n, n < hist_cap
+};
+
+}  // namespace lgf

@@ -1,0 +1,69 @@
+// Host-side launchers of the liblgf kernels (one translation unit each for
+// the link kernels and the FFT kernels; the C ABI lives in lgf_api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgf_common.cuh"
+
+namespace lgf {
+
+constexpr int kMaxL = 64;       // longest lattice extent the on-chip FFT takes
+constexpr int kMaxStages = 6;   // radix stages per axis (4^3 = 64)
+
+// Mixed-radix factorisation of one axis, radix 4 first, then 2, 3, 5.
+struct AxisPlan {
+  int L;
+  int nst;
+  int radix[kMaxStages];
+};
+
+// Everything the FFT kernels need to know about the lattice.
+struct FftGeom {
+  AxisPlan ax[4];
+  int L[4];
+  int64_t V;
+  double p2max;   // sum_mu max_k 4 sin^2(pi k / L_mu)
+  int Bx;         // consecutive x per z-t CTA
+  int Pxy;        // padded row pitch of an x-y plane in shared memory
+  int Pt;         // padded pitch of one t slice of a z-t tile
+};
+
+bool make_axis_plan(int L, AxisPlan* p);
+
+// byte sizes of the dynamic shared memory each FFT kernel needs
+size_t fft_xy_smem(const FftGeom& fg, int real_bytes);
+size_t fft_zt_smem(const FftGeom& fg, int real_bytes);
+cudaError_t fft_set_smem_limits(int real_bytes, size_t xy, size_t zt);
+
+// prec: 8 = FP64, 4 = FP32; nc: complex entries stored per matrix (9 or 6)
+cudaError_t launch_gradient(int prec, int nc, const void* U, void* D, double2* partial,
+                            const Geom& geo, const DevState* st, cudaStream_t s);
+cudaError_t launch_reduce(const double2* partial, int n, DevState* st, double normF,
+                          double normT, int mode, cudaStream_t s);
+cudaError_t launch_fft_xy(int prec, void* D, const FftGeom& fg, const void* tw, int inverse,
+                          const DevState* st, cudaStream_t s);
+cudaError_t launch_fft_zt(int prec, void* D, const FftGeom& fg, const void* tw,
+                          const double* sin2, const DevState* st, cudaStream_t s);
+cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
+                           const DevState* st, cudaStream_t s);
+cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& geo,
+                          const DevState* st, cudaStream_t s);
+// host [s][mu][3][3] complex128 layout (on the device) <-> SoA storage
+// (nmu matrices per site: 4 for links, 1 for a gauge field)
+cudaError_t launch_aos_to_soa(int prec, int nc, const double* aos, void* U, int64_t V, int nmu, cudaStream_t s);
+cudaError_t launch_soa_to_aos(int prec, int nc, const void* U, double* aos, int64_t V, int nmu, cudaStream_t s);
+// G <- reunitarised g G (storage precision); FP64 reunitarised copy of G
+cudaError_t launch_accumulate(int prec, int nc, void* G, const void* g, int64_t V, const DevState* st,
+                              cudaStream_t s);
+cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, int64_t V, cudaStream_t s);
+// G <- 1 at every site
+cudaError_t launch_set_identity(int prec, int nc, void* G, int64_t V, cudaStream_t s);
+// packed gradient fields [4][V] -> [V][4] complex128 (for probes)
+cudaError_t launch_unpack_fields(int prec, const void* D, double* out, int64_t V, cudaStream_t s);
+
+constexpr int kGradThreads = 256;
+inline int gradient_blocks(int64_t V) { return (int)((V + kGradThreads - 1) / kGradThreads); }
+
+}  // namespace lgf
