@@ -144,7 +144,8 @@ int lgf_fix_split(lgf_handle h, int* fp32_iters, int* fp64_iters);
  * of the last lgf_fix, up to cap entries; *n_out receives the count. */
 int lgf_history(lgf_handle h, double* theta_out, int cap, int* n_out);
 
-/* Text of the last error on h (or of the last failed lgf_create if h is NULL). */
+/* Text of the last error on h; with h NULL, of the last failed lgf_create or
+ * lgf_functional_noalloc on the calling host thread. */
 const char* lgf_last_error(lgf_handle h);
 
 /* Kernel launches this handle has issued since creation (for accounting). */
@@ -174,6 +175,37 @@ int lgf_profile_read(lgf_handle h, double* ms, long long* launches, int n);
 
 /* Short name of a kernel kind ("update", ...), "" if out of range. */
 const char* lgf_kernel_name(int kind);
+
+/* F and theta of links the caller already holds in device memory, computed
+ * without allocating any memory.  The paper has no counterpart: this exists
+ * for callers that may not allocate on the GPU -- a host program that
+ * reserves the device memory for its own pool and forbids the libraries it
+ * loads to call cudaMalloc, or monitoring code that must not change the
+ * memory footprint of the job it observes.
+ *
+ *   links   device pointer, the library's structure-of-arrays storage for
+ *           dtype: NC complex planes of V elements per direction,
+ *           element [(mu*NC + c)*V + s], c = 3i + j, NC = 9 (18-real) or 6
+ *           (12-real: rows 1-2, row 3 rebuilt), complex128 for LGF_F64 /
+ *           LGF_F64_R12, complex64 for LGF_F32 / LGF_F32_R12; s and mu as in
+ *           the host layout.  Read only.
+ *   out     device pointer to 2 doubles: out[0] = F, out[1] = theta.
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream).
+ *
+ * The work is queued on `stream` and the call returns without waiting; out
+ * is valid once the stream has reached it.  The per-block partial sums live
+ * in a fixed array inside the library (256 KiB on every GPU that loads it,
+ * held until the process exits), so V may be at most 4,194,304 sites
+ * (e.g. 32^4 or 48^3 x 12; 64^4 is rejected with LGF_ERR_ARG).  Every call
+ * shares that array: calls that overlap on the GPU race on it and give wrong
+ * results, so order them on one stream or synchronise between them.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  Errors: LGF_ERR_ARG for bad extents,
+ * dtype, size or NULL pointers, LGF_ERR_CUDA for a failed lookup or launch;
+ * the text is in lgf_last_error(NULL). */
+int lgf_functional_noalloc(const void* links, int Lx, int Ly, int Lz, int Lt, int dtype, double* out,
+                           void* stream);
 
 #ifdef __cplusplus
 }

@@ -52,6 +52,7 @@ SIGNATURES = {
     "lgf_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "lgf_profile_read": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "lgf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "lgf_functional_noalloc": (ctypes.c_int, [_P] + [ctypes.c_int] * 5 + [_P, _P]),
 }
 LGF_NUM_KERNELS = 8
 

@@ -50,6 +50,8 @@ struct Engine {
 
 }  // namespace
 
+void lgf::set_global_error(const std::string& msg) { g_last_create_error = msg; }
+
 struct lgf_ctx {
   int L[4] = {0, 0, 0, 0};
   int64_t V = 0;

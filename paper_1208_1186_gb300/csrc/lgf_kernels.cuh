@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "lgf_common.cuh"
 
 namespace lgf {
@@ -62,6 +64,9 @@ cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, i
 cudaError_t launch_set_identity(int prec, int nc, void* G, int64_t V, cudaStream_t s);
 // packed gradient fields [4][V] -> [V][4] complex128 (for probes)
 cudaError_t launch_unpack_fields(int prec, const void* D, double* out, int64_t V, cudaStream_t s);
+
+// text returned by lgf_last_error(NULL) on this host thread
+void set_global_error(const std::string& msg);
 
 constexpr int kGradThreads = 256;
 inline int gradient_blocks(int64_t V) { return (int)((V + kGradThreads - 1) / kGradThreads); }
