@@ -49,7 +49,8 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "32^4-f32"
 KERNEL_SOURCES = {"update": "k_links.cu", "gradient": "k_links.cu", "build_g": "k_links.cu",
-                  "accumulate": "k_links.cu", "fft_xy": "k_fft.cu", "fft_zt": "k_fft.cu"}
+                  "accumulate": "k_links.cu", "fft_xy": "k_fft.cu", "fft_zt": "k_fft.cu",
+                  "fft_axis": "k_fft_axis.cu", "fft_t": "k_fft_axis.cu"}
 
 
 def log(*a):
@@ -60,15 +61,23 @@ def log(*a):
 # algorithmic bytes per site of each kernel (unique HBM bytes a launch must
 # move: neighbour links and neighbour g count once, via the caches)
 # ---------------------------------------------------------------------------
-def bytes_per_site(kernel: str, prec: int, r: int) -> float:
+def bytes_per_site(kernel: str, prec: int, r: int, gauge_rep: bool = False) -> float:
+    if gauge_rep:  # links U0 fixed, gauge G updated: see k_gauge_rep.cu
+        table = {
+            "gradient": 5 * r + 8,   # own U0 links and own G in, packed gradient out
+            "build_g": 8 + 2 * r,    # packed gradient in, G in and out (g never stored)
+        }
+        if kernel in table:
+            return table[kernel] * prec
     table = {
         "gradient": 4 * r + 8,   # own links in, packed gradient out
         "fft_xy": 16,            # 4 complex in, 4 complex out
         "fft_zt": 16,
+        "fft_axis": 16,          # one axis pass: 4 complex in, 4 complex out
+        "fft_t": 17,             # t pass: the same plus the acceleration factor
         "build_g": 8 + r,        # packed gradient in, g out
         "update": 9 * r,         # links in and out, g in
         "accumulate": 3 * r,     # g in, G in and out
-        "reduce": 0,
     }
     return table.get(kernel, 0) * prec
 
@@ -232,6 +241,9 @@ def run_ours(args, W):
     Ud = torch.from_numpy(U).to("cuda")
     stream = torch.cuda.Stream()
     gf = lgf.GaugeFixer(dims, W["dtype"], stream=stream, alpha=W["alpha"])
+    gauge_rep = W["dtype"].startswith("f32") and args.link_update == 0
+    if W["dtype"].startswith("f32"):
+        gf.set_param(6, args.link_update)  # LGF_LINK_UPDATE
     gf.load_links(Ud)
     smi = ClockSampler(gpu_id_for_smi(torch)) if rank == 0 else None
     try:
@@ -302,13 +314,14 @@ def run_ours(args, W):
         if n == 0 or name in ("other",):
             continue
         per_launch_ms = kms / n
-        b = bytes_per_site(name, prec, r) * V
+        b = bytes_per_site(name, prec, r, gauge_rep) * V
         kernels[name] = {"launches": n, "ms_per_launch": round(per_launch_ms, 5),
                          "share": round(kms / sum(v[0] for v in prof.values()), 4),
                          "algorithmic_gbs": round(b / (per_launch_ms * 1e-3) / 1e9, 1) if b else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     ach = kernels[dom]["algorithmic_gbs"]
-    step_bytes = sum(bytes_per_site(k, prec, r) for k in kernels) * V
+    step_bytes = sum(bytes_per_site(k, prec, r, gauge_rep) * kernels[k]["launches"] / args.steps
+                     for k in kernels) * V
     value = world * V * args.steps / (ms_max / 1e3)
     h2d = V * 576
     d2h = V * 576
@@ -326,6 +339,8 @@ def run_ours(args, W):
         "dtype": "f32" if prec == 4 else "f64",
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
         "config": {"workload": W["desc"], "lattice": list(dims), "storage": W["dtype"], "alpha": W["alpha"],
+                   "link_update": ("gauge representation: U0 fixed, G <- g G, links formed on the fly"
+                                   if gauge_rep else "links updated in place"),
                    "link_scale": W["link_scale"], "gauge_scale": W["gauge_scale"], "seed": W["seed"],
                    "l2": f"inputs larger than L2: links {4 * r * prec * V / 1e6:.0f} MB per sweep",
                    "parallelism": f"replicas x{world} (independent configs, no collective on the data path)"},
@@ -409,6 +424,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--link-update", type=int, default=0, choices=[0, 1],
+                    help="FP32 storage: 0 gauge representation (default), 1 links updated in place")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 steps (minimum)")

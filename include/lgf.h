@@ -72,7 +72,17 @@ enum lgf_param {
   LGF_CHECK_EVERY = 1,  /* lgf_fix: iterations queued between host checks (32)  */
   LGF_TAIL_THETA = 2,   /* mixed precision: theta at which the FP32 phase hands
                            over to the FP64 tail (default 1e-11)                */
-  LGF_TAIL_MAX_FP32 = 3 /* mixed precision: cap on FP32 iterations (default: all) */
+  LGF_TAIL_MAX_FP32 = 3, /* mixed precision: cap on FP32 iterations (default: all) */
+  LGF_REUNIT_FP64 = 4,   /* FP32 storage: reunitarise g in FP64 arithmetic (0/1,
+                            default 0: g is stored in FP32, so FP64 arithmetic
+                            would be rounded away on the store)                */
+  LGF_FFT_PLANES = 5,    /* 1: use the x-y / z-t plane FFT kernels even where
+                            the per-axis register passes apply (default 0)     */
+  LGF_LINK_UPDATE = 6    /* FP32 storage, from the next load: 0 (default) keeps
+                            the loaded links and applies each update to the
+                            accumulated gauge transformation G, forming
+                            G U G^dagger on the fly; 1 updates the FP32 links
+                            in place and accumulates G beside them            */
 };
 
 /* Device allocator hooks.  alloc returns a device pointer (NULL on failure);
@@ -153,15 +163,16 @@ long long lgf_launch_count(lgf_handle h);
 
 /* Kernel kinds of one iteration, for lgf_profile_read(). */
 enum lgf_kernel {
-  LGF_K_GRADIENT = 0,   /* gradient Delta + block partials of F, theta     */
-  LGF_K_REDUCE = 1,     /* final FP64 sums and the stop decision            */
+  LGF_K_GRADIENT = 0,   /* gradient Delta, FP64 F/theta sums, stop decision */
+  LGF_K_FFT_AXIS = 1,   /* one-axis FFT pass (x, y or z; fwd or inv)        */
   LGF_K_FFT_XY = 2,     /* x-y plane FFT (forward and inverse)              */
   LGF_K_FFT_ZT = 3,     /* z-t plane FFT, forward + p2_max/p2 + inverse     */
   LGF_K_BUILD_G = 4,    /* g = reunitarised (1 + alpha/2 Delta~)            */
   LGF_K_UPDATE = 5,     /* U_mu(x) <- g(x) U_mu(x) g(x+mu)^dagger          */
   LGF_K_ACCUMULATE = 6, /* mixed precision: G <- g G                        */
   LGF_K_OTHER = 7,      /* layout conversions, copies                       */
-  LGF_NUM_KERNELS = 8
+  LGF_K_FFT_T = 8,      /* t pass: forward t FFT, p2_max/p2, inverse t FFT  */
+  LGF_NUM_KERNELS = 9
 };
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream right

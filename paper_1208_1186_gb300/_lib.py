@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "LGF_OK", -1: "LGF_ERR_ARG", -2: "LGF_ERR_CUDA", -3: "LGF_ERR
                 -4: "LGF_ERR_NOT_CONVERGED", -5: "LGF_ERR_NONFINITE", -6: "LGF_ERR_TIMEOUT"}
 
 LGF_ALPHA, LGF_CHECK_EVERY, LGF_TAIL_THETA, LGF_TAIL_MAX_FP32 = 0, 1, 2, 3
+LGF_REUNIT_FP64, LGF_FFT_PLANES, LGF_LINK_UPDATE = 4, 5, 6
 
 # every symbol include/lgf.h declares: name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -54,7 +55,7 @@ SIGNATURES = {
     "lgf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "lgf_functional_noalloc": (ctypes.c_int, [_P] + [ctypes.c_int] * 5 + [_P, _P]),
 }
-LGF_NUM_KERNELS = 8
+LGF_NUM_KERNELS = 9
 
 _lib = None
 

@@ -1,0 +1,218 @@
+// FP32 engine in gauge representation.
+//
+// Steepest descent only ever moves the links along their gauge orbit: after n
+// iterations U_mu(x) = G(x) U0_mu(x) G(x+mu)^dagger, with U0 the loaded links
+// and G = g_n ... g_1 the accumulated gauge transformation.  This engine
+// keeps U0 fixed and updates G instead of the links: the update of the method,
+// U_mu(x) <- g(x) U_mu(x) g(x+mu)^dagger, becomes G(x) <- g(x) G(x), and the
+// gradient kernel forms the current links on the fly.  Per iteration the link
+// array is read once and never written, which removes the link write-back
+// and the separate update sweep (about 570 instead of 1420 algorithmic bytes
+// per site for 18-real FP32 storage), and the links can never drift off the
+// orbit of the loaded configuration.  The FP64 tail starts from
+// G U0 G^dagger formed in FP64 from the FP64 input.
+//
+//   k_gradient_grep  B = sum_mu G(x-mu) U0_mu(x-mu),  C = sum_mu U0_mu(x) G(x+mu)^dag,
+//                    sum_mu U_mu(x) = G(x) C,  sum_mu U_mu(x-mu) = B G(x)^dag,
+//                    A = B G^dag - G C, then Delta, F, theta as in k_gradient
+//                    (10 SU(3) products per site instead of 16).
+//   k_gstep          g = reunitarised (1 + alpha/2 Delta~), G <- reunitarised g G.
+//   k_materialize    G(x) U0_mu(x) G(x+mu)^dag as host-layout FP64 links.
+#include "lgf_kernels.cuh"
+#include "lgf_reduce.cuh"
+
+namespace lgf {
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ void add_to(M3<T>& acc, const M3<T>& t) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc.e[i][j] = acc.e[i][j] + t.e[i][j];
+}
+
+template <class T, int NC>
+__device__ __forceinline__ M3<T> load_rw(const cx<T>* base, int64_t V, int64_t s) {
+  M3<T> m;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m.e[c / 3][c % 3] = base[c * V + s];
+  if (NC == 6) complete_row3(m);
+  return m;
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(kGradThreads, 2) k_gradient_grep(const cx<T>* __restrict__ U0,
+                                                                const cx<T>* __restrict__ G, cx<T>* __restrict__ D,
+                                                                double2* __restrict__ partial, const Geom geo,
+                                                                DevState* st, int mode, double normF, double normT) {
+  if (mode == 1 && st->done) return;
+  const int64_t V = geo.V;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T fsum = 0, tsum = 0;
+  if (s < V) {
+    int c[4];
+    site_coords(geo, s, c);
+    M3<T> B, C;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) B.e[i][j] = C.e[i][j] = mk<T>(0, 0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const cx<T>* base = U0 + (int64_t)mu * NC * V;
+      M3<T> t;
+      {
+        const M3<T> u = load_m3<T, NC>(base, V, s);
+        const M3<T> gf = load_m3<T, NC>(G, V, site_fwd(geo, s, c, mu));
+        mm_dag<T, 3>(t, u, gf);
+        add_to(C, t);
+      }
+      {
+        const int64_t sb = site_back(geo, s, c, mu);
+        const M3<T> gb = load_m3<T, NC>(G, V, sb);
+        const M3<T> ub = load_m3<T, NC>(base, V, sb);
+        mm<T, 3>(t, gb, ub);
+        add_to(B, t);
+      }
+    }
+    const M3<T> gx = load_m3<T, NC>(G, V, s);
+    M3<T> Uf, Ub;
+    mm<T, 3>(Uf, gx, C);      // sum of the links leaving x
+    mm_dag<T, 3>(Ub, B, gx);  // sum of the links arriving at x
+    fsum = Uf.e[0][0].re + Uf.e[1][1].re + Uf.e[2][2].re;
+    M3<T> A;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) A.e[i][j] = Ub.e[i][j] - Uf.e[i][j];
+    const cx<T> d01 = A.e[0][1] - conj(A.e[1][0]);
+    const cx<T> d02 = A.e[0][2] - conj(A.e[2][0]);
+    const cx<T> d12 = A.e[1][2] - conj(A.e[2][1]);
+    const T a0 = 2 * A.e[0][0].im, a1 = 2 * A.e[1][1].im, a2 = 2 * A.e[2][2].im;
+    const T tr = (a0 + a1 + a2) / (T)3;
+    const T i0 = a0 - tr, i1 = a1 - tr, i2 = -(i0 + i1);
+    D[s] = d01;
+    D[V + s] = d02;
+    D[2 * V + s] = d12;
+    D[3 * V + s] = mk<T>(i0, i1);
+    tsum = 2 * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
+  }
+  grid_reduce<T>(fsum, tsum, partial, st, normF, normT, mode);
+}
+
+// g from the accelerated gradient; G <- g G unless G is null; g stored if
+// g_out is not null.  RT: arithmetic of g, the product and both projections.
+template <class T, int NC, class RT>
+__global__ void __launch_bounds__(256) k_gstep(const cx<T>* __restrict__ D, cx<T>* G, cx<T>* __restrict__ g_out,
+                                               int64_t V, double hd, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const RT h = (RT)hd;
+  const cx<RT> c0 = cvt<RT>(ldg(D + s));
+  const cx<RT> c1 = cvt<RT>(ldg(D + V + s));
+  const cx<RT> c2 = cvt<RT>(ldg(D + 2 * V + s));
+  const cx<RT> c3 = cvt<RT>(ldg(D + 3 * V + s));
+  M3<RT> g;
+  g.e[0][0] = mk<RT>(1, h * c3.re);
+  g.e[0][1] = scale(c0, h);
+  g.e[0][2] = scale(c1, h);
+  g.e[1][0] = mk<RT>(-h * c0.re, h * c0.im);
+  g.e[1][1] = mk<RT>(1, h * c3.im);
+  g.e[1][2] = scale(c2, h);
+  reunitarize(g);
+  if (g_out != nullptr) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) g_out[c * V + s] = cvt<T>(g.e[c / 3][c % 3]);
+  }
+  if (G == nullptr) return;
+  const M3<T> Gt = load_rw<T, NC>(G, V, s);
+  M3<RT> Gx, r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Gx.e[i][j] = cvt<RT>(Gt.e[i][j]);
+  mm<RT, 2>(r, g, Gx);
+  reunitarize(r);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) G[c * V + s] = cvt<T>(r.e[c / 3][c % 3]);
+}
+
+// one thread per (site, mu): the current link in the host layout
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_materialize(const cx<T>* __restrict__ U0, const cx<T>* __restrict__ G,
+                                                     double* __restrict__ aos, const Geom geo) {
+  const int64_t V = geo.V;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * V) return;
+  const int64_t s = i >> 2;
+  const int mu = (int)(i & 3);
+  int c[4];
+  site_coords(geo, s, c);
+  const M3<T> u = load_m3<T, NC>(U0 + (int64_t)mu * NC * V, V, s);
+  const M3<T> gx = load_m3<T, NC>(G, V, s);
+  const M3<T> gf = load_m3<T, NC>(G, V, site_fwd(geo, s, c, mu));
+  M3<T> w, r;
+  mm<T, 3>(w, gx, u);
+  mm_dag<T, 3>(r, w, gf);
+  double* dst = aos + i * 18;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    dst[2 * q] = (double)r.e[q / 3][q % 3].re;
+    dst[2 * q + 1] = (double)r.e[q / 3][q % 3].im;
+  }
+}
+
+inline unsigned nblocks(int64_t n, int thr) { return (unsigned)((n + thr - 1) / thr); }
+
+}  // namespace
+
+cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D, double2* partial, const Geom& geo,
+                                 DevState* st, int mode, cudaStream_t s) {
+  const unsigned nb = (unsigned)gradient_blocks(geo.V);
+  const double nF = 1.0 / (12.0 * (double)geo.V), nT = 1.0 / (3.0 * (double)geo.V);
+  if (nc == 9)
+    k_gradient_grep<float, 9><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
+                                                          static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
+                                                          partial, geo, st, mode, nF, nT);
+  else
+    k_gradient_grep<float, 6><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
+                                                          static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
+                                                          partial, geo, st, mode, nF, nT);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,
+                         const DevState* st, cudaStream_t s) {
+  const auto Dp = static_cast<const cx<float>*>(D);
+  const auto Gp = static_cast<cx<float>*>(G);
+  const auto gp = static_cast<cx<float>*>(g_out);
+  const unsigned nb = nblocks(V, 256);
+  if (nc == 9) {
+    if (reunit_fp64)
+      k_gstep<float, 9, double><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+    else
+      k_gstep<float, 9, float><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+  } else {
+    if (reunit_fp64)
+      k_gstep<float, 6, double><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+    else
+      k_gstep<float, 6, float><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+  }
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s) {
+  const unsigned nb = nblocks(4 * geo.V, 256);
+  if (nc == 9)
+    k_materialize<float, 9><<<nb, 256, 0, s>>>(static_cast<const cx<float>*>(U0), static_cast<const cx<float>*>(G),
+                                                aos, geo);
+  else
+    k_materialize<float, 6><<<nb, 256, 0, s>>>(static_cast<const cx<float>*>(U0), static_cast<const cx<float>*>(G),
+                                                aos, geo);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace lgf

@@ -6,43 +6,19 @@
 //               (Delta01, Delta02, Delta12, Im Delta00 + i Im Delta11); block
 //               partial sums of Re Tr U and Tr Delta Delta^dag in FP64 with
 //               warp shuffles.
-//   k_reduce    fixed-order FP64 sum of the block partials -> F, theta, and
-//               the stop decision of the iteration queue.
+//               The last block to finish sums the partials in fixed order ->
+//               F, theta, and the stop decision of the iteration queue.
 //   k_build_g   g(x) = reunitarised (1 + alpha/2 Delta~(x)), FP64 arithmetic.
 //   k_update    U_mu(x) <- g(x) U_mu(x) g(x+mu)^dag.
 //
 // Links of direction mu occupy NC complex planes of V elements:
 // U[(mu*NC + c)*V + s]; NC = 9 stores every entry, NC = 6 rows 1-2 only.
 #include "lgf_kernels.cuh"
+#include "lgf_reduce.cuh"
 
 namespace lgf {
 
 namespace {
-
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[32], sb[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    sa[w] = a;
-    sb[w] = b;
-  }
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  if (w == 0) {
-    a = l < nw ? sa[l] : 0.0;
-    b = l < nw ? sb[l] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-  }
-}
 
 template <class T, int NC>
 __device__ __forceinline__ M3<T> load_m3_rw(const cx<T>* base, int64_t V, int64_t s) {
@@ -53,14 +29,19 @@ __device__ __forceinline__ M3<T> load_m3_rw(const cx<T>* base, int64_t V, int64_
   return m;
 }
 
+// Gradient of every site, stored packed, and the reduction of F and theta
+// (grid_reduce: per-site and per-warp sums in T, FP64 above; the last block
+// to arrive adds the block sums in index order, writes F and theta and, in
+// mode 1, decides whether this iteration's update is applied).  mode 1
+// launches return at once once a previous iteration has stopped the queue.
 template <class T, int NC>
 __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restrict__ U, cx<T>* __restrict__ D,
                                                            double2* __restrict__ partial, const Geom geo,
-                                                           const DevState* __restrict__ st) {
-  if (st != nullptr && st->done) return;
+                                                           DevState* st, int mode, double normF, double normT) {
+  if (mode == 1 && st->done) return;
   const int64_t V = geo.V;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double fsum = 0.0, tsum = 0.0;
+  T fsum = 0, tsum = 0;
   if (s < V) {
     int c[4];
     site_coords(geo, s, c);
@@ -74,7 +55,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restri
       const cx<T>* base = U + (int64_t)mu * NC * V;
       const M3<T> own = load_m3<T, NC>(base, V, s);
       const M3<T> back = load_m3<T, NC>(base, V, site_back(geo, s, c, mu));
-      fsum += (double)own.e[0][0].re + (double)own.e[1][1].re + (double)own.e[2][2].re;
+      fsum += own.e[0][0].re + own.e[1][1].re + own.e[2][2].re;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -85,64 +66,34 @@ __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restri
     const cx<T> d12 = A.e[1][2] - conj(A.e[2][1]);
     const T a0 = 2 * A.e[0][0].im, a1 = 2 * A.e[1][1].im, a2 = 2 * A.e[2][2].im;
     const T tr = (a0 + a1 + a2) / (T)3;
-    const T i0 = a0 - tr, i1 = a1 - tr;
+    const T i0 = a0 - tr, i1 = a1 - tr, i2 = -(i0 + i1);
     D[s] = d01;
     D[V + s] = d02;
     D[2 * V + s] = d12;
     D[3 * V + s] = mk<T>(i0, i1);
-    const double di0 = i0, di1 = i1, di2 = -(di0 + di1);
-    tsum = 2.0 * ((double)norm2(cvt<double>(d01)) + (double)norm2(cvt<double>(d02)) +
-                  (double)norm2(cvt<double>(d12))) +
-           di0 * di0 + di1 * di1 + di2 * di2;
+    tsum = 2 * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
   }
-  block_sum2(fsum, tsum);
-  if (threadIdx.x == 0) partial[blockIdx.x] = make_double2(fsum, tsum);
+  grid_reduce<T>(fsum, tsum, partial, st, normF, normT, mode);
 }
 
-// mode 0: F and theta only.  mode 1: also the iteration decision (history,
-// stop at theta < tol or at max_iter updates, count the update otherwise).
-__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, int n, DevState* st,
-                                                 double normF, double normT, int mode) {
-  if (mode == 1 && st->done) return;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double2 p = partial[i];
-    a += p.x;
-    b += p.y;
-  }
-  block_sum2(a, b);
-  if (threadIdx.x != 0) return;
-  const double F = a * normF, th = b * normT;
-  st->F = F;
-  st->theta = th;
-  const bool bad = !isfinite(F) || !isfinite(th);
-  if (bad) st->nonfinite = 1;
-  if (mode != 1) return;
-  if (st->hist != nullptr && st->iters < st->hist_cap) st->hist[st->iters] = th;
-  if (bad || (st->tol >= 0.0 && th < st->tol) || st->iters >= st->max_iter) {
-    st->done = 1;
-  } else {
-    st->iters += 1;
-  }
-}
-
-template <class T, int NC>
+template <class T, int NC, class RT>
 __global__ void __launch_bounds__(256) k_build_g(const cx<T>* __restrict__ D, cx<T>* __restrict__ g, int64_t V,
-                                                 double h, const DevState* __restrict__ st) {
+                                                 double hd, const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const cx<double> c0 = cvt<double>(ldg(D + s));
-  const cx<double> c1 = cvt<double>(ldg(D + V + s));
-  const cx<double> c2 = cvt<double>(ldg(D + 2 * V + s));
-  const cx<double> c3 = cvt<double>(ldg(D + 3 * V + s));
+  const RT h = (RT)hd;
+  const cx<RT> c0 = cvt<RT>(ldg(D + s));
+  const cx<RT> c1 = cvt<RT>(ldg(D + V + s));
+  const cx<RT> c2 = cvt<RT>(ldg(D + 2 * V + s));
+  const cx<RT> c3 = cvt<RT>(ldg(D + 3 * V + s));
   // rows 1-2 of 1 + h Delta~; Delta~10 = -conj(Delta~01), Delta~_ii = i Im
-  M3<double> m;
-  m.e[0][0] = mk<double>(1.0, h * c3.re);
+  M3<RT> m;
+  m.e[0][0] = mk<RT>(1, h * c3.re);
   m.e[0][1] = scale(c0, h);
   m.e[0][2] = scale(c1, h);
-  m.e[1][0] = mk<double>(-h * c0.re, h * c0.im);
-  m.e[1][1] = mk<double>(1.0, h * c3.im);
+  m.e[1][0] = mk<RT>(-h * c0.re, h * c0.im);
+  m.e[1][1] = mk<RT>(1, h * c3.im);
   m.e[1][2] = scale(c2, h);
   reunitarize(m);
 #pragma unroll
@@ -160,7 +111,7 @@ __global__ void __launch_bounds__(256) k_update(cx<T>* U, const cx<T>* __restric
   site_coords(geo, s, c);
   const M3<T> gx = load_m3<T, NC>(g, V, s);
   constexpr int ROWS = NC / 3;
-#pragma unroll 1
+#pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
     cx<T>* base = U + (int64_t)mu * NC * V;
     const M3<T> u = load_m3_rw<T, NC>(base, V, s);
@@ -279,25 +230,29 @@ inline unsigned blocks_for(int64_t n, int thr) { return (unsigned)((n + thr - 1)
   } while (0)
 
 cudaError_t launch_gradient(int prec, int nc, const void* U, void* D, double2* partial, const Geom& geo,
-                            const DevState* st, cudaStream_t s) {
+                            DevState* st, int mode, cudaStream_t s) {
   const unsigned nb = (unsigned)gradient_blocks(geo.V);
+  const double nF = 1.0 / (12.0 * (double)geo.V), nT = 1.0 / (3.0 * (double)geo.V);
   LGF_DISPATCH(prec, nc,
-               (k_gradient<T, NC><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<T>*>(U),
-                                                              static_cast<cx<T>*>(D), partial, geo, st)));
-  return cudaPeekAtLastError();
-}
-
-cudaError_t launch_reduce(const double2* partial, int n, DevState* st, double normF, double normT, int mode,
-                          cudaStream_t s) {
-  k_reduce<<<1, 1024, 0, s>>>(partial, n, st, normF, normT, mode);
+               (k_gradient<T, NC><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<T>*>(U), static_cast<cx<T>*>(D),
+                                                              partial, geo, st, mode, nF, nT)));
   return cudaPeekAtLastError();
 }
 
 cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
-                           const DevState* st, cudaStream_t s) {
+                           bool reunit_fp64, const DevState* st, cudaStream_t s) {
+  if (prec == 4 && !reunit_fp64) {
+    if (nc == 9)
+      k_build_g<float, 9, float><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<float>*>(D),
+                                                                   static_cast<cx<float>*>(g), V, half_alpha, st);
+    else
+      k_build_g<float, 6, float><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<float>*>(D),
+                                                                   static_cast<cx<float>*>(g), V, half_alpha, st);
+    return cudaPeekAtLastError();
+  }
   LGF_DISPATCH(prec, nc,
-               (k_build_g<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<T>*>(D),
-                                                                    static_cast<cx<T>*>(g), V, half_alpha, st)));
+               (k_build_g<T, NC, double><<<blocks_for(V, 256), 256, 0, s>>>(
+                   static_cast<const cx<T>*>(D), static_cast<cx<T>*>(g), V, half_alpha, st)));
   return cudaPeekAtLastError();
 }
 

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/lgf.h"
+#include "fft_reg.cuh"
 #include "lgf_kernels.cuh"
 
 using namespace lgf;
@@ -44,7 +45,10 @@ struct Engine {
   void* D = nullptr;
   void* g = nullptr;
   void* tw = nullptr;
-  FftGeom fg{};  // FFT tiling for this precision
+  FftGeom fg{};  // FFT tiling for this precision (plane pipeline)
+  bool axis = false;     // per-axis register FFT pipeline (else plane pipeline)
+  bool grep = false;     // FP32 engine: gauge representation (U holds the loaded links, G is updated)
+  void* kfac = nullptr;  // axis pipeline: p2_max/(V p2(k)) per site, digit-reversed order
   size_t cbytes() const { return 2 * (size_t)prec; }
 };
 
@@ -63,6 +67,9 @@ struct lgf_ctx {
   int check_every = 32;
   double tail_theta = 1e-11;
   long long tail_max32 = -1;
+  bool reunit_fp64 = false;   // FP32 storage: reunitarise g in FP64 arithmetic
+  bool force_planes = false;  // use the plane FFT pipeline even where the axis one applies
+  bool explicit_fp32 = false; // FP32 engine: update the links in place instead of G (from the next load)
 
   Geom geo{};
   Engine e64, e32;
@@ -193,6 +200,44 @@ int alloc_engine(lgf_handle h, Engine& e) {
     LGF_CUDA(h, cudaMemcpy(e.tw, tw64.data(), tw64.size() * sizeof(double), cudaMemcpyHostToDevice));
   else
     LGF_CUDA(h, cudaMemcpy(e.tw, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  e.axis = true;
+  for (int a = 0; a < 4; ++a) e.axis = e.axis && axis_pass_supported(e.prec, h->L[a]);
+  if (e.axis) {
+    // acceleration factor at every position the forward passes leave a mode:
+    // position p along an axis holds frequency digit_rev(L, p)
+    e.kfac = dev_alloc(h, (size_t)V * e.prec);
+    if (!e.kfac) return fail(h, LGF_ERR_OOM, "device allocation failed");
+    std::vector<double> s2[4];
+    double p2max = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      const int L = h->L[a];
+      s2[a].resize(L);
+      double m = 0.0;
+      for (int p = 0; p < L; ++p) {
+        const long double sk =
+            sinl(3.14159265358979323846264338327950288L * (long double)regfft::digit_rev(L, p) / (long double)L);
+        s2[a][p] = (double)(4.0L * sk * sk);
+        m = s2[a][p] > m ? s2[a][p] : m;
+      }
+      p2max += m;
+    }
+    std::vector<double> k64;
+    std::vector<float> k32;
+    if (e.prec == 8) k64.resize(V); else k32.resize(V);
+    int64_t s = 0;
+    for (int t = 0; t < h->L[3]; ++t)
+      for (int z = 0; z < h->L[2]; ++z)
+        for (int y = 0; y < h->L[1]; ++y)
+          for (int x = 0; x < h->L[0]; ++x, ++s) {
+            double f = 0.0;
+            if (x | y | z | t) f = p2max / ((s2[0][x] + s2[1][y] + s2[2][z] + s2[3][t]) * (double)V);
+            if (e.prec == 8) k64[s] = f; else k32[s] = (float)f;
+          }
+    if (e.prec == 8)
+      LGF_CUDA(h, cudaMemcpy(e.kfac, k64.data(), (size_t)V * 8, cudaMemcpyHostToDevice));
+    else
+      LGF_CUDA(h, cudaMemcpy(e.kfac, k32.data(), (size_t)V * 4, cudaMemcpyHostToDevice));
+  }
   return LGF_OK;
 }
 
@@ -227,31 +272,60 @@ int reset_state(lgf_handle h, double tol, int max_iter, bool with_hist) {
   return LGF_OK;
 }
 
-// Steps a1-a6 of one iteration (gradient through g) on engine e.  st may be
-// null (no stop logic).
-int queue_to_gauge(lgf_handle h, Engine& e, const DevState* st, int reduce_mode) {
+// Fourier acceleration of the packed gradient in e.D (forward 4D FFT, times
+// p2_max/(V p2), inverse), with either pipeline.
+int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
   cudaStream_t s = h->stream;
-  LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, st, s));
-  LGF_LAUNCH(h, LGF_K_REDUCE,
-             launch_reduce(h->partial, h->nblk, h->st, 1.0 / (12.0 * (double)h->V), 1.0 / (3.0 * (double)h->V),
-                           reduce_mode, s));
-  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 0, st, s));
-  LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_fft_zt(e.prec, e.D, e.fg, e.tw, h->sin2, st, s));
-  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 1, st, s));
-  LGF_LAUNCH(h, LGF_K_BUILD_G, launch_build_g(e.prec, e.nc, e.D, e.g, h->V, 0.5 * h->alpha, st, s));
+  if (e.axis && !h->force_planes) {
+    const int64_t V = h->V;
+    const int64_t Sy = h->L[0], Sz = (int64_t)h->L[0] * h->L[1];
+    const char* tw = static_cast<const char*>(e.tw);
+    const size_t tws = (size_t)kMaxL * e.cbytes();
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, tw, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, tw + tws, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, tw + 2 * tws, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_T, launch_tpass(e.prec, h->L[3], e.D, V, e.kfac, tw + 3 * tws, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, tw + 2 * tws, 1, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, tw + tws, 1, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, tw, 1, st, s));
+  } else {
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_fft_zt(e.prec, e.D, e.fg, e.tw, h->sin2, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 1, st, s));
+  }
   return LGF_OK;
 }
 
-// One full iteration.  On the FP32 engine of a mixed handle the gauge
-// transformation accumulated since the last load is kept up to date, so that
-// the FP32 links always equal G U_loaded G^dagger up to FP32 rounding.
+// Gradient (+ F/theta reduction) of the engine's current links.
+int queue_gradient(lgf_handle h, Engine& e, int mode) {
+  if (e.grep)
+    LGF_LAUNCH(h, LGF_K_GRADIENT,
+               launch_gradient_grep(e.nc, e.U, h->G, e.D, h->partial, h->geo, h->st, mode, h->stream));
+  else
+    LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, h->st, mode, h->stream));
+  return LGF_OK;
+}
+
+// One full iteration on engine e, with the stop logic of an iteration queue.
+// Gauge representation: gradient, acceleration, G <- g G.  Otherwise:
+// gradient, acceleration, g, link update, and on the FP32 engine of a mixed
+// handle G <- g G as well, so that the FP32 links always equal
+// G U_loaded G^dagger up to FP32 rounding.
 int queue_iteration(lgf_handle h, Engine& e) {
-  const bool track_gauge = h->mixed && &e == &h->e32;
-  int rc = queue_to_gauge(h, e, h->st, 1);
+  cudaStream_t s = h->stream;
+  int rc = queue_gradient(h, e, 1);
+  if (!rc) rc = queue_accelerate(h, e, h->st);
   if (rc) return rc;
-  LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(e.prec, e.nc, e.U, e.g, h->geo, h->st, h->stream));
-  if (track_gauge)
-    LGF_LAUNCH(h, LGF_K_ACCUMULATE, launch_accumulate(e.prec, e.nc, h->G, e.g, h->V, h->st, h->stream));
+  if (e.grep) {
+    LGF_LAUNCH(h, LGF_K_BUILD_G,
+               launch_gstep(e.nc, e.D, h->G, nullptr, h->V, 0.5 * h->alpha, h->reunit_fp64, h->st, s));
+    return LGF_OK;
+  }
+  LGF_LAUNCH(h, LGF_K_BUILD_G,
+             launch_build_g(e.prec, e.nc, e.D, e.g, h->V, 0.5 * h->alpha, h->reunit_fp64, h->st, s));
+  LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(e.prec, e.nc, e.U, e.g, h->geo, h->st, s));
+  if (h->mixed && &e == &h->e32)
+    LGF_LAUNCH(h, LGF_K_ACCUMULATE, launch_accumulate(e.prec, e.nc, h->G, e.g, h->V, h->st, s));
   return LGF_OK;
 }
 
@@ -393,6 +467,7 @@ int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out) {
   // the opt-in limit is process-wide per kernel: always raise it to the device maximum
   cudaError_t e = fft_set_smem_limits(8, smem_optin, smem_optin);
   if (e == cudaSuccess) e = fft_set_smem_limits(4, smem_optin, smem_optin);
+  if (e == cudaSuccess) e = axis_pass_init();
   if (e != cudaSuccess) {
     cuda_fail(h, e, "cudaFuncSetAttribute");
     return bail(LGF_ERR_CUDA);
@@ -478,6 +553,15 @@ int lgf_set_param(lgf_handle h, int key, double value) {
     case LGF_TAIL_MAX_FP32:
       h->tail_max32 = (long long)value;
       return LGF_OK;
+    case LGF_REUNIT_FP64:
+      h->reunit_fp64 = value != 0.0;
+      return LGF_OK;
+    case LGF_FFT_PLANES:
+      h->force_planes = value != 0.0;
+      return LGF_OK;
+    case LGF_LINK_UPDATE:
+      h->explicit_fp32 = value != 0.0;
+      return LGF_OK;
     default:
       return fail(h, LGF_ERR_ARG, "unknown parameter key");
   }
@@ -489,6 +573,7 @@ static int load_from_device_aos(lgf_handle h, const double* aos) {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, 9, aos, h->Uorig, V, 4, h->stream));
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(4, h->e32.nc, aos, h->e32.U, V, 4, h->stream));
     LGF_LAUNCH(h, LGF_K_OTHER, launch_set_identity(4, h->e32.nc, h->G, V, h->stream));
+    h->e32.grep = !h->explicit_fp32;
     h->cur = &h->e32;
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
@@ -519,7 +604,10 @@ int lgf_store_links(lgf_handle h, double* host_aos) {
   int rc = ensure_staging(h);
   if (rc) return rc;
   Engine& e = *h->cur;
-  LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(e.prec, e.nc, e.U, h->staging, h->V, 4, h->stream));
+  if (e.grep)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, h->staging, h->geo, h->stream));
+  else
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(e.prec, e.nc, e.U, h->staging, h->V, 4, h->stream));
   LGF_CUDA(h, cudaMemcpyAsync(host_aos, h->staging, (size_t)h->V * 72 * sizeof(double), cudaMemcpyDeviceToHost,
                               h->stream));
   LGF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -586,11 +674,8 @@ int lgf_functional(lgf_handle h, double* F, double* theta) {
   if (!h) return LGF_ERR_ARG;
   if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
   Engine& e = *h->cur;
-  LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, nullptr, h->stream));
-  LGF_LAUNCH(h, LGF_K_REDUCE,
-             launch_reduce(h->partial, h->nblk, h->st, 1.0 / (12.0 * (double)h->V), 1.0 / (3.0 * (double)h->V), 0,
-                           h->stream));
-  int rc = sync_state(h);
+  int rc = queue_gradient(h, e, 0);
+  if (!rc) rc = sync_state(h);
   if (rc) return rc;
   if (F) *F = h->st_host->F;
   if (theta) *theta = h->st_host->theta;
@@ -606,18 +691,20 @@ int lgf_probe(lgf_handle h, double* delta_packed, double* delta_tilde_packed, do
   Engine& e = *h->cur;
   const int64_t V = h->V;
   cudaStream_t s = h->stream;
-  LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient(e.prec, e.nc, e.U, e.D, h->partial, h->geo, nullptr, s));
-  LGF_LAUNCH(h, LGF_K_REDUCE,
-             launch_reduce(h->partial, h->nblk, h->st, 1.0 / (12.0 * (double)V), 1.0 / (3.0 * (double)V), 0, s));
+  rc = queue_gradient(h, e, 0);
+  if (rc) return rc;
   if (delta_packed) {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_unpack_fields(e.prec, e.D, h->staging, V, s));
     LGF_CUDA(h, cudaMemcpyAsync(delta_packed, h->staging, (size_t)V * 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     LGF_CUDA(h, cudaStreamSynchronize(s));
   }
-  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 0, nullptr, s));
-  LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_fft_zt(e.prec, e.D, e.fg, e.tw, h->sin2, nullptr, s));
-  LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 1, nullptr, s));
-  LGF_LAUNCH(h, LGF_K_BUILD_G, launch_build_g(e.prec, e.nc, e.D, e.g, V, 0.5 * h->alpha, nullptr, s));
+  rc = queue_accelerate(h, e, nullptr);
+  if (rc) return rc;
+  if (e.grep)  // g only: G is left alone
+    LGF_LAUNCH(h, LGF_K_BUILD_G, launch_gstep(e.nc, e.D, nullptr, e.g, V, 0.5 * h->alpha, h->reunit_fp64, nullptr, s));
+  else
+    LGF_LAUNCH(h, LGF_K_BUILD_G,
+               launch_build_g(e.prec, e.nc, e.D, e.g, V, 0.5 * h->alpha, h->reunit_fp64, nullptr, s));
   if (delta_tilde_packed) {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_unpack_fields(e.prec, e.D, h->staging, V, s));
     LGF_CUDA(h, cudaMemcpyAsync(delta_tilde_packed, h->staging, (size_t)V * 8 * sizeof(double),
@@ -679,8 +766,8 @@ int lgf_profile_read(lgf_handle h, double* ms, long long* launches, int n) {
 }
 
 const char* lgf_kernel_name(int kind) {
-  static const char* names[LGF_NUM_KERNELS] = {"gradient", "reduce", "fft_xy", "fft_zt",
-                                               "build_g",  "update", "accumulate", "other"};
+  static const char* names[LGF_NUM_KERNELS] = {"gradient", "fft_axis", "fft_xy", "fft_zt", "build_g",
+                                               "update",   "accumulate", "other", "fft_t"};
   return (kind >= 0 && kind < LGF_NUM_KERNELS) ? names[kind] : "";
 }
 

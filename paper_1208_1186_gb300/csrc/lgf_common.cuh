@@ -185,7 +185,7 @@ struct DevState {
   int max_iter;      // stop once iters reaches this (fix mode)
   double tol;        // stop once theta < tol (fix mode; < 0 disables)
   int hist_cap;
-  int pad_;
+  unsigned int arrive;  // blocks of the current gradient launch that are done
   double* hist;      // theta before update n, n < hist_cap
 };
 

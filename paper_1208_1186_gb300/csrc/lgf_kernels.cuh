@@ -40,16 +40,16 @@ size_t fft_zt_smem(const FftGeom& fg, int real_bytes);
 cudaError_t fft_set_smem_limits(int real_bytes, size_t xy, size_t zt);
 
 // prec: 8 = FP64, 4 = FP32; nc: complex entries stored per matrix (9 or 6)
+// gradient + FP64 F/theta reduction (its last block finishes it); mode 0: F
+// and theta only, mode 1: also the stop decision of an iteration queue
 cudaError_t launch_gradient(int prec, int nc, const void* U, void* D, double2* partial,
-                            const Geom& geo, const DevState* st, cudaStream_t s);
-cudaError_t launch_reduce(const double2* partial, int n, DevState* st, double normF,
-                          double normT, int mode, cudaStream_t s);
+                            const Geom& geo, DevState* st, int mode, cudaStream_t s);
 cudaError_t launch_fft_xy(int prec, void* D, const FftGeom& fg, const void* tw, int inverse,
                           const DevState* st, cudaStream_t s);
 cudaError_t launch_fft_zt(int prec, void* D, const FftGeom& fg, const void* tw,
                           const double* sin2, const DevState* st, cudaStream_t s);
 cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
-                           const DevState* st, cudaStream_t s);
+                           bool reunit_fp64, const DevState* st, cudaStream_t s);
 cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& geo,
                           const DevState* st, cudaStream_t s);
 // host [s][mu][3][3] complex128 layout (on the device) <-> SoA storage
@@ -64,6 +64,25 @@ cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, i
 cudaError_t launch_set_identity(int prec, int nc, void* G, int64_t V, cudaStream_t s);
 // packed gradient fields [4][V] -> [V][4] complex128 (for probes)
 cudaError_t launch_unpack_fields(int prec, const void* D, double* out, int64_t V, cudaStream_t s);
+
+// per-axis register FFT passes (k_fft_axis.cu); lengths 4..32 (FP64) and up
+// to 64 (FP32) with radices 4, 2, 3, 5
+bool axis_pass_supported(int prec, int L);
+cudaError_t axis_pass_init();
+cudaError_t launch_xpass(int prec, int L, void* D, int64_t V, const void* tw, int inverse, const DevState* st,
+                         cudaStream_t s);
+cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const void* tw, int inverse,
+                           const DevState* st, cudaStream_t s);
+cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, const void* kfac, const void* tw, const DevState* st,
+                         cudaStream_t s);
+
+// FP32 engine in gauge representation (k_gauge_rep.cu): links formed on the
+// fly as G U0 G^dagger; the update acts on G
+cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D, double2* partial, const Geom& geo,
+                                 DevState* st, int mode, cudaStream_t s);
+cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,
+                         const DevState* st, cudaStream_t s);
+cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s);
 
 // text returned by lgf_last_error(NULL) on this host thread
 void set_global_error(const std::string& msg);

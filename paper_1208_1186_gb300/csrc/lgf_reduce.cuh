@@ -1,0 +1,96 @@
+// Block and grid reductions of (Re Tr U, Tr Delta Delta^dagger) and the stop
+// decision of an iteration queue, shared by the gradient kernels.
+//
+// Per-site terms and the sum over a warp are taken in the storage precision T;
+// everything above the warp (warps of a block, blocks of the grid) is summed
+// in FP64, in a fixed order, so that the result does not depend on which
+// block finishes last.  (With T = double every stage is FP64.)  On GB300 the
+// FP64 pipe runs at about 1/60 of the FP32 rate, so keeping the per-site and
+// per-warp stages in FP32 for FP32 storage is what keeps the gradient kernel
+// memory-bound.
+#pragma once
+
+#include "lgf_common.cuh"
+
+namespace lgf {
+
+// Sum (a, b) over the block; the result is valid in thread 0.
+template <class T>
+__device__ __forceinline__ void block_sum_mixed(T a, T b, double& ra, double& rb) {
+  __shared__ double sa[32], sb[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = (double)a;
+    sb[w] = (double)b;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double x = 0.0, y = 0.0;
+  if (w == 0) {
+    x = l < nw ? sa[l] : 0.0;
+    y = l < nw ? sb[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+  }
+  ra = x;
+  rb = y;
+}
+
+// F, theta and the stop decision from the grid sums (one thread).
+__device__ __forceinline__ void finish_reduction(DevState* st, double fs, double ts, double normF, double normT,
+                                                 int mode) {
+  const double F = fs * normF, th = ts * normT;
+  st->F = F;
+  st->theta = th;
+  const bool bad = !isfinite(F) || !isfinite(th);
+  if (bad) st->nonfinite = 1;
+  if (mode != 1) return;
+  if (st->hist != nullptr && st->iters < st->hist_cap) st->hist[st->iters] = th;
+  if (bad || (st->tol >= 0.0 && th < st->tol) || st->iters >= st->max_iter) {
+    st->done = 1;
+  } else {
+    st->iters += 1;
+  }
+}
+
+// Block partials -> grid result: every block stores its pair; the last block
+// to arrive adds all pairs in index order and finishes the reduction.
+// Must be called by every thread of every block.
+template <class T>
+__device__ __forceinline__ void grid_reduce(T fs, T ts, double2* __restrict__ partial, DevState* st, double normF,
+                                            double normT, int mode) {
+  double a, b;
+  block_sum_mixed<T>(fs, ts, a, b);
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = make_double2(a, b);
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->arrive, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    const double2 p = __ldcg(partial + i);
+    x += p.x;
+    y += p.y;
+  }
+  __syncthreads();  // the shared scratch of block_sum_mixed is reused
+  block_sum_mixed<double>(x, y, a, b);
+  if (threadIdx.x == 0) {
+    st->arrive = 0;
+    finish_reduction(st, a, b, normF, normT, mode);
+  }
+}
+
+}  // namespace lgf

@@ -9,6 +9,8 @@ contracts towards its fixed point, so rounding differences do not grow).  The
 FP32 storage path is compared through its FP64-tail result: the final F to
 1e-12 relative, theta < 1e-15.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -19,9 +21,13 @@ pytestmark = pytest.mark.gpu
 
 ALPHA = 0.08
 
+# Lattices whose every extent is in {4, 6, 8, 12, 16, 20, 24, 32} run the
+# per-axis register FFT passes; the others run the x-y / z-t plane kernels.
 STEP_DIMS = [
-    (8, 8, 8, 8),      # C1 shape
-    (4, 6, 10, 12),    # radices 2, 3, 5; V = 2880, ragged last block
+    (8, 8, 8, 8),      # C1 shape (axis passes)
+    (6, 12, 4, 20),    # axis passes, radices 2, 3, 4, 5; V = 5760
+    (20, 8, 24, 6),    # axis passes, V = 23040
+    (4, 6, 10, 12),    # plane kernels (10); V = 2880, ragged last block
     (12, 2, 20, 3),    # odd t extent
     (5, 4, 3, 2),      # odd x extent (one x per z-t tile)
     (64, 2, 2, 2),     # longest x
@@ -45,12 +51,20 @@ def _packed(D):
     return O.pack_delta(D)
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_fix(dims, seed, link_scale, tol):
+    U = I.synthetic_config(dims, seed=seed, link_scale=link_scale)
+    return U, O.fix(U, tol, 2000, ALPHA)
+
+
+@pytest.mark.parametrize("planes", [0, 1])
 @pytest.mark.parametrize("dtype", ["f64", "f64_r12"])
 @pytest.mark.parametrize("dims", STEP_DIMS)
-def test_one_step_matches_oracle(lgf, dims, dtype):
+def test_one_step_matches_oracle(lgf, dims, dtype, planes):
     U = I.synthetic_config(dims, seed=3, link_scale=0.5)
     ref = O.step_parts(U, ALPHA)
     with lgf.GaugeFixer(dims, dtype) as gf:
+        gf.set_param(5, planes)  # LGF_FFT_PLANES
         gf.load_links(U)
         out = gf.probe()
         F, th = gf.functional()
@@ -106,13 +120,16 @@ def test_fix_matches_oracle_c1(lgf):
     assert np.max(np.abs(out - ref["U"])) <= 1e-10
 
 
+@pytest.mark.parametrize("link_update", [0, 1])
+@pytest.mark.parametrize("reunit_fp64", [0, 1])
 @pytest.mark.parametrize("dtype", ["f32", "f32_r12"])
-@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (4, 6, 10, 12)])
-def test_mixed_precision_fix_matches_fp64_functional(lgf, dims, dtype):
-    U = I.synthetic_config(dims, seed=2, link_scale=0.5)
-    ref = O.fix(U, 1e-15, 2000, ALPHA)
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (4, 6, 10, 12), (16, 12, 8, 48)])
+def test_mixed_precision_fix_matches_fp64_functional(lgf, dims, dtype, reunit_fp64, link_update):
+    U, ref = _oracle_fix(dims, 2, 0.5, 1e-15)
     assert ref["converged"]
     with lgf.GaugeFixer(dims, dtype) as gf:
+        gf.set_param(4, reunit_fp64)  # LGF_REUNIT_FP64
+        gf.set_param(6, link_update)  # LGF_LINK_UPDATE: 0 gauge representation, 1 links in place
         gf.load_links(U)
         iters, conv = gf.fix(1e-15, 2000)
         F, th = gf.functional()
@@ -123,18 +140,33 @@ def test_mixed_precision_fix_matches_fp64_functional(lgf, dims, dtype):
     assert O.average_plaquette(out) == pytest.approx(O.average_plaquette(U), abs=1e-12)
 
 
-def test_fp32_iterations_track_fp64(lgf):
+@pytest.mark.parametrize("link_update", [0, 1])
+@pytest.mark.parametrize("dtype", ["f32", "f32_r12"])
+def test_fp32_iterations_track_fp64(lgf, dtype, link_update):
     """FP32 storage: after 10 iterations every link element is within FP32
-    rounding growth (2e-5) of the FP64 oracle."""
+    rounding growth (2e-5) of the FP64 oracle, in both update modes; one step
+    matches the oracle's intermediates to FP32 rounding.  The accelerated
+    gradient goes through a forward and an inverse FFT over V = 4096 points
+    in FP32: its error is a few eps * log2(V) ~ 4e-6 of its largest entry
+    (the acceleration makes |Delta~| reach ~20 here)."""
     dims = (8, 8, 8, 8)
     U = I.synthetic_config(dims, seed=0, link_scale=0.3)
     ref = O.iterate(U, 10, ALPHA)
-    for dtype in ("f32", "f32_r12"):
-        with lgf.GaugeFixer(dims, dtype) as gf:
-            gf.load_links(U)
-            gf.iterate(10)
-            out = gf.store_links()
-        assert np.max(np.abs(out - ref)) <= 2e-5, dtype
+    parts = O.step_parts(U, ALPHA)
+    with lgf.GaugeFixer(dims, dtype) as gf:
+        gf.set_param(6, link_update)
+        gf.load_links(U)
+        pr = gf.probe()
+        F, th = gf.functional()
+        gf.iterate(10)
+        out = gf.store_links()
+    np.testing.assert_allclose(pr["delta"], _packed(parts["Delta"]), rtol=0, atol=5e-6)
+    dt_ref = _packed(parts["Delta_tilde"])
+    np.testing.assert_allclose(pr["delta_tilde"], dt_ref, rtol=0, atol=4e-6 * np.max(np.abs(dt_ref)))
+    np.testing.assert_allclose(pr["g"], parts["g"], rtol=0, atol=1e-6)
+    assert F == pytest.approx(parts["F"], rel=1e-6)
+    assert th == pytest.approx(parts["theta"], rel=1e-5)
+    assert np.max(np.abs(out - ref)) <= 2e-5
 
 
 # ---------------------------------------------------------------------------
@@ -189,12 +221,14 @@ def test_bad_parameters_are_rejected(lgf):
             gf.iterate(1)  # nothing loaded
 
 
-def test_determinism(lgf):
+@pytest.mark.parametrize("link_update", [0, 1])
+def test_determinism(lgf, link_update):
     dims = (8, 8, 8, 8)
     U = I.synthetic_config(dims, seed=7, link_scale=0.5)
     outs = []
     for _ in range(2):
         with lgf.GaugeFixer(dims, "f32") as gf:
+            gf.set_param(6, link_update)
             gf.load_links(U)
             gf.iterate(20)
             outs.append((gf.store_links(), gf.functional()))

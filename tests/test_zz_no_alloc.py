@@ -55,8 +55,13 @@ def test_noalloc_functional_matches_lgf_functional(dtype):
         assert st == _lib.LGF_OK, lib.lgf_last_error(None)
         torch.cuda.synchronize()
         F, th = out.tolist()
-        assert F == pytest.approx(F_ref, rel=1e-13)
-        assert th == pytest.approx(th_ref, rel=1e-12)
+        # FP64 storage: both sides sum FP64 terms (rel 1e-13 / 1e-12, as in
+        # the FP64 parity tests).  FP32 storage: lgf_functional sums each warp
+        # in FP32 before the FP64 sum, this entry point sums FP64 terms, so
+        # they agree to FP32 rounding (rel 1e-6 / 1e-5, as the FP32 tests).
+        rel_F, rel_th = (1e-13, 1e-12) if dtype.startswith("f64") else (1e-6, 1e-5)
+        assert F == pytest.approx(F_ref, rel=rel_F)
+        assert th == pytest.approx(th_ref, rel=rel_th)
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
