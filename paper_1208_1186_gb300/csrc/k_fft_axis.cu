@@ -49,7 +49,19 @@ __global__ void __launch_bounds__(128) k_xpass(cx<T>* __restrict__ D, int64_t to
   const int nl = (int)((total_lines - g0) < NL ? (total_lines - g0) : NL);
   cx<T>* chunk = D + g0 * L;
   const int ne = nl * L;
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) tile[(e / L) * P + (e % L)] = chunk[e];
+  constexpr int PER = NL * L / 128;  // elements per thread of a full tile
+  if (nl == NL) {  // full tile: every load of a thread in flight at once
+    cx<T> r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) r[k] = chunk[threadIdx.x + 128 * k];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + 128 * k;
+      tile[(e / L) * P + (e % L)] = r[k];
+    }
+  } else {
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) tile[(e / L) * P + (e % L)] = chunk[e];
+  }
   __syncthreads();
   for (int ln = threadIdx.x; ln < nl; ln += blockDim.x) {
     cx<T> v[L];
@@ -64,7 +76,15 @@ __global__ void __launch_bounds__(128) k_xpass(cx<T>* __restrict__ D, int64_t to
     for (int p = 0; p < L; ++p) row[p] = v[p];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) chunk[e] = tile[(e / L) * P + (e % L)];
+  if (nl == NL) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + 128 * k;
+      chunk[e] = tile[(e / L) * P + (e % L)];
+    }
+  } else {
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) chunk[e] = tile[(e / L) * P + (e % L)];
+  }
 }
 
 // One thread per line along an axis of stride S (y: Lx, z: Lx*Ly).
@@ -92,12 +112,21 @@ __global__ void __launch_bounds__(128) k_strided(cx<T>* __restrict__ D, int64_t 
 }
 
 // One thread per t-line: forward t, times the acceleration factor, inverse t.
+// FP64 reads the factor from the per-site table kfac (an FP64 division per
+// mode would be slow on this GPU); FP32 forms it from the per-axis tables
+// s2p[axis][position] = 4 sin^2(pi k / L) at the digit-reversed frequency k
+// of each position: K = p2max / V / (s2x + s2y + s2z + s2t), 0 at k = 0.
 template <class T, int L>
-__global__ void __launch_bounds__(128) k_tpass(cx<T>* __restrict__ D, int64_t V, const T* __restrict__ kfac,
-                                               const cx<T>* __restrict__ tw, const DevState* __restrict__ st) {
+__global__ void __launch_bounds__(128) k_tpass(cx<T>* __restrict__ D, int64_t V, int Lx, int Ly,
+                                               const T* __restrict__ kfac, const float* __restrict__ s2p,
+                                               float c_over_V, const cx<T>* __restrict__ tw,
+                                               const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   __shared__ cx<T> tws[kMaxL];
+  __shared__ float s2t[kMaxL];
   load_tw(tws, tw, L);
+  if (sizeof(T) == 4)
+    for (int i = threadIdx.x; i < L; i += blockDim.x) s2t[i] = s2p[3 * kMaxL + i];
   __syncthreads();
   const int64_t S = V / L;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,8 +137,19 @@ __global__ void __launch_bounds__(128) k_tpass(cx<T>* __restrict__ D, int64_t V,
 #pragma unroll
   for (int p = 0; p < L; ++p) v[p] = line[p * S];
   regfft::forward<T, L>(v, tws);
+  if constexpr (sizeof(T) == 4) {
+    const int x = (int)(l % Lx), y = (int)((l / Lx) % Ly), z = (int)(l / ((int64_t)Lx * Ly));
+    const float a = __ldg(s2p + x) + __ldg(s2p + kMaxL + y) + __ldg(s2p + 2 * kMaxL + z);
 #pragma unroll
-  for (int p = 0; p < L; ++p) v[p] = scale(v[p], __ldg(kfac + l + p * S));
+    for (int p = 0; p < L; ++p) {
+      float k = c_over_V * __frcp_rn(a + s2t[p]);
+      if (p == 0 && l == 0) k = 0.0f;
+      v[p] = scale(v[p], (T)k);
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = scale(v[p], __ldg(kfac + l + p * S));
+  }
   regfft::inverse<T, L>(v, tws);
 #pragma unroll
   for (int p = 0; p < L; ++p) line[p * S] = v[p];
@@ -153,9 +193,10 @@ cudaError_t strided_launch(void* D, int64_t V, int64_t S, const void* tw, int in
 }
 
 template <class T, int L>
-cudaError_t tpass_launch(void* D, int64_t V, const void* kfac, const void* tw, const DevState* st, cudaStream_t s) {
+cudaError_t tpass_launch(void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V,
+                         const void* tw, const DevState* st, cudaStream_t s) {
   const unsigned nb = (unsigned)((4 * (V / L) + 127) / 128);
-  k_tpass<T, L><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, static_cast<const T*>(kfac),
+  k_tpass<T, L><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V,
                                    static_cast<const cx<T>*>(tw), st);
   return cudaPeekAtLastError();
 }
@@ -223,12 +264,12 @@ cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, const void* kfac, const void* tw, const DevState* st,
-                         cudaStream_t s) {
-#define LGF_CASE(N)                                                          \
-  case N:                                                                    \
-    if (prec == 4) return tpass_launch<float, N>(D, V, kfac, tw, st, s);     \
-    if constexpr (N <= 32) return tpass_launch<double, N>(D, V, kfac, tw, st, s); \
+cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p,
+                         float c_over_V, const void* tw, const DevState* st, cudaStream_t s) {
+#define LGF_CASE(N)                                                                                 \
+  case N:                                                                                           \
+    if (prec == 4) return tpass_launch<float, N>(D, V, Lx, Ly, kfac, s2p, c_over_V, tw, st, s);     \
+    if constexpr (N <= 32) return tpass_launch<double, N>(D, V, Lx, Ly, kfac, s2p, c_over_V, tw, st, s); \
     break;
   switch (L) { LGF_AXIS_LENGTHS(LGF_CASE) }
 #undef LGF_CASE

@@ -43,7 +43,7 @@ __device__ __forceinline__ M3<T> load_rw(const cx<T>* base, int64_t V, int64_t s
 }
 
 template <class T, int NC>
-__global__ void __launch_bounds__(kGradThreads, 2) k_gradient_grep(const cx<T>* __restrict__ U0,
+__global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* __restrict__ U0,
                                                                 const cx<T>* __restrict__ G, cx<T>* __restrict__ D,
                                                                 double2* __restrict__ partial, const Geom geo,
                                                                 DevState* st, int mode, double normF, double normT) {
@@ -62,19 +62,16 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_gradient_grep(const cx<T>* 
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const cx<T>* base = U0 + (int64_t)mu * NC * V;
-      M3<T> t;
       {
         const M3<T> u = load_m3<T, NC>(base, V, s);
         const M3<T> gf = load_m3<T, NC>(G, V, site_fwd(geo, s, c, mu));
-        mm_dag<T, 3>(t, u, gf);
-        add_to(C, t);
+        mm_dag_acc(C, u, gf);
       }
       {
         const int64_t sb = site_back(geo, s, c, mu);
         const M3<T> gb = load_m3<T, NC>(G, V, sb);
         const M3<T> ub = load_m3<T, NC>(base, V, sb);
-        mm<T, 3>(t, gb, ub);
-        add_to(B, t);
+        mm_acc(B, gb, ub);
       }
     }
     const M3<T> gx = load_m3<T, NC>(G, V, s);
@@ -171,14 +168,14 @@ inline unsigned nblocks(int64_t n, int thr) { return (unsigned)((n + thr - 1) / 
 
 cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D, double2* partial, const Geom& geo,
                                  DevState* st, int mode, cudaStream_t s) {
-  const unsigned nb = (unsigned)gradient_blocks(geo.V);
   const double nF = 1.0 / (12.0 * (double)geo.V), nT = 1.0 / (3.0 * (double)geo.V);
+  const unsigned nb = (unsigned)((geo.V + kGrepThreads - 1) / kGrepThreads);
   if (nc == 9)
-    k_gradient_grep<float, 9><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
+    k_gradient_grep<float, 9><<<nb, kGrepThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
                                                           static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
                                                           partial, geo, st, mode, nF, nT);
   else
-    k_gradient_grep<float, 6><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
+    k_gradient_grep<float, 6><<<nb, kGrepThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
                                                           static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
                                                           partial, geo, st, mode, nF, nT);
   return cudaPeekAtLastError();

@@ -48,7 +48,9 @@ struct Engine {
   FftGeom fg{};  // FFT tiling for this precision (plane pipeline)
   bool axis = false;     // per-axis register FFT pipeline (else plane pipeline)
   bool grep = false;     // FP32 engine: gauge representation (U holds the loaded links, G is updated)
-  void* kfac = nullptr;  // axis pipeline: p2_max/(V p2(k)) per site, digit-reversed order
+  void* kfac = nullptr;  // axis pipeline, FP64: p2_max/(V p2(k)) per site, digit-reversed order
+  float* s2p = nullptr;  // axis pipeline, FP32: [4][kMaxL] 4 sin^2(pi k/L) at digit-reversed positions
+  float c_over_V = 0.f;  // p2_max / V
   size_t cbytes() const { return 2 * (size_t)prec; }
 };
 
@@ -205,9 +207,8 @@ int alloc_engine(lgf_handle h, Engine& e) {
   if (e.axis) {
     // acceleration factor at every position the forward passes leave a mode:
     // position p along an axis holds frequency digit_rev(L, p)
-    e.kfac = dev_alloc(h, (size_t)V * e.prec);
-    if (!e.kfac) return fail(h, LGF_ERR_OOM, "device allocation failed");
     std::vector<double> s2[4];
+    std::vector<float> s2f(4 * kMaxL, 0.0f);
     double p2max = 0.0;
     for (int a = 0; a < 4; ++a) {
       const int L = h->L[a];
@@ -217,26 +218,28 @@ int alloc_engine(lgf_handle h, Engine& e) {
         const long double sk =
             sinl(3.14159265358979323846264338327950288L * (long double)regfft::digit_rev(L, p) / (long double)L);
         s2[a][p] = (double)(4.0L * sk * sk);
+        s2f[a * kMaxL + p] = (float)s2[a][p];
         m = s2[a][p] > m ? s2[a][p] : m;
       }
       p2max += m;
     }
-    std::vector<double> k64;
-    std::vector<float> k32;
-    if (e.prec == 8) k64.resize(V); else k32.resize(V);
-    int64_t s = 0;
-    for (int t = 0; t < h->L[3]; ++t)
-      for (int z = 0; z < h->L[2]; ++z)
-        for (int y = 0; y < h->L[1]; ++y)
-          for (int x = 0; x < h->L[0]; ++x, ++s) {
-            double f = 0.0;
-            if (x | y | z | t) f = p2max / ((s2[0][x] + s2[1][y] + s2[2][z] + s2[3][t]) * (double)V);
-            if (e.prec == 8) k64[s] = f; else k32[s] = (float)f;
-          }
-    if (e.prec == 8)
+    e.c_over_V = (float)(p2max / (double)V);
+    if (e.prec == 4) {
+      e.s2p = static_cast<float*>(dev_alloc(h, 4 * kMaxL * sizeof(float)));
+      if (!e.s2p) return fail(h, LGF_ERR_OOM, "device allocation failed");
+      LGF_CUDA(h, cudaMemcpy(e.s2p, s2f.data(), s2f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      e.kfac = dev_alloc(h, (size_t)V * e.prec);
+      if (!e.kfac) return fail(h, LGF_ERR_OOM, "device allocation failed");
+      std::vector<double> k64(V);
+      int64_t s = 0;
+      for (int t = 0; t < h->L[3]; ++t)
+        for (int z = 0; z < h->L[2]; ++z)
+          for (int y = 0; y < h->L[1]; ++y)
+            for (int x = 0; x < h->L[0]; ++x, ++s)
+              k64[s] = (x | y | z | t) ? p2max / ((s2[0][x] + s2[1][y] + s2[2][z] + s2[3][t]) * (double)V) : 0.0;
       LGF_CUDA(h, cudaMemcpy(e.kfac, k64.data(), (size_t)V * 8, cudaMemcpyHostToDevice));
-    else
-      LGF_CUDA(h, cudaMemcpy(e.kfac, k32.data(), (size_t)V * 4, cudaMemcpyHostToDevice));
+    }
   }
   return LGF_OK;
 }
@@ -284,7 +287,8 @@ int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
     LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, tw, 0, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, tw + tws, 0, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, tw + 2 * tws, 0, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_T, launch_tpass(e.prec, h->L[3], e.D, V, e.kfac, tw + 3 * tws, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_T, launch_tpass(e.prec, h->L[3], e.D, V, h->L[0], h->L[1], e.kfac, e.s2p, e.c_over_V,
+                                            tw + 3 * tws, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, tw + 2 * tws, 1, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, tw + tws, 1, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, tw, 1, st, s));
@@ -486,7 +490,7 @@ int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out) {
     }
   }
   h->nblk = gradient_blocks(V);
-  h->partial = static_cast<double2*>(dev_alloc(h, (size_t)h->nblk * sizeof(double2)));
+  h->partial = static_cast<double2*>(dev_alloc(h, (size_t)partial_capacity(V) * sizeof(double2)));
   h->st = static_cast<DevState*>(dev_alloc(h, sizeof(DevState)));
   h->sin2 = static_cast<double*>(dev_alloc(h, 4 * kMaxL * sizeof(double)));
   h->hist_cap = 1 << 16;

@@ -46,6 +46,24 @@ __device__ __forceinline__ T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; 
 template <class D, class S>
 __device__ __forceinline__ cx<D> cvt(cx<S> a) { return mk<D>((D)a.re, (D)a.im); }
 
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// acc + a*b as four fused multiply-adds
+template <class T>
+__device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
+  const T re = fmaT(-a.im, b.im, fmaT(a.re, b.re, acc.re));
+  const T im = fmaT(a.im, b.re, fmaT(a.re, b.im, acc.im));
+  return mk<T>(re, im);
+}
+// acc + a*conj(b) as four fused multiply-adds
+template <class T>
+__device__ __forceinline__ cx<T> cmac_cj(cx<T> acc, cx<T> a, cx<T> b) {
+  const T re = fmaT(a.im, b.im, fmaT(a.re, b.re, acc.re));
+  const T im = fmaT(-a.re, b.im, fmaT(a.im, b.re, acc.im));
+  return mk<T>(re, im);
+}
+
 // read-only, cached load of one complex element
 template <class T>
 __device__ __forceinline__ cx<T> ldg(const cx<T>* p);
@@ -101,9 +119,8 @@ __device__ __forceinline__ void mm(M3<T>& c, const M3<T>& a, const M3<T>& b) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       cx<T> acc = a.e[i][0] * b.e[0][j];
-      acc = acc + a.e[i][1] * b.e[1][j];
-      acc = acc + a.e[i][2] * b.e[2][j];
-      c.e[i][j] = acc;
+      acc = cmac(acc, a.e[i][1], b.e[1][j]);
+      c.e[i][j] = cmac(acc, a.e[i][2], b.e[2][j]);
     }
 }
 
@@ -115,9 +132,34 @@ __device__ __forceinline__ void mm_dag(M3<T>& c, const M3<T>& a, const M3<T>& b)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       cx<T> acc = mul_cj(a.e[i][0], b.e[j][0]);
-      acc = acc + mul_cj(a.e[i][1], b.e[j][1]);
-      acc = acc + mul_cj(a.e[i][2], b.e[j][2]);
-      c.e[i][j] = acc;
+      acc = cmac_cj(acc, a.e[i][1], b.e[j][1]);
+      c.e[i][j] = cmac_cj(acc, a.e[i][2], b.e[j][2]);
+    }
+}
+
+// c += a * b
+template <class T>
+__device__ __forceinline__ void mm_acc(M3<T>& c, const M3<T>& a, const M3<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> acc = cmac(c.e[i][j], a.e[i][0], b.e[0][j]);
+      acc = cmac(acc, a.e[i][1], b.e[1][j]);
+      c.e[i][j] = cmac(acc, a.e[i][2], b.e[2][j]);
+    }
+}
+
+// c += a * b^dagger
+template <class T>
+__device__ __forceinline__ void mm_dag_acc(M3<T>& c, const M3<T>& a, const M3<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> acc = cmac_cj(c.e[i][j], a.e[i][0], b.e[j][0]);
+      acc = cmac_cj(acc, a.e[i][1], b.e[j][1]);
+      c.e[i][j] = cmac_cj(acc, a.e[i][2], b.e[j][2]);
     }
 }
 

@@ -73,8 +73,10 @@ cudaError_t launch_xpass(int prec, int L, void* D, int64_t V, const void* tw, in
                          cudaStream_t s);
 cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const void* tw, int inverse,
                            const DevState* st, cudaStream_t s);
-cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, const void* kfac, const void* tw, const DevState* st,
-                         cudaStream_t s);
+// FP64: factor from the per-site table kfac; FP32: from s2p[axis][position]
+// (4 sin^2 at the digit-reversed frequency) and c_over_V = p2_max / V
+cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p,
+                         float c_over_V, const void* tw, const DevState* st, cudaStream_t s);
 
 // FP32 engine in gauge representation (k_gauge_rep.cu): links formed on the
 // fly as G U0 G^dagger; the update acts on G
@@ -87,7 +89,10 @@ cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* ao
 // text returned by lgf_last_error(NULL) on this host thread
 void set_global_error(const std::string& msg);
 
-constexpr int kGradThreads = 256;
+constexpr int kGradThreads = 256;  // k_gradient block size
+constexpr int kGrepThreads = 256;  // k_gradient_grep block size
 inline int gradient_blocks(int64_t V) { return (int)((V + kGradThreads - 1) / kGradThreads); }
+// capacity of the block-partials buffer: enough for the smallest block size
+inline int64_t partial_capacity(int64_t V) { return (V + 63) / 64 + 1; }
 
 }  // namespace lgf
