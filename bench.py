@@ -190,20 +190,37 @@ def time_oracle(U, n: int, alpha: float) -> float:
 
 
 # ---------------------------------------------------------------------------
-def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current source of that kernel."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        rec = json.load(open(path))[workload][kernel]
-    except Exception:
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+COMMON_SOURCES = ("lgf_common.cuh", "lgf_reduce.cuh", "lgf_kernels.cuh", "fft_reg.cuh")
+
+
+def kernel_source_hash(kernel: str, gauge_rep: bool) -> str | None:
+    """sha256 (16 hex) of the sources the kernel is compiled from."""
+    name = "k_gauge_rep.cu" if (gauge_rep and kernel in ("gradient", "build_g")) else KERNEL_SOURCES.get(kernel)
+    if name is None:
         return None
-    src = os.path.join(ROOT, "paper_1208_1186_gb300", "csrc", KERNEL_SOURCES.get(kernel, ""))
+    h = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for f in (name,) + COMMON_SOURCES:
+            h.update(open(os.path.join(ROOT, "paper_1208_1186_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
-    return rec.get("dram_bytes_per_launch") if rec.get("source_sha256_16") == h else None
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, workload: str, gauge_rep: bool):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (lines 'workload kernel dram_bytes_per_launch source_hash'), if it was
+    taken on the current source of that kernel; else None."""
+    want = kernel_source_hash(kernel, gauge_rep)
+    try:
+        for line in open(TRAFFIC_FILE):
+            p = line.split()
+            if len(p) == 4 and not line.startswith("#") and p[0] == workload and p[1] == kernel:
+                return float(p[2]) if p[3] == want else None
+    except OSError:
+        pass
+    return None
 
 
 def run_ours(args, W):
@@ -346,7 +363,7 @@ def run_ours(args, W):
                    "parallelism": f"replicas x{world} (independent configs, no collective on the data path)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(ach / hbm_peak, 4) if ach else None,
-                     "traffic": profile_traffic(dom, args.workload),
+                     "traffic": profile_traffic(dom, args.workload, gauge_rep),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
         "step_roofline": {"algorithmic_bytes_per_site": step_bytes / V,
                           "achieved_gbs": round(step_bytes / (ms_max / args.steps * 1e-3) / 1e9, 1),

@@ -88,27 +88,35 @@ __global__ void __launch_bounds__(128) k_xpass(cx<T>* __restrict__ D, int64_t to
 }
 
 // One thread per line along an axis of stride S (y: Lx, z: Lx*Ly).
+// FP32 lines up to 32 points: four 128-thread blocks per SM (128 registers)
+template <class T, int L>
+constexpr int pass_min_blocks() {
+  return (sizeof(T) == 4 && L <= 32) ? 4 : 1;
+}
+
 template <class T, int L, bool INV>
-__global__ void __launch_bounds__(128) k_strided(cx<T>* __restrict__ D, int64_t V, int64_t S,
+__global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_strided(cx<T>* __restrict__ D, int64_t V, int64_t S,
                                                  const cx<T>* __restrict__ tw, const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   __shared__ cx<T> tws[kMaxL];
   load_tw(tws, tw, L);
   __syncthreads();
-  const int64_t nl = V / L;  // lines per field
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // 32-bit offsets: 4 V < 2^31 for extents <= 64
+  const int nl = (int)(V / L);  // lines per field
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= 4 * nl) return;
-  const int64_t f = g / nl, l = g - f * nl;
-  cx<T>* line = D + f * V + (l % S) + (l / S) * S * L;
+  const int Si = (int)S;
+  const int f = g / nl, l = g - f * nl;
+  cx<T>* line = D + (f * (int)V + (l % Si) + (l / Si) * Si * L);
   cx<T> v[L];
 #pragma unroll
-  for (int p = 0; p < L; ++p) v[p] = line[p * S];
+  for (int p = 0; p < L; ++p) v[p] = line[p * Si];
   if (INV)
     regfft::inverse<T, L>(v, tws);
   else
     regfft::forward<T, L>(v, tws);
 #pragma unroll
-  for (int p = 0; p < L; ++p) line[p * S] = v[p];
+  for (int p = 0; p < L; ++p) line[p * Si] = v[p];
 }
 
 // One thread per t-line: forward t, times the acceleration factor, inverse t.
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(128) k_strided(cx<T>* __restrict__ D, int64_t 
 // s2p[axis][position] = 4 sin^2(pi k / L) at the digit-reversed frequency k
 // of each position: K = p2max / V / (s2x + s2y + s2z + s2t), 0 at k = 0.
 template <class T, int L>
-__global__ void __launch_bounds__(128) k_tpass(cx<T>* __restrict__ D, int64_t V, int Lx, int Ly,
+__global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_tpass(cx<T>* __restrict__ D, int64_t V, int Lx, int Ly,
                                                const T* __restrict__ kfac, const float* __restrict__ s2p,
                                                float c_over_V, const cx<T>* __restrict__ tw,
                                                const DevState* __restrict__ st) {
@@ -128,17 +136,17 @@ __global__ void __launch_bounds__(128) k_tpass(cx<T>* __restrict__ D, int64_t V,
   if (sizeof(T) == 4)
     for (int i = threadIdx.x; i < L; i += blockDim.x) s2t[i] = s2p[3 * kMaxL + i];
   __syncthreads();
-  const int64_t S = V / L;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int S = (int)(V / L);  // 32-bit offsets: 4 V < 2^31 for extents <= 64
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= 4 * S) return;
-  const int64_t f = g / S, l = g - f * S;
-  cx<T>* line = D + f * V + l;
+  const int f = g / S, l = g - f * S;
+  cx<T>* line = D + (f * (int)V + l);
   cx<T> v[L];
 #pragma unroll
   for (int p = 0; p < L; ++p) v[p] = line[p * S];
   regfft::forward<T, L>(v, tws);
   if constexpr (sizeof(T) == 4) {
-    const int x = (int)(l % Lx), y = (int)((l / Lx) % Ly), z = (int)(l / ((int64_t)Lx * Ly));
+    const int x = l % Lx, y = (l / Lx) % Ly, z = l / (Lx * Ly);
     const float a = __ldg(s2p + x) + __ldg(s2p + kMaxL + y) + __ldg(s2p + 2 * kMaxL + z);
 #pragma unroll
     for (int p = 0; p < L; ++p) {
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(128) k_tpass(cx<T>* __restrict__ D, int64_t V,
     }
   } else {
 #pragma unroll
-    for (int p = 0; p < L; ++p) v[p] = scale(v[p], __ldg(kfac + l + p * S));
+    for (int p = 0; p < L; ++p) v[p] = scale(v[p], __ldg(kfac + (l + p * S)));
   }
   regfft::inverse<T, L>(v, tws);
 #pragma unroll

@@ -48,12 +48,12 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
                                                                 double2* __restrict__ partial, const Geom geo,
                                                                 DevState* st, int mode, double normF, double normT) {
   if (mode == 1 && st->done) return;
-  const int64_t V = geo.V;
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = (int)geo.V;  // 36 V < 2^31 for extents <= 64
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   T fsum = 0, tsum = 0;
   if (s < V) {
     int c[4];
-    site_coords(geo, s, c);
+    site_coords_i(geo.L, s, c);
     M3<T> B, C;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -61,20 +61,23 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
       for (int j = 0; j < 3; ++j) B.e[i][j] = C.e[i][j] = mk<T>(0, 0);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const cx<T>* base = U0 + (int64_t)mu * NC * V;
+      const cx<T>* base = U0 + mu * NC * V;
+      const int st_mu = (int)geo.stride[mu];
+      const int span = (geo.L[mu] - 1) * st_mu;
       {
-        const M3<T> u = load_m3<T, NC>(base, V, s);
-        const M3<T> gf = load_m3<T, NC>(G, V, site_fwd(geo, s, c, mu));
+        const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - span;
+        const M3<T> u = load_m3i<T, NC>(base, V, s);
+        const M3<T> gf = load_m3i<T, NC>(G, V, sf);
         mm_dag_acc(C, u, gf);
       }
       {
-        const int64_t sb = site_back(geo, s, c, mu);
-        const M3<T> gb = load_m3<T, NC>(G, V, sb);
-        const M3<T> ub = load_m3<T, NC>(base, V, sb);
+        const int sb = c[mu] > 0 ? s - st_mu : s + span;
+        const M3<T> gb = load_m3i<T, NC>(G, V, sb);
+        const M3<T> ub = load_m3i<T, NC>(base, V, sb);
         mm_acc(B, gb, ub);
       }
     }
-    const M3<T> gx = load_m3<T, NC>(G, V, s);
+    const M3<T> gx = load_m3i<T, NC>(G, V, s);
     M3<T> Uf, Ub;
     mm<T, 3>(Uf, gx, C);      // sum of the links leaving x
     mm_dag<T, 3>(Ub, B, gx);  // sum of the links arriving at x

@@ -105,6 +105,26 @@ __device__ __forceinline__ M3<T> load_m3(const cx<T>* __restrict__ base, int64_t
   return m;
 }
 
+// The same with 32-bit element offsets (valid while NC * 4 * V < 2^31, which
+// the 64-site extent limit guarantees: at most 36 * 64^4 elements).
+template <class T, int NC>
+__device__ __forceinline__ M3<T> load_m3i(const cx<T>* __restrict__ base, int V, int s) {
+  M3<T> m;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m.e[c / 3][c % 3] = ldg(base + (c * V + s));
+  if (NC == 6) complete_row3(m);
+  return m;
+}
+
+__device__ __forceinline__ void site_coords_i(const int L[4], int s, int c[4]) {
+  c[0] = s % L[0];
+  s /= L[0];
+  c[1] = s % L[1];
+  s /= L[1];
+  c[2] = s % L[2];
+  c[3] = s / L[2];
+}
+
 template <class T, int NC>
 __device__ __forceinline__ void store_m3(cx<T>* __restrict__ base, int64_t V, int64_t s, const M3<T>& m) {
 #pragma unroll
