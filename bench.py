@@ -49,7 +49,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "32^4-f32"
 KERNEL_SOURCES = {"update": "k_links.cu", "gradient": "k_links.cu", "build_g": "k_links.cu",
-                  "accumulate": "k_links.cu", "fft_xy": "k_fft.cu", "fft_zt": "k_fft.cu",
+                  "accumulate": "k_links.cu", "fft_xy": "k_fft_plane.cu", "fft_zt": "k_fft_plane.cu",
                   "fft_axis": "k_fft_axis.cu", "fft_t": "k_fft_axis.cu"}
 
 

@@ -76,8 +76,11 @@ enum lgf_param {
   LGF_REUNIT_FP64 = 4,   /* FP32 storage: reunitarise g in FP64 arithmetic (0/1,
                             default 0: g is stored in FP32, so FP64 arithmetic
                             would be rounded away on the store)                */
-  LGF_FFT_PLANES = 5,    /* 1: use the x-y / z-t plane FFT kernels even where
-                            the per-axis register passes apply (default 0)     */
+  LGF_FFT_PIPELINE = 5,  /* FFT pipeline: 0 (default) automatic -- register
+                            planes (x-y + z-t passes) where instantiated, else
+                            per-axis register passes, else shared-memory
+                            Stockham planes; 1 Stockham planes; 2 per-axis
+                            passes; 3 register planes (1 where not available) */
   LGF_LINK_UPDATE = 6    /* FP32 storage, from the next load: 0 (default) keeps
                             the loaded links and applies each update to the
                             accumulated gauge transformation G, forming

@@ -1,0 +1,373 @@
+// Fourier acceleration in three streaming passes, with the paper's "2D plus
+// 2D" split of the 4D transform (Sec. 2.2) and in-register line FFTs
+// (fft_reg.cuh):
+//
+//   k_plane_xy(fwd) -> k_plane_zt(fwd z, fwd t, x p2_max/(V p2), inv t, inv z)
+//   -> k_plane_xy(inv)
+//
+// k_plane_xy: one CTA per (z, t) plane; the four fields of the plane
+// (4 LX LY complex) are staged in shared memory; one thread per x-line does
+// the x transforms, then one thread per y-line the y transforms.
+// k_plane_zt: one CTA per (field, y, run of BX consecutive x) with the whole
+// (z, t) plane of that run in shared memory; z lines, then t lines (forward,
+// acceleration factor, inverse in registers), then z lines again.
+//
+// Frequencies are left in digit-reversed order by the forward transforms and
+// taken in that order by the inverse ones, so the acceleration factor is
+// applied at digit-reversed positions (the same tables as the per-axis
+// pipeline).  The packed gradient crosses memory three times per iteration
+// instead of seven.
+#include "fft_reg.cuh"
+#include "lgf_kernels.cuh"
+
+namespace lgf {
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ void load_tw_p(cx<T>* dst, const cx<T>* __restrict__ src, int L) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
+}
+
+template <int LX, int LY>
+constexpr int xy_threads() {
+  return 4 * (LX > LY ? LX : LY);
+}
+
+template <class T, int LX, int LY>
+constexpr size_t xy_smem_bytes() {
+  return ((size_t)4 * LY * (LX + 1) + LX + LY) * sizeof(cx<T>);
+}
+
+template <class T, int LX, int LY, bool INV>
+__global__ void __launch_bounds__(xy_threads<LX, LY>()) k_plane_xy(cx<T>* __restrict__ D, int V,
+                                                                   const cx<T>* __restrict__ twx_g,
+                                                                   const cx<T>* __restrict__ twy_g,
+                                                                   const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  constexpr int NT = xy_threads<LX, LY>();
+  constexpr int P = LX + 1;
+  constexpr int N = LX * LY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);  // [f][y][x], row pitch P
+  cx<T>* twx = tile + 4 * LY * P;
+  cx<T>* twy = twx + LX;
+  load_tw_p(twx, twx_g, LX);
+  load_tw_p(twy, twy_g, LY);
+  const int plane = blockIdx.x * N;
+  // stage the 4 planes (each contiguous in its field)
+  static_assert((4 * N) % NT == 0, "tile must split evenly over the threads");
+  constexpr int PER = 4 * N / NT;
+  {
+    cx<T> r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + NT * k;
+      const int f = i / N, q = i % N;
+      r[k] = D[f * V + plane + q];
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + NT * k;
+      const int f = i / N, q = i % N;
+      tile[(f * LY + q / LX) * P + q % LX] = r[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 * LY) {  // x lines
+    cx<T>* row = tile + threadIdx.x * P;
+    cx<T> v[LX];
+#pragma unroll
+    for (int p = 0; p < LX; ++p) v[p] = row[p];
+    if (INV)
+      regfft::inverse<T, LX>(v, twx);
+    else
+      regfft::forward<T, LX>(v, twx);
+#pragma unroll
+    for (int p = 0; p < LX; ++p) row[p] = v[p];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 * LX) {  // y lines
+    const int f = threadIdx.x / LX, x = threadIdx.x % LX;
+    cx<T>* col = tile + f * LY * P + x;
+    cx<T> v[LY];
+#pragma unroll
+    for (int p = 0; p < LY; ++p) v[p] = col[p * P];
+    if (INV)
+      regfft::inverse<T, LY>(v, twy);
+    else
+      regfft::forward<T, LY>(v, twy);
+#pragma unroll
+    for (int p = 0; p < LY; ++p) col[p * P] = v[p];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + NT * k;
+    const int f = i / N, q = i % N;
+    D[f * V + plane + q] = tile[(f * LY + q / LX) * P + q % LX];
+  }
+}
+
+// x-run width of a z-t tile: 32 bytes of consecutive complex numbers
+template <class T>
+constexpr int zt_bx() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
+
+// pitch of one t slice: BX*LZ plus padding that shifts consecutive t slices
+// by one run of BX elements across the 32 shared-memory banks
+template <class T, int LZ>
+constexpr int zt_pitch() {
+  constexpr int BX = zt_bx<T>();
+  constexpr int W = (int)sizeof(cx<T>) / 4;  // banks per element
+  for (int pad = 0; pad < 32; ++pad)
+    if ((((BX * LZ + pad) * W) % 32) == ((BX * W) % 32)) return BX * LZ + pad;
+  return BX * LZ;
+}
+
+template <class T, int LZ, int LT>
+constexpr int zt_threads() {
+  return zt_bx<T>() * (LZ > LT ? LZ : LT);
+}
+
+template <class T, int LZ, int LT>
+constexpr size_t zt_smem_bytes() {
+  return ((size_t)zt_pitch<T, LZ>() * LT + LZ + LT) * sizeof(cx<T>);
+}
+
+// FP32: factor from s2p[axis][position] (4 sin^2 at the digit-reversed
+// frequency) and c_over_V = p2_max / V, 0 at k = 0.  FP64: per-site table
+// kfac (an FP64 division per mode would be slow on this GPU).
+template <class T, int LZ, int LT>
+__global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __restrict__ D, int Lx, int Ly,
+                                                                      const T* __restrict__ kfac,
+                                                                      const float* __restrict__ s2p, float c_over_V,
+                                                                      const cx<T>* __restrict__ twz_g,
+                                                                      const cx<T>* __restrict__ twt_g,
+                                                                      const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  constexpr int BX = zt_bx<T>();
+  constexpr int NT = zt_threads<T, LZ, LT>();
+  constexpr int PT = zt_pitch<T, LZ>();
+  constexpr int N = BX * LZ * LT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);  // [t][z][xb], t pitch PT
+  cx<T>* twz = tile + PT * LT;
+  cx<T>* twt = twz + LZ;
+  load_tw_p(twz, twz_g, LZ);
+  load_tw_p(twt, twt_g, LT);
+  const int nxr = Lx / BX;
+  const int x0 = (blockIdx.x % nxr) * BX;
+  const int y = blockIdx.x / nxr;
+  const int f = blockIdx.y;
+  const int LxLy = Lx * Ly;
+  const int V = LxLy * LZ * LT;
+  cx<T>* Df = D + (f * V + x0 + Lx * y);
+  static_assert(N % NT == 0, "tile must split evenly over the threads");
+  constexpr int PER = N / NT;
+  {
+    cx<T> r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + NT * k;
+      const int xb = i % BX, q = i / BX;  // q = z + LZ t
+      r[k] = Df[xb + LxLy * q];
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + NT * k;
+      const int xb = i % BX, q = i / BX;
+      tile[(q / LZ) * PT + (q % LZ) * BX + xb] = r[k];
+    }
+  }
+  __syncthreads();
+  // forward z: lines (xb, t)
+  if (threadIdx.x < BX * LT) {
+    const int xb = threadIdx.x % BX, t = threadIdx.x / BX;
+    cx<T>* line = tile + t * PT + xb;
+    cx<T> v[LZ];
+#pragma unroll
+    for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
+    regfft::forward<T, LZ>(v, twz);
+#pragma unroll
+    for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
+  }
+  __syncthreads();
+  // t lines (xb, z): forward, acceleration factor, inverse
+  if (threadIdx.x < BX * LZ) {
+    const int xb = threadIdx.x % BX, z = threadIdx.x / BX;
+    cx<T>* line = tile + z * BX + xb;
+    cx<T> v[LT];
+#pragma unroll
+    for (int p = 0; p < LT; ++p) v[p] = line[p * PT];
+    regfft::forward<T, LT>(v, twt);
+    const int x = x0 + xb;
+    if constexpr (sizeof(T) == 4) {
+      const float a = __ldg(s2p + x) + __ldg(s2p + kMaxL + y) + __ldg(s2p + 2 * kMaxL + z);
+      const bool origin = (x | y | z) == 0;
+#pragma unroll
+      for (int p = 0; p < LT; ++p) {
+        float kf = c_over_V * __frcp_rn(a + __ldg(s2p + 3 * kMaxL + p));
+        if (p == 0 && origin) kf = 0.0f;
+        v[p] = scale(v[p], (T)kf);
+      }
+    } else {
+      const T* kl = kfac + (x + Lx * (y + Ly * z));
+#pragma unroll
+      for (int p = 0; p < LT; ++p) v[p] = scale(v[p], __ldg(kl + p * (LxLy * LZ)));
+    }
+    regfft::inverse<T, LT>(v, twt);
+#pragma unroll
+    for (int p = 0; p < LT; ++p) line[p * PT] = v[p];
+  }
+  __syncthreads();
+  // inverse z
+  if (threadIdx.x < BX * LT) {
+    const int xb = threadIdx.x % BX, t = threadIdx.x / BX;
+    cx<T>* line = tile + t * PT + xb;
+    cx<T> v[LZ];
+#pragma unroll
+    for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
+    regfft::inverse<T, LZ>(v, twz);
+#pragma unroll
+    for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + NT * k;
+    const int xb = i % BX, q = i / BX;
+    Df[xb + LxLy * q] = tile[(q / LZ) * PT + (q % LZ) * BX + xb];
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// instantiated x-y planes (LX = LY) and z-t planes (LZ, LT), per precision
+#define LGF_XY_F32(X) X(4) X(6) X(8) X(12) X(16) X(20) X(24) X(32) X(48)
+#define LGF_XY_F64(X) X(4) X(6) X(8) X(12) X(16) X(20) X(24) X(32)
+#define LGF_ZT_F32(X)                                                                                      \
+  X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(48, 48) X(48, 8) X(48, 12) \
+  X(24, 48) X(32, 8) X(32, 16) X(16, 32)
+#define LGF_ZT_F64(X) \
+  X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(32, 8) X(32, 16) X(16, 32)
+
+template <class T, int L>
+cudaError_t xy_launch(void* D, int64_t V, const void* twx, const void* twy, int inverse, const DevState* st,
+                      cudaStream_t s, int Lz, int Lt) {
+  const unsigned nb = (unsigned)(Lz * Lt);
+  constexpr int NT = xy_threads<L, L>();
+  constexpr size_t sm = xy_smem_bytes<T, L, L>();
+  const auto Dp = static_cast<cx<T>*>(D);
+  const auto a = static_cast<const cx<T>*>(twx);
+  const auto b = static_cast<const cx<T>*>(twy);
+  if (inverse)
+    k_plane_xy<T, L, L, true><<<nb, NT, sm, s>>>(Dp, (int)V, a, b, st);
+  else
+    k_plane_xy<T, L, L, false><<<nb, NT, sm, s>>>(Dp, (int)V, a, b, st);
+  return cudaPeekAtLastError();
+}
+
+template <class T, int LZ, int LT>
+cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V, const void* twz,
+                      const void* twt, const DevState* st, cudaStream_t s) {
+  dim3 grid((unsigned)((Lx / zt_bx<T>()) * Ly), 4);
+  k_plane_zt<T, LZ, LT><<<grid, zt_threads<T, LZ, LT>(), zt_smem_bytes<T, LZ, LT>(), s>>>(
+      static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, static_cast<const cx<T>*>(twz),
+      static_cast<const cx<T>*>(twt), st);
+  return cudaPeekAtLastError();
+}
+
+template <class T, int L>
+cudaError_t xy_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_plane_xy<T, L, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)xy_smem_bytes<T, L, L>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_plane_xy<T, L, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)xy_smem_bytes<T, L, L>());
+  return e;
+}
+
+template <class T, int LZ, int LT>
+cudaError_t zt_attr() {
+  return cudaFuncSetAttribute(k_plane_zt<T, LZ, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)zt_smem_bytes<T, LZ, LT>());
+}
+
+}  // namespace
+
+bool plane_pipeline_supported(int prec, int Lx, int Ly, int Lz, int Lt) {
+  if (Lx != Ly) return false;
+  if (Lx % (prec == 4 ? 4 : 2) != 0) return false;
+  bool xy = false, zt = false;
+#define LGF_XYQ(L) xy = xy || Lx == L;
+#define LGF_ZTQ(A, B) zt = zt || (Lz == A && Lt == B);
+  if (prec == 4) {
+    LGF_XY_F32(LGF_XYQ)
+    LGF_ZT_F32(LGF_ZTQ)
+  } else {
+    LGF_XY_F64(LGF_XYQ)
+    LGF_ZT_F64(LGF_ZTQ)
+  }
+#undef LGF_XYQ
+#undef LGF_ZTQ
+  return xy && zt;
+}
+
+cudaError_t plane_pipeline_init() {
+  cudaError_t e = cudaSuccess;
+#define LGF_XYA32(L) \
+  if (e == cudaSuccess) e = xy_attr<float, L>();
+#define LGF_XYA64(L) \
+  if (e == cudaSuccess) e = xy_attr<double, L>();
+#define LGF_ZTA32(A, B) \
+  if (e == cudaSuccess) e = zt_attr<float, A, B>();
+#define LGF_ZTA64(A, B) \
+  if (e == cudaSuccess) e = zt_attr<double, A, B>();
+  LGF_XY_F32(LGF_XYA32)
+  LGF_XY_F64(LGF_XYA64)
+  LGF_ZT_F32(LGF_ZTA32)
+  LGF_ZT_F64(LGF_ZTA64)
+#undef LGF_XYA32
+#undef LGF_XYA64
+#undef LGF_ZTA32
+#undef LGF_ZTA64
+  return e;
+}
+
+cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, const void* twx, const void* twy,
+                            int inverse, const DevState* st, cudaStream_t s) {
+#define LGF_XY32(N) \
+  if (L == N) return xy_launch<float, N>(D, V, twx, twy, inverse, st, s, Lz, Lt);
+#define LGF_XY64(N) \
+  if (L == N) return xy_launch<double, N>(D, V, twx, twy, inverse, st, s, Lz, Lt);
+  if (prec == 4) {
+    LGF_XY_F32(LGF_XY32)
+  } else {
+    LGF_XY_F64(LGF_XY64)
+  }
+#undef LGF_XY32
+#undef LGF_XY64
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
+                            float c_over_V, const void* twz, const void* twt, const DevState* st, cudaStream_t s) {
+#define LGF_ZT32(A, B) \
+  if (Lz == A && Lt == B) return zt_launch<float, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, twz, twt, st, s);
+#define LGF_ZT64(A, B) \
+  if (Lz == A && Lt == B) return zt_launch<double, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, twz, twt, st, s);
+  if (prec == 4) {
+    LGF_ZT_F32(LGF_ZT32)
+  } else {
+    LGF_ZT_F64(LGF_ZT64)
+  }
+#undef LGF_ZT32
+#undef LGF_ZT64
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lgf

@@ -46,7 +46,8 @@ struct Engine {
   void* g = nullptr;
   void* tw = nullptr;
   FftGeom fg{};  // FFT tiling for this precision (plane pipeline)
-  bool axis = false;     // per-axis register FFT pipeline (else plane pipeline)
+  bool axis = false;     // per-axis register FFT passes apply to this lattice
+  bool plane = false;    // three-pass register plane pipeline applies
   bool grep = false;     // FP32 engine: gauge representation (U holds the loaded links, G is updated)
   void* kfac = nullptr;  // axis pipeline, FP64: p2_max/(V p2(k)) per site, digit-reversed order
   float* s2p = nullptr;  // axis pipeline, FP32: [4][kMaxL] 4 sin^2(pi k/L) at digit-reversed positions
@@ -70,7 +71,7 @@ struct lgf_ctx {
   double tail_theta = 1e-11;
   long long tail_max32 = -1;
   bool reunit_fp64 = false;   // FP32 storage: reunitarise g in FP64 arithmetic
-  bool force_planes = false;  // use the plane FFT pipeline even where the axis one applies
+  int fft_pipeline = 0;       // 0 auto, 1 Stockham planes, 2 axis passes, 3 register planes
   bool explicit_fp32 = false; // FP32 engine: update the links in place instead of G (from the next load)
 
   Geom geo{};
@@ -204,7 +205,8 @@ int alloc_engine(lgf_handle h, Engine& e) {
     LGF_CUDA(h, cudaMemcpy(e.tw, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice));
   e.axis = true;
   for (int a = 0; a < 4; ++a) e.axis = e.axis && axis_pass_supported(e.prec, h->L[a]);
-  if (e.axis) {
+  e.plane = plane_pipeline_supported(e.prec, h->L[0], h->L[1], h->L[2], h->L[3]);
+  if (e.axis || e.plane) {
     // acceleration factor at every position the forward passes leave a mode:
     // position p along an axis holds frequency digit_rev(L, p)
     std::vector<double> s2[4];
@@ -275,11 +277,33 @@ int reset_state(lgf_handle h, double tol, int max_iter, bool with_hist) {
   return LGF_OK;
 }
 
+// FFT pipeline for engine e: the register plane pipeline (3 passes) where
+// its shapes are instantiated, else the per-axis register passes (7), else
+// the shared-memory Stockham plane kernels; LGF_FFT_PIPELINE can force one
+// (falling back to Stockham where the forced one does not apply).
+int pick_pipeline(lgf_handle h, const Engine& e) {
+  switch (h->fft_pipeline) {
+    case 1: return 1;
+    case 2: return e.axis ? 2 : 1;
+    case 3: return e.plane ? 3 : 1;
+    default: return e.plane ? 3 : (e.axis ? 2 : 1);
+  }
+}
+
 // Fourier acceleration of the packed gradient in e.D (forward 4D FFT, times
-// p2_max/(V p2), inverse), with either pipeline.
+// p2_max/(V p2), inverse).
 int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
   cudaStream_t s = h->stream;
-  if (e.axis && !h->force_planes) {
+  const int pipe = pick_pipeline(h, e);
+  if (pipe == 3) {
+    const char* tw = static_cast<const char*>(e.tw);
+    const size_t tws = (size_t)kMaxL * e.cbytes();
+    const int* L = h->L;
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], tw, tw + tws, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V,
+                                                tw + 2 * tws, tw + 3 * tws, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], tw, tw + tws, 1, st, s));
+  } else if (pipe == 2) {
     const int64_t V = h->V;
     const int64_t Sy = h->L[0], Sz = (int64_t)h->L[0] * h->L[1];
     const char* tw = static_cast<const char*>(e.tw);
@@ -472,6 +496,7 @@ int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out) {
   cudaError_t e = fft_set_smem_limits(8, smem_optin, smem_optin);
   if (e == cudaSuccess) e = fft_set_smem_limits(4, smem_optin, smem_optin);
   if (e == cudaSuccess) e = axis_pass_init();
+  if (e == cudaSuccess) e = plane_pipeline_init();
   if (e != cudaSuccess) {
     cuda_fail(h, e, "cudaFuncSetAttribute");
     return bail(LGF_ERR_CUDA);
@@ -560,8 +585,9 @@ int lgf_set_param(lgf_handle h, int key, double value) {
     case LGF_REUNIT_FP64:
       h->reunit_fp64 = value != 0.0;
       return LGF_OK;
-    case LGF_FFT_PLANES:
-      h->force_planes = value != 0.0;
+    case LGF_FFT_PIPELINE:
+      if (!(value >= 0 && value <= 3)) return fail(h, LGF_ERR_ARG, "FFT pipeline must be 0, 1, 2 or 3");
+      h->fft_pipeline = (int)value;
       return LGF_OK;
     case LGF_LINK_UPDATE:
       h->explicit_fp32 = value != 0.0;

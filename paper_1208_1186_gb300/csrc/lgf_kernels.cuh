@@ -78,6 +78,16 @@ cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const
 cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p,
                          float c_over_V, const void* tw, const DevState* st, cudaStream_t s);
 
+// three-pass plane pipeline with register FFTs (k_fft_plane.cu): x-y plane
+// (Lx = Ly) and z-t plane (fwd, acceleration factor, inv) kernels for a list
+// of instantiated shapes
+bool plane_pipeline_supported(int prec, int Lx, int Ly, int Lz, int Lt);
+cudaError_t plane_pipeline_init();
+cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, const void* twx, const void* twy,
+                            int inverse, const DevState* st, cudaStream_t s);
+cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
+                            float c_over_V, const void* twz, const void* twt, const DevState* st, cudaStream_t s);
+
 // FP32 engine in gauge representation (k_gauge_rep.cu): links formed on the
 // fly as G U0 G^dagger; the update acts on G
 cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D, double2* partial, const Geom& geo,

@@ -21,10 +21,12 @@ pytestmark = pytest.mark.gpu
 
 ALPHA = 0.08
 
-# Lattices whose every extent is in {4, 6, 8, 12, 16, 20, 24, 32} run the
-# per-axis register FFT passes; the others run the x-y / z-t plane kernels.
+# FFT pipelines (LGF_FFT_PIPELINE): register planes where Lx = Ly and the
+# (Lz, Lt) shape is instantiated; else per-axis register passes where every
+# extent is in {4, 6, 8, 12, 16, 20, 24, 32}; else Stockham plane kernels.
 STEP_DIMS = [
-    (8, 8, 8, 8),      # C1 shape (axis passes)
+    (8, 8, 8, 8),      # C1 shape (register planes)
+    (12, 12, 32, 8),   # register planes, z-t plane 32 x 8
     (6, 12, 4, 20),    # axis passes, radices 2, 3, 4, 5; V = 5760
     (20, 8, 24, 6),    # axis passes, V = 23040
     (4, 6, 10, 12),    # plane kernels (10); V = 2880, ragged last block
@@ -57,14 +59,14 @@ def _oracle_fix(dims, seed, link_scale, tol):
     return U, O.fix(U, tol, 2000, ALPHA)
 
 
-@pytest.mark.parametrize("planes", [0, 1])
+@pytest.mark.parametrize("planes", [0, 1, 2, 3])
 @pytest.mark.parametrize("dtype", ["f64", "f64_r12"])
 @pytest.mark.parametrize("dims", STEP_DIMS)
 def test_one_step_matches_oracle(lgf, dims, dtype, planes):
     U = I.synthetic_config(dims, seed=3, link_scale=0.5)
     ref = O.step_parts(U, ALPHA)
     with lgf.GaugeFixer(dims, dtype) as gf:
-        gf.set_param(5, planes)  # LGF_FFT_PLANES
+        gf.set_param(5, planes)  # LGF_FFT_PIPELINE: auto, Stockham, axis passes, register planes
         gf.load_links(U)
         out = gf.probe()
         F, th = gf.functional()
@@ -123,7 +125,7 @@ def test_fix_matches_oracle_c1(lgf):
 @pytest.mark.parametrize("link_update", [0, 1])
 @pytest.mark.parametrize("reunit_fp64", [0, 1])
 @pytest.mark.parametrize("dtype", ["f32", "f32_r12"])
-@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (4, 6, 10, 12), (16, 12, 8, 48)])
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (4, 6, 10, 12), (16, 12, 8, 48), (8, 8, 32, 16)])
 def test_mixed_precision_fix_matches_fp64_functional(lgf, dims, dtype, reunit_fp64, link_update):
     U, ref = _oracle_fix(dims, 2, 0.5, 1e-15)
     assert ref["converged"]
