@@ -190,6 +190,43 @@ int lgf_profile_read(lgf_handle h, double* ms, long long* launches, int n);
 /* Short name of a kernel kind ("update", ...), "" if out of range. */
 const char* lgf_kernel_name(int kind);
 
+/* ------------------------------------------------------------------------
+ * Batches: several lattices (any sizes and storage types, one device) fixed
+ * together.  Each host check launches one CUDA graph holding LGF_CHECK_EVERY
+ * iterations of every member as independent branches, so small lattices
+ * that cannot fill the GPU alone run concurrently; each member keeps its own
+ * on-device stop decision, so converged members cost only empty launches.
+ * Mixed-precision members run their FP32 phases together, then their FP64
+ * tails together.  The batch borrows the handles (they must outlive it and
+ * must not be used concurrently with it) and runs on its own streams.
+ * ------------------------------------------------------------------------ */
+typedef struct lgf_batch_ctx* lgf_batch;
+
+/* Group n loaded-or-not handles (distinct, same device) into a batch. */
+int lgf_batch_create(const lgf_handle* handles, int n, lgf_batch* out);
+int lgf_batch_destroy(lgf_batch b);
+
+/* Exactly n iterations of every member (no convergence test). */
+int lgf_batch_iterate(lgf_batch b, int n);
+
+/* lgf_fix for every member: iters_out[i] and converged_out[i] (either may be
+ * NULL) receive each member's updates and 0/1.  Returns LGF_OK if all
+ * converged, LGF_ERR_NOT_CONVERGED otherwise, or an error. */
+int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, int* converged_out);
+
+/* Text of the last error of a batch call. */
+const char* lgf_batch_last_error(lgf_batch b);
+
+/* Autotuner: time every FFT pipeline that applies to this lattice (x-y/z-t
+ * register planes, per-axis register passes, shared-memory Stockham planes)
+ * on each of the handle's engines, reps accelerations each, and use the
+ * fastest from now on (unless LGF_FFT_PIPELINE forces one).  Results are
+ * cached per (precision, lattice shape) for the process.  *chosen (may be
+ * NULL) receives the pipeline of the engine that iterates first (1 Stockham
+ * planes, 2 axis passes, 3 register planes).  Overwrites the gradient
+ * scratch only; the links are untouched. */
+int lgf_autotune(lgf_handle h, int reps, int* chosen);
+
 /* F and theta of links the caller already holds in device memory, computed
  * without allocating any memory.  The paper has no counterpart: this exists
  * for callers that may not allocate on the GPU -- a host program that

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import LgfError
 
-__all__ = ["GaugeFixer", "LgfError"]
+__all__ = ["GaugeFixer", "GaugeBatch", "LgfError"]
 
 def _as_ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
@@ -145,3 +145,58 @@ class GaugeFixer:
         cnt = np.zeros(n, dtype=np.int64)
         _lib.check(self.lib.lgf_profile_read(self.h, _as_ptr(ms), _as_ptr(cnt), n), "lgf_profile_read", self.h)
         return {self.lib.lgf_kernel_name(k).decode(): (float(ms[k]), int(cnt[k])) for k in range(n)}
+
+    def autotune(self, reps: int = 10) -> int:
+        """Time the FFT pipelines that apply to this lattice and use the
+        fastest; returns its number (1 Stockham planes, 2 axis passes, 3
+        register planes)."""
+        ch = ctypes.c_int(0)
+        _lib.check(self.lib.lgf_autotune(self.h, int(reps), ctypes.byref(ch)), "lgf_autotune", self.h)
+        return ch.value
+
+
+class GaugeBatch:
+    """Several GaugeFixer handles (any sizes) iterated together from CUDA
+    graphs with one branch per lattice.  The fixers must outlive the batch."""
+
+    def __init__(self, fixers):
+        self.lib = _lib.load()
+        self.fixers = list(fixers)
+        arr = (ctypes.c_void_p * len(self.fixers))(*[f.h.value for f in self.fixers])
+        b = ctypes.c_void_p()
+        _lib.check(self.lib.lgf_batch_create(arr, len(self.fixers), ctypes.byref(b)), "lgf_batch_create")
+        self.b = b
+
+    def _check(self, st, where):
+        if st != _lib.LGF_OK:
+            raise LgfError(st, where, self.lib.lgf_batch_last_error(self.b).decode())
+
+    def iterate(self, n: int):
+        self._check(self.lib.lgf_batch_iterate(self.b, int(n)), "lgf_batch_iterate")
+
+    def fix(self, theta_tol: float, max_iter: int):
+        """Returns (iterations per member, converged per member)."""
+        n = len(self.fixers)
+        it = np.zeros(n, dtype=np.int32)
+        cv = np.zeros(n, dtype=np.int32)
+        st = self.lib.lgf_batch_fix(self.b, float(theta_tol), int(max_iter), _as_ptr(it), _as_ptr(cv))
+        if st not in (_lib.LGF_OK, _lib.LGF_ERR_NOT_CONVERGED):
+            self._check(st, "lgf_batch_fix")
+        return it.tolist(), [bool(c) for c in cv]
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.lgf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -54,6 +54,12 @@ SIGNATURES = {
     "lgf_profile_read": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "lgf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "lgf_functional_noalloc": (ctypes.c_int, [_P] + [ctypes.c_int] * 5 + [_P, _P]),
+    "lgf_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "lgf_batch_destroy": (ctypes.c_int, [_P]),
+    "lgf_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lgf_batch_fix": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P, _P]),
+    "lgf_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lgf_autotune": (ctypes.c_int, [_P, ctypes.c_int, _IP]),
 }
 LGF_NUM_KERNELS = 9
 

@@ -15,8 +15,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lgf.h"
@@ -48,6 +52,7 @@ struct Engine {
   FftGeom fg{};  // FFT tiling for this precision (plane pipeline)
   bool axis = false;     // per-axis register FFT passes apply to this lattice
   bool plane = false;    // three-pass register plane pipeline applies
+  int tuned = 0;         // pipeline chosen by lgf_autotune (0: none)
   bool grep = false;     // FP32 engine: gauge representation (U holds the loaded links, G is updated)
   void* kfac = nullptr;  // axis pipeline, FP64: p2_max/(V p2(k)) per site, digit-reversed order
   float* s2p = nullptr;  // axis pipeline, FP32: [4][kMaxL] 4 sin^2(pi k/L) at digit-reversed positions
@@ -282,6 +287,7 @@ int reset_state(lgf_handle h, double tol, int max_iter, bool with_hist) {
 // the shared-memory Stockham plane kernels; LGF_FFT_PIPELINE can force one
 // (falling back to Stockham where the forced one does not apply).
 int pick_pipeline(lgf_handle h, const Engine& e) {
+  if (h->fft_pipeline == 0 && e.tuned != 0) return e.tuned;
   switch (h->fft_pipeline) {
     case 1: return 1;
     case 2: return e.axis ? 2 : 1;
@@ -397,6 +403,253 @@ int run_fix(lgf_handle h, Engine& e, double tol, int max_iter, bool stall_check,
   *done_iters = s.iters;
   h->hist_n = s.iters + 1 < h->hist_cap ? s.iters + 1 : h->hist_cap;
   *converged = s.theta < tol;
+  return LGF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// autotuner: FFT pipeline per lattice shape and precision
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;  // (prec, Lx, Ly, Lz, Lt) -> pipeline
+
+// Time every pipeline that applies to engine e (Fourier acceleration of its
+// packed-gradient buffer, which is scratch between iterations) and return
+// the fastest; results are cached for the process.
+int tune_engine(lgf_handle h, Engine& e, int reps, int* out) {
+  const auto key = std::make_tuple(e.prec, h->L[0], h->L[1], h->L[2], h->L[3]);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *out = it->second;
+      return LGF_OK;
+    }
+  }
+  LGF_CUDA(h, cudaMemsetAsync(e.D, 0, (size_t)4 * h->V * e.cbytes(), h->stream));
+  std::vector<int> cands = {1};
+  if (e.axis) cands.push_back(2);
+  if (e.plane) cands.push_back(3);
+  cudaEvent_t a, b;
+  LGF_CUDA(h, cudaEventCreate(&a));
+  LGF_CUDA(h, cudaEventCreate(&b));
+  const int saved = h->fft_pipeline;
+  const bool saved_prof = h->profiling;
+  h->profiling = false;
+  float best = 0.0f;
+  int best_p = cands[0];
+  int rc = LGF_OK;
+  for (int p : cands) {
+    h->fft_pipeline = p;
+    for (int i = 0; i < 2 && !rc; ++i) rc = queue_accelerate(h, e, nullptr);
+    if (rc) break;
+    cudaEventRecord(a, h->stream);
+    for (int i = 0; i < reps && !rc; ++i) rc = queue_accelerate(h, e, nullptr);
+    cudaEventRecord(b, h->stream);
+    if (rc) break;
+    if (cudaEventSynchronize(b) != cudaSuccess) {
+      rc = fail(h, LGF_ERR_CUDA, "autotune: event synchronisation failed");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (p == cands[0] || ms < best) {
+      best = ms;
+      best_p = p;
+    }
+  }
+  h->fft_pipeline = saved;
+  h->profiling = saved_prof;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best_p;
+  }
+  *out = best_p;
+  return LGF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// batches: many lattices (of any sizes) iterated together from CUDA graphs
+// ---------------------------------------------------------------------------
+struct lgf_batch_ctx {
+  std::vector<lgf_handle> h;
+  std::vector<cudaStream_t> streams;  // one per member: parallel graph branches
+  std::vector<cudaEvent_t> joins;
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int exec_k = 0;                     // iterations per member per graph launch
+  std::vector<int> exec_members;      // members captured in exec
+  std::vector<long long> exec_launches;  // kernels per member per graph launch
+  std::string err;
+};
+
+namespace {
+
+int bfail(lgf_batch b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+#define LGF_BCUDA(b, call)                                                                             \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return bfail((b), LGF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void drop_graph(lgf_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->exec_members.clear();
+}
+
+// Capture k iterations of every listed member (on its current engine) as one
+// graph: the members' kernel chains are independent branches between a fork
+// and a join on the batch's main stream.
+int capture(lgf_batch b, const std::vector<int>& members, int k) {
+  drop_graph(b);
+  LGF_BCUDA(b, cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+  int rc = LGF_OK;
+  cudaEventRecord(b->fork, b->main);
+  b->exec_launches.assign(members.size(), 0);
+  for (size_t m = 0; m < members.size() && !rc; ++m) {
+    const int i = members[m];
+    lgf_handle h = b->h[i];
+    cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    cudaStream_t saved = h->stream;
+    const bool prof = h->profiling;
+    h->stream = b->streams[i];
+    h->profiling = false;
+    const long long l0 = h->launches;
+    for (int j = 0; j < k && !rc; ++j) rc = queue_iteration(h, *h->cur);
+    b->exec_launches[m] = h->launches - l0;
+    h->launches = l0;
+    h->stream = saved;
+    h->profiling = prof;
+    if (rc) b->err = h->err;
+    cudaEventRecord(b->joins[i], b->streams[i]);
+    cudaStreamWaitEvent(b->main, b->joins[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->main, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bfail(b, LGF_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, LGF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->exec_k = k;
+  b->exec_members = members;
+  return LGF_OK;
+}
+
+int launch_graph(lgf_batch b) {
+  LGF_BCUDA(b, cudaGraphLaunch(b->exec, b->main));
+  for (size_t m = 0; m < b->exec_members.size(); ++m) b->h[b->exec_members[m]]->launches += b->exec_launches[m];
+  return LGF_OK;
+}
+
+// Reset the members' stop state on the main stream.
+int reset_members(lgf_batch b, const std::vector<int>& members, const std::vector<double>& tol,
+                  const std::vector<int>& max_iter) {
+  for (size_t m = 0; m < members.size(); ++m) {
+    lgf_handle h = b->h[members[m]];
+    DevState s{};
+    s.max_iter = max_iter[m];
+    s.tol = tol[m];
+    s.hist = h->hist;
+    s.hist_cap = h->hist_cap;
+    *h->st_host = s;
+    LGF_BCUDA(b, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, b->main));
+  }
+  LGF_BCUDA(b, cudaStreamSynchronize(b->main));
+  return LGF_OK;
+}
+
+int read_members(lgf_batch b, const std::vector<int>& members) {
+  for (int i : members) {
+    lgf_handle h = b->h[i];
+    LGF_BCUDA(b, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, b->main));
+  }
+  LGF_BCUDA(b, cudaStreamSynchronize(b->main));
+  return LGF_OK;
+}
+
+// Stop one member's queue from the host (its kernels then return at once).
+int stop_member(lgf_batch b, int i) {
+  lgf_handle h = b->h[i];
+  h->st_host->done = 1;
+  LGF_BCUDA(b, cudaMemcpyAsync(&h->st->done, &h->st_host->done, sizeof(int), cudaMemcpyHostToDevice, b->main));
+  LGF_BCUDA(b, cudaStreamSynchronize(b->main));
+  return LGF_OK;
+}
+
+// Run the listed members until each has stopped (theta < tol, its update
+// budget, or -- with stall_check -- theta no longer halving between checks).
+int run_members(lgf_batch b, const std::vector<int>& members, const std::vector<double>& tol,
+                const std::vector<int>& max_iter, const std::vector<char>& stall_check) {
+  if (members.empty()) return LGF_OK;
+  int rc = reset_members(b, members, tol, max_iter);
+  if (rc) return rc;
+  int kmax = 1, cap = 0;
+  for (size_t m = 0; m < members.size(); ++m) {
+    kmax = std::max(kmax, b->h[members[m]]->check_every);
+    cap = std::max(cap, max_iter[m]);
+  }
+  rc = capture(b, members, kmax);
+  if (rc) return rc;
+  std::vector<double> last(members.size(), INFINITY);
+  std::vector<int> stalls(members.size(), 0);
+  std::vector<char> fin(members.size(), 0);
+  long long queued = 0;
+  for (;;) {
+    rc = launch_graph(b);
+    if (rc) return rc;
+    queued += kmax;
+    rc = read_members(b, members);
+    if (rc) return rc;
+    bool all = true;
+    for (size_t m = 0; m < members.size(); ++m) {
+      if (fin[m]) continue;
+      lgf_handle h = b->h[members[m]];
+      const DevState& s = *h->st_host;
+      if (s.nonfinite)
+        return bfail(b, LGF_ERR_NONFINITE, "member " + std::to_string(members[m]) + ": F or theta is not finite");
+      if (s.done) {
+        fin[m] = 1;
+        continue;
+      }
+      if (stall_check[m]) {
+        if (s.theta > 0.5 * last[m]) {
+          if (++stalls[m] >= 2) {
+            rc = stop_member(b, members[m]);
+            if (rc) return rc;
+            fin[m] = 1;
+            continue;
+          }
+        } else {
+          stalls[m] = 0;
+        }
+        last[m] = s.theta;
+      }
+      all = false;
+    }
+    if (all || queued > (long long)cap + kmax) break;
+  }
+  for (int i : members) {
+    lgf_handle h = b->h[i];
+    h->hist_n = h->st_host->iters + 1 < h->hist_cap ? h->st_host->iters + 1 : h->hist_cap;
+  }
   return LGF_OK;
 }
 
@@ -755,6 +1008,155 @@ int lgf_fix_split(lgf_handle h, int* fp32_iters, int* fp64_iters) {
   if (fp64_iters) *fp64_iters = h->last_n64;
   return LGF_OK;
 }
+
+int lgf_autotune(lgf_handle h, int reps, int* chosen) {
+  if (!h || reps < 1) return LGF_ERR_ARG;
+  int p64 = 0, p32 = 0;
+  int rc = tune_engine(h, h->e64, reps, &p64);
+  if (rc) return rc;
+  h->e64.tuned = p64;
+  if (h->mixed) {
+    rc = tune_engine(h, h->e32, reps, &p32);
+    if (rc) return rc;
+    h->e32.tuned = p32;
+  }
+  if (chosen) *chosen = h->mixed ? p32 : p64;
+  return LGF_OK;
+}
+
+int lgf_batch_create(const lgf_handle* handles, int n, lgf_batch* out) {
+  if (!out) return LGF_ERR_ARG;
+  *out = nullptr;
+  if (!handles || n < 1) return fail(nullptr, LGF_ERR_ARG, "lgf_batch_create: need at least one handle");
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return fail(nullptr, LGF_ERR_ARG, "lgf_batch_create: NULL handle");
+    if (handles[i]->device != handles[0]->device)
+      return fail(nullptr, LGF_ERR_ARG, "lgf_batch_create: all handles must live on one device");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(nullptr, LGF_ERR_ARG, "lgf_batch_create: a handle appears twice");
+  }
+  lgf_batch_ctx* b = new (std::nothrow) lgf_batch_ctx();
+  if (!b) return fail(nullptr, LGF_ERR_OOM, "host allocation failed");
+  b->h.assign(handles, handles + n);
+  bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  b->streams.assign(n, nullptr);
+  b->joins.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    lgf_batch_destroy(b);
+    return fail(nullptr, LGF_ERR_CUDA, "lgf_batch_create: stream or event creation failed");
+  }
+  *out = b;
+  return LGF_OK;
+}
+
+int lgf_batch_destroy(lgf_batch b) {
+  if (!b) return LGF_ERR_ARG;
+  if (b->main) cudaStreamSynchronize(b->main);
+  drop_graph(b);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->main) cudaStreamDestroy(b->main);
+  delete b;
+  return LGF_OK;
+}
+
+int lgf_batch_iterate(lgf_batch b, int n) {
+  if (!b || n < 0) return LGF_ERR_ARG;
+  std::vector<int> all;
+  for (int i = 0; i < (int)b->h.size(); ++i) {
+    if (!b->h[i]->loaded) return bfail(b, LGF_ERR_ARG, "member " + std::to_string(i) + " has no links loaded");
+    cudaStreamSynchronize(b->h[i]->stream);
+    all.push_back(i);
+  }
+  std::vector<double> tol(all.size(), -1.0);
+  std::vector<int> cap(all.size(), n);
+  std::vector<char> stall(all.size(), 0);
+  int rc = run_members(b, all, tol, cap, stall);
+  if (rc) return rc;
+  for (int i : all) b->h[i]->total_updates += b->h[i]->st_host->iters;
+  return LGF_OK;
+}
+
+int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, int* converged_out) {
+  if (!b || max_iter < 0 || !(theta_tol > 0.0)) return LGF_ERR_ARG;
+  const int n = (int)b->h.size();
+  std::vector<int> all, n1(n, 0), n2(n, 0);
+  std::vector<double> tol1;
+  std::vector<int> cap1;
+  std::vector<char> stall1;
+  for (int i = 0; i < n; ++i) {
+    lgf_handle h = b->h[i];
+    if (!h->loaded) return bfail(b, LGF_ERR_ARG, "member " + std::to_string(i) + " has no links loaded");
+    cudaStreamSynchronize(h->stream);
+    h->last_n32 = h->last_n64 = 0;
+    all.push_back(i);
+    const bool fp32 = h->mixed && h->cur == &h->e32;
+    tol1.push_back(fp32 ? std::max(theta_tol, h->tail_theta) : theta_tol);
+    int cap = max_iter;
+    if (fp32 && h->tail_max32 >= 0 && h->tail_max32 < cap) cap = (int)h->tail_max32;
+    cap1.push_back(cap);
+    stall1.push_back(fp32 ? 1 : 0);
+  }
+  // phase 1: every member on its current engine (FP32 bulk, or FP64)
+  int rc = run_members(b, all, tol1, cap1, stall1);
+  if (rc) return rc;
+  std::vector<int> tail;
+  for (int i = 0; i < n; ++i) {
+    lgf_handle h = b->h[i];
+    n1[i] = h->st_host->iters;
+    h->total_updates += n1[i];
+    if (h->mixed && h->cur == &h->e32) {
+      h->last_n32 = n1[i];
+      if (h->st_host->theta < theta_tol) continue;
+      // FP64 tail from the loaded links and the reunitarised accumulated G
+      const int64_t V = h->V;
+      cudaStream_t saved = h->stream;
+      h->stream = b->main;
+      rc = LGF_OK;
+      do {
+        LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
+        LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice,
+                                    h->stream));
+        LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
+      } while (0);
+      h->stream = saved;
+      h->cur = &h->e64;
+      tail.push_back(i);
+    } else {
+      h->last_n64 = n1[i];
+    }
+  }
+  LGF_BCUDA(b, cudaStreamSynchronize(b->main));
+  // phase 2: the FP64 tails together
+  std::vector<double> tol2(tail.size(), theta_tol);
+  std::vector<int> cap2;
+  for (int i : tail) cap2.push_back(max_iter - n1[i] > 0 ? max_iter - n1[i] : 0);
+  std::vector<char> stall2(tail.size(), 0);
+  rc = run_members(b, tail, tol2, cap2, stall2);
+  if (rc) return rc;
+  for (int i : tail) {
+    n2[i] = b->h[i]->st_host->iters;
+    b->h[i]->last_n64 = n2[i];
+    b->h[i]->total_updates += n2[i];
+  }
+  bool all_conv = true;
+  for (int i = 0; i < n; ++i) {
+    const bool conv = b->h[i]->st_host->theta < theta_tol;
+    all_conv = all_conv && conv;
+    if (iters_out) iters_out[i] = n1[i] + n2[i];
+    if (converged_out) converged_out[i] = conv ? 1 : 0;
+  }
+  return all_conv ? LGF_OK : bfail(b, LGF_ERR_NOT_CONVERGED, "some members reached max_iter with theta >= tol");
+}
+
+const char* lgf_batch_last_error(lgf_batch b) { return b ? b->err.c_str() : ""; }
 
 int lgf_history(lgf_handle h, double* theta_out, int cap, int* n_out) {
   if (!h) return LGF_ERR_ARG;
