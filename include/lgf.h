@@ -227,6 +227,56 @@ const char* lgf_batch_last_error(lgf_batch b);
  * scratch only; the links are untouched. */
 int lgf_autotune(lgf_handle h, int reps, int* chosen);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start.  A 4D convolutional network (three periodic 3^4-tap
+ * layers, 48 -> 32 -> 32 -> 8 channels, ReLU after the first two, BF16
+ * weights and activations with FP32 accumulation on the tensor cores)
+ * maps per-site features of the loaded links -- the su(3) coefficients of
+ * the traceless anti-Hermitian part of each link (32) and the six plaquette
+ * traces / 3 -- to eight coefficients c_a; the warm start is the gauge
+ * transformation g0(x) = exp(sum_a c_a i lambda_a / 2), installed as the
+ * initial accumulated transformation of an FP32 gauge-representation
+ * handle, after which lgf_fix runs the plain method (the judge, via theta
+ * and F; it may end in a different Gribov copy than without the warm start).
+ * Training maximises F(U^{g0}), the method's own functional: the signal
+ * fed back is its derivative along left translations of g0, i.e. the
+ * transformed links' gradient projected on the generators.  The paper has no
+ * learned component; all network work runs on the handle's stream.
+ * ------------------------------------------------------------------------ */
+typedef struct lgf_net_ctx* lgf_net;
+
+/* Number of FP32 parameters: W1[81][48][32], b1[32], W2[81][32][32], b2[32],
+ * W3[81][32][8], b3[8] (tap = ((dt*3 + dz)*3 + dy)*3 + dx, offsets d - 1). */
+int lgf_net_param_count(void);
+
+/* New network on the current device, He-initialised from a counter-based
+ * generator (SplitMix64 + Box-Muller) with this seed. */
+int lgf_net_create(unsigned long long seed, lgf_net* out);
+int lgf_net_destroy(lgf_net n);
+
+/* Copy the FP32 parameters out / in (setting them resets the optimiser). */
+int lgf_net_get_params(lgf_net n, float* host);
+int lgf_net_set_params(lgf_net n, const float* host);
+
+/* Network output c[V][8] for the links loaded in h (an LGF_F32 or
+ * LGF_F32_R12 handle in gauge representation, V a multiple of 16); host_c
+ * may be NULL. */
+int lgf_net_forward(lgf_net n, lgf_handle h, float* host_c);
+
+/* One training step on the links loaded in h: forward, loss -F(U^{g0}),
+ * backward, and (if lr > 0) one Adam step (beta 0.9/0.999).  *F_out (may be
+ * NULL) receives F(U^{g0}) before the step; host_grad (may be NULL) receives
+ * the parameter gradient of -F (layout of lgf_net_get_params).  Leaves the
+ * handle's links untouched. */
+int lgf_net_train_step(lgf_net n, lgf_handle h, double lr, double* F_out, float* host_grad);
+
+/* Install the predicted g0 as the initial gauge transformation of h; call
+ * right after lgf_load_links (the following lgf_fix starts from U^{g0}). */
+int lgf_net_warm_start(lgf_net n, lgf_handle h);
+
+/* Text of the last error of a network call (NULL: of lgf_net_create). */
+const char* lgf_net_last_error(lgf_net n);
+
 /* F and theta of links the caller already holds in device memory, computed
  * without allocating any memory.  The paper has no counterpart: this exists
  * for callers that may not allocate on the GPU -- a host program that

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import LgfError
 
-__all__ = ["GaugeFixer", "GaugeBatch", "LgfError"]
+__all__ = ["GaugeFixer", "GaugeBatch", "WarmStartNet", "LgfError"]
 
 def _as_ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
@@ -200,3 +200,60 @@ class GaugeBatch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class WarmStartNet:
+    """The learned warm start (lgf_net_*): a small 4D convolutional network
+    that predicts the initial gauge transformation of an FP32 handle."""
+
+    def __init__(self, seed: int = 0, torch_allocator: bool = True):
+        self.lib = _lib.load()
+        if torch_allocator:
+            _lib.use_torch_allocator()
+        n = ctypes.c_void_p()
+        st = self.lib.lgf_net_create(ctypes.c_ulonglong(seed), ctypes.byref(n))
+        if st != _lib.LGF_OK:
+            raise LgfError(st, "lgf_net_create", self.lib.lgf_net_last_error(None).decode())
+        self.n = n
+        self.nparams = int(self.lib.lgf_net_param_count())
+
+    def _check(self, st, where):
+        if st != _lib.LGF_OK:
+            raise LgfError(st, where, self.lib.lgf_net_last_error(self.n).decode())
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparams, dtype=np.float32)
+        self._check(self.lib.lgf_net_get_params(self.n, _as_ptr(p)), "lgf_net_get_params")
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        self._check(self.lib.lgf_net_set_params(self.n, _as_ptr(p)), "lgf_net_set_params")
+
+    def forward(self, gf: "GaugeFixer") -> np.ndarray:
+        c = np.empty(gf.shape + (8,), dtype=np.float32)
+        self._check(self.lib.lgf_net_forward(self.n, gf.h, _as_ptr(c)), "lgf_net_forward")
+        return c
+
+    def train_step(self, gf: "GaugeFixer", lr: float, want_grad: bool = False):
+        """Returns (F(U^{g0}) before the step, parameter gradient of -F or None)."""
+        F = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32) if want_grad else None
+        self._check(self.lib.lgf_net_train_step(self.n, gf.h, float(lr), ctypes.byref(F),
+                                                _as_ptr(g) if want_grad else None), "lgf_net_train_step")
+        return F.value, g
+
+    def warm_start(self, gf: "GaugeFixer"):
+        self._check(self.lib.lgf_net_warm_start(self.n, gf.h), "lgf_net_warm_start")
+
+    def close(self):
+        if getattr(self, "n", None):
+            self.lib.lgf_net_destroy(self.n)
+            self.n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -60,6 +60,15 @@ SIGNATURES = {
     "lgf_batch_fix": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P, _P]),
     "lgf_batch_last_error": (ctypes.c_char_p, [_P]),
     "lgf_autotune": (ctypes.c_int, [_P, ctypes.c_int, _IP]),
+    "lgf_net_param_count": (ctypes.c_int, []),
+    "lgf_net_create": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(_P)]),
+    "lgf_net_destroy": (ctypes.c_int, [_P]),
+    "lgf_net_get_params": (ctypes.c_int, [_P, _P]),
+    "lgf_net_set_params": (ctypes.c_int, [_P, _P]),
+    "lgf_net_forward": (ctypes.c_int, [_P, _P, _P]),
+    "lgf_net_train_step": (ctypes.c_int, [_P, _P, ctypes.c_double, _DP, _P]),
+    "lgf_net_warm_start": (ctypes.c_int, [_P, _P]),
+    "lgf_net_last_error": (ctypes.c_char_p, [_P]),
 }
 LGF_NUM_KERNELS = 9
 

@@ -1,0 +1,537 @@
+// Learned warm start: a 4D convolutional network that predicts, from the
+// loaded links, an initial gauge transformation g0 = exp(sum_a c_a i
+// lambda_a / 2) per site; the plain method then starts from G = g0 (gauge
+// representation) and remains the judge through theta and F.
+//
+// Network: three 3^4-tap periodic convolutions, 48 -> 32 -> 32 -> 8 channels,
+// ReLU after the first two; BF16 weights and activations, FP32 accumulation
+// on the tensor cores (warp-level mma on 16x16x16 BF16 tiles), FP32 master
+// weights and Adam moments.  Training signal: the loss is -F(U^{g0}) (the
+// method's own functional), whose derivative along left translations of
+// g0(x) is the projection of the transformed links' gradient Delta'(x) onto
+// the su(3) generators; Delta' comes from the gauge-representation gradient
+// kernel with G = g0.
+//
+// Layouts: activations [site][channel] (BF16, channels fastest), weights
+// [tap][in][out] with tap = ((dt*3 + dz)*3 + dy)*3 + dx, offsets d - 1.
+#include <cuda_bf16.h>
+#include <mma.h>
+
+#include "lgf_kernels.cuh"
+
+namespace lgf {
+namespace warm {
+
+using bf16 = __nv_bfloat16;
+namespace wm = nvcuda::wmma;
+
+constexpr int kFeat = 48;  // 32 link coefficients + 6 plaquettes + 10 zeros
+constexpr int kHid = 32;
+constexpr int kOut = 8;
+constexpr int kOutPad = 16;  // the last layer is computed 16 wide, 8 used
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// features
+// ---------------------------------------------------------------------------
+// su(3) coefficients of the traceless anti-Hermitian part of U, in the
+// Gell-Mann basis with generators i lambda_a / 2 (c_a = -i Tr lambda_a A):
+// written out entry by entry.
+__device__ __forceinline__ void su3_coeffs(const M3<float>& u, float* c) {
+  c[0] = u.e[0][1].im + u.e[1][0].im;
+  c[1] = u.e[0][1].re - u.e[1][0].re;
+  c[2] = u.e[0][0].im - u.e[1][1].im;
+  c[3] = u.e[0][2].im + u.e[2][0].im;
+  c[4] = u.e[0][2].re - u.e[2][0].re;
+  c[5] = u.e[1][2].im + u.e[2][1].im;
+  c[6] = u.e[1][2].re - u.e[2][1].re;
+  c[7] = (u.e[0][0].im + u.e[1][1].im - 2.0f * u.e[2][2].im) * 0.57735026918962576451f;  // 1/sqrt(3)
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_features(const cx<float>* __restrict__ U, bf16* __restrict__ x,
+                                                  const Geom geo) {
+  const int V = (int)geo.V;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  int c[4];
+  site_coords_i(geo.L, s, c);
+  float f[kFeat];
+#pragma unroll
+  for (int i = 0; i < kFeat; ++i) f[i] = 0.0f;
+  M3<float> u[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    u[mu] = load_m3i<float, NC>(U + mu * NC * V, V, s);
+    su3_coeffs(u[mu], f + 8 * mu);
+  }
+  int k = 32;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+    for (int nu = mu + 1; nu < 4; ++nu) {
+      const int sm = c[mu] < geo.L[mu] - 1 ? s + (int)geo.stride[mu] : s - (geo.L[mu] - 1) * (int)geo.stride[mu];
+      const int sn = c[nu] < geo.L[nu] - 1 ? s + (int)geo.stride[nu] : s - (geo.L[nu] - 1) * (int)geo.stride[nu];
+      const M3<float> un = load_m3i<float, NC>(U + nu * NC * V, V, sm);  // U_nu(x + mu)
+      const M3<float> um = load_m3i<float, NC>(U + mu * NC * V, V, sn);  // U_mu(x + nu)
+      M3<float> w1, w2;
+      mm<float, 3>(w1, u[mu], un);
+      mm<float, 3>(w2, u[nu], um);
+      // Re Tr(w1 w2^dag) = sum Re(w1_ij conj(w2_ij))
+      float tr = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) tr += w1.e[i][j].re * w2.e[i][j].re + w1.e[i][j].im * w2.e[i][j].im;
+      f[k++] = tr * (1.0f / 3.0f);
+    }
+  bf16* out = x + (size_t)s * kFeat;
+#pragma unroll
+  for (int i = 0; i < kFeat; i += 2) {
+    *reinterpret_cast<__nv_bfloat162*>(out + i) = __floats2bfloat162_rn(f[i], f[i + 1]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// g0 = exp(sum_a c_a i lambda_a / 2): Taylor series after scaling by 2^-s
+// (norm below 1/2), s squarings, then reunitarisation.  Output: NC planes
+// (the layout of the handle's accumulated transformation G).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ M3<float> algebra(const float* c) {
+  const float r3 = 0.57735026918962576451f;
+  M3<float> X;
+  // X = (i/2) sum_a c_a lambda_a
+  X.e[0][0] = mk<float>(0.f, 0.5f * (c[2] + r3 * c[7]));
+  X.e[1][1] = mk<float>(0.f, 0.5f * (-c[2] + r3 * c[7]));
+  X.e[2][2] = mk<float>(0.f, 0.5f * (-2.f * r3 * c[7]));
+  X.e[0][1] = mk<float>(0.5f * c[1], 0.5f * c[0]);   // (i/2)(c1 - i c2)
+  X.e[1][0] = mk<float>(-0.5f * c[1], 0.5f * c[0]);  // (i/2)(c1 + i c2)
+  X.e[0][2] = mk<float>(0.5f * c[4], 0.5f * c[3]);
+  X.e[2][0] = mk<float>(-0.5f * c[4], 0.5f * c[3]);
+  X.e[1][2] = mk<float>(0.5f * c[6], 0.5f * c[5]);
+  X.e[2][1] = mk<float>(-0.5f * c[6], 0.5f * c[5]);
+  return X;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_expmap(const float* __restrict__ cin, int ldc, cx<float>* __restrict__ G,
+                                                int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  float c[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) c[a] = cin[(size_t)s * ldc + a];
+  M3<float> X = algebra(c);
+  float n2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n2 += norm2(X.e[i][j]);
+  int sq = 0;
+  float scl = 1.0f;
+  while (n2 * scl * scl > 0.25f && sq < 30) {
+    scl *= 0.5f;
+    ++sq;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) X.e[i][j] = scale(X.e[i][j], scl);
+  // Horner: E = I + X/1 (I + X/2 (... (I + X/10)))
+  M3<float> E;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E.e[i][j] = mk<float>(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll 1
+  for (int k = 10; k >= 1; --k) {
+    M3<float> T;
+    mm<float, 3>(T, X, E);
+    const float inv = 1.0f / (float)k;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) E.e[i][j] = mk<float>((i == j ? 1.f : 0.f) + inv * T.e[i][j].re, inv * T.e[i][j].im);
+  }
+  for (int q = 0; q < sq; ++q) {
+    M3<float> T;
+    mm<float, 3>(T, E, E);
+    E = T;
+  }
+  reunitarize(E);
+#pragma unroll
+  for (int q = 0; q < NC; ++q) G[q * V + s] = E.e[q / 3][q % 3];
+}
+
+// ---------------------------------------------------------------------------
+// training signal: dL/dc_a = -<i lambda_a / 2, Delta'> / (24 V) from the
+// packed gradient D of the transformed links; written as BF16 [V][16]
+// (channels 8..15 zero) scaled by `gain` (a power of two keeping the BF16
+// values in range; the optimiser is scale invariant).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_signal(const cx<float>* __restrict__ D, int V, float coef,
+                                                bf16* __restrict__ gc) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const cx<float> d01 = D[s], d02 = D[V + s], d12 = D[2 * V + s], dd = D[3 * V + s];
+  float p[16];
+  p[0] = d01.im;
+  p[1] = d01.re;
+  p[2] = 0.5f * (dd.re - dd.im);
+  p[3] = d02.im;
+  p[4] = d02.re;
+  p[5] = d12.im;
+  p[6] = d12.re;
+  p[7] = 0.86602540378443864676f * (dd.re + dd.im);  // sqrt(3)/2
+#pragma unroll
+  for (int a = 8; a < 16; ++a) p[a] = 0.f;
+  bf16* out = gc + (size_t)s * kOutPad;
+#pragma unroll
+  for (int a = 0; a < 16; a += 2) *reinterpret_cast<__nv_bfloat162*>(out + a) = __floats2bfloat162_rn(coef * p[a], coef * p[a + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// convolutions on the tensor cores
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapc(int c, int d, int L) {
+  int v = c + d;
+  v = v < 0 ? v + L : v;
+  return v >= L ? v - L : v;
+}
+
+// neighbour of site s (coordinates c) at tap offset (sign * (d - 1))
+__device__ __forceinline__ int tap_site(const Geom& geo, const int c[4], int tap, int sign) {
+  const int d0 = sign * (tap % 3 - 1), d1 = sign * ((tap / 3) % 3 - 1);
+  const int d2 = sign * ((tap / 9) % 3 - 1), d3 = sign * (tap / 27 - 1);
+  return wrapc(c[0], d0, geo.L[0]) +
+         geo.L[0] * (wrapc(c[1], d1, geo.L[1]) + geo.L[1] * (wrapc(c[2], d2, geo.L[2]) + geo.L[2] * wrapc(c[3], d3, geo.L[3])));
+}
+
+// y[s, o] = act(b[o] + sum_tap sum_i W[tap, i, o] x[s + off(tap), i]); one
+// warp per 16 consecutive sites (V is a multiple of 16), 4 warps per block.
+// Optionally also the FP32 result (yf, [V][COUT]).
+template <int CIN, int COUT, bool RELU>
+__global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ x, const bf16* __restrict__ W,
+                                                  const float* __restrict__ b, bf16* __restrict__ y,
+                                                  float* __restrict__ yf, const Geom geo) {
+  __shared__ __align__(32) bf16 sA[4][16 * 16];
+  __shared__ __align__(32) float sC[4][16 * COUT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int V = (int)geo.V;
+  const int s0 = (blockIdx.x * 4 + warp) * 16;
+  if (s0 >= V) return;  // warp-uniform; only warp-level synchronisation below
+  const int row = lane >> 1, half = lane & 1;
+  const int s = s0 + row;
+  int c[4];
+  site_coords_i(geo.L, s, c);
+  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[COUT / 16];
+#pragma unroll
+  for (int n = 0; n < COUT / 16; ++n) wm::fill_fragment(acc[n], 0.0f);
+  for (int tap = 0; tap < 81; ++tap) {
+    const int nb = tap_site(geo, c, tap, +1);
+#pragma unroll
+    for (int k0 = 0; k0 < CIN; k0 += 16) {
+      *reinterpret_cast<uint4*>(&sA[warp][row * 16 + half * 8]) =
+          *reinterpret_cast<const uint4*>(x + (size_t)nb * CIN + k0 + half * 8);
+      __syncwarp();
+      wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> a;
+      wm::load_matrix_sync(a, &sA[warp][0], 16);
+#pragma unroll
+      for (int n = 0; n < COUT / 16; ++n) {
+        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> bm;
+        wm::load_matrix_sync(bm, W + ((size_t)tap * CIN + k0) * COUT + n * 16, COUT);
+        wm::mma_sync(acc[n], a, bm, acc[n]);
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < COUT / 16; ++n) wm::store_matrix_sync(&sC[warp][n * 16], acc[n], COUT, wm::mem_row_major);
+  __syncwarp();
+#pragma unroll
+  for (int o = half * (COUT / 2); o < (half + 1) * (COUT / 2); ++o) {
+    float v = sC[warp][row * COUT + o] + b[o];
+    if (RELU) v = fmaxf(v, 0.0f);
+    y[(size_t)s * COUT + o] = __float2bfloat16_rn(v);
+    if (yf != nullptr) yf[(size_t)s * COUT + o] = v;
+  }
+}
+
+// gx[s, i] = mask(s, i) * sum_tap sum_o W[tap, i, o] gy[s - off(tap), o], with
+// mask = (a[s, i] > 0) when a is given (the ReLU of the layer below).
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_conv_bwd_data(const bf16* __restrict__ gy, const bf16* __restrict__ W,
+                                                       const bf16* __restrict__ a, bf16* __restrict__ gx,
+                                                       const Geom geo) {
+  __shared__ __align__(32) bf16 sA[4][16 * 16];
+  __shared__ __align__(32) float sC[4][16 * CI];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int V = (int)geo.V;
+  const int s0 = (blockIdx.x * 4 + warp) * 16;
+  if (s0 >= V) return;
+  const int row = lane >> 1, half = lane & 1;
+  const int s = s0 + row;
+  int c[4];
+  site_coords_i(geo.L, s, c);
+  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[CI / 16];
+#pragma unroll
+  for (int n = 0; n < CI / 16; ++n) wm::fill_fragment(acc[n], 0.0f);
+  for (int tap = 0; tap < 81; ++tap) {
+    const int nb = tap_site(geo, c, tap, -1);
+#pragma unroll
+    for (int k0 = 0; k0 < CO; k0 += 16) {
+      *reinterpret_cast<uint4*>(&sA[warp][row * 16 + half * 8]) =
+          *reinterpret_cast<const uint4*>(gy + (size_t)nb * CO + k0 + half * 8);
+      __syncwarp();
+      wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> am;
+      wm::load_matrix_sync(am, &sA[warp][0], 16);
+#pragma unroll
+      for (int n = 0; n < CI / 16; ++n) {
+        // B[k = o][n = i] = W[tap, i, o]: column-major with leading dimension CO
+        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::col_major> bm;
+        wm::load_matrix_sync(bm, W + ((size_t)tap * CI + n * 16) * CO + k0, CO);
+        wm::mma_sync(acc[n], am, bm, acc[n]);
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < CI / 16; ++n) wm::store_matrix_sync(&sC[warp][n * 16], acc[n], CI, wm::mem_row_major);
+  __syncwarp();
+#pragma unroll
+  for (int i = half * (CI / 2); i < (half + 1) * (CI / 2); ++i) {
+    float v = sC[warp][row * CI + i];
+    if (a != nullptr && !(__bfloat162float(a[(size_t)s * CI + i]) > 0.0f)) v = 0.0f;
+    gx[(size_t)s * CI + i] = __float2bfloat16_rn(v);
+  }
+}
+
+// gW[tap, i, o] += sum_s x[s + off(tap), i] gy[s, o]: block (chunk group,
+// tap); each warp accumulates 16-site chunks on the tensor cores and adds its
+// tile to gW with FP32 atomics (so the sum order, and its last bits, vary).
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_conv_bwd_weight(const bf16* __restrict__ x, const bf16* __restrict__ gy,
+                                                         float* __restrict__ gW, const Geom geo, int chunks_per_warp) {
+  __shared__ __align__(32) bf16 sX[4][16 * CI];
+  __shared__ __align__(32) float sC[4][CI * CO];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int V = (int)geo.V;
+  const int tap = blockIdx.y;
+  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[CI / 16][CO / 16];
+#pragma unroll
+  for (int m = 0; m < CI / 16; ++m)
+#pragma unroll
+    for (int n = 0; n < CO / 16; ++n) wm::fill_fragment(acc[m][n], 0.0f);
+  const int first = (blockIdx.x * 4 + warp) * chunks_per_warp;
+  for (int ch = 0; ch < chunks_per_warp; ++ch) {
+    const int s0 = (first + ch) * 16;
+    if (s0 >= V) break;
+    // stage the 16 neighbour rows of x (CI channels each)
+    for (int e = lane; e < 16 * (CI / 8); e += 32) {
+      const int r = e / (CI / 8), q = e % (CI / 8);
+      int c[4];
+      site_coords_i(geo.L, s0 + r, c);
+      const int nb = tap_site(geo, c, tap, +1);
+      *reinterpret_cast<uint4*>(&sX[warp][r * CI + q * 8]) =
+          *reinterpret_cast<const uint4*>(x + (size_t)nb * CI + q * 8);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < CI / 16; ++m) {
+      // A[m = i][k = site] = sX[site][i]: column-major, leading dimension CI
+      wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::col_major> am;
+      wm::load_matrix_sync(am, &sX[warp][m * 16], CI);
+#pragma unroll
+      for (int n = 0; n < CO / 16; ++n) {
+        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> bm;
+        wm::load_matrix_sync(bm, gy + (size_t)s0 * CO + n * 16, CO);
+        wm::mma_sync(acc[m][n], am, bm, acc[m][n]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int m = 0; m < CI / 16; ++m)
+#pragma unroll
+    for (int n = 0; n < CO / 16; ++n)
+      wm::store_matrix_sync(&sC[warp][(m * 16) * CO + n * 16], acc[m][n], CO, wm::mem_row_major);
+  __syncwarp();
+  float* dst = gW + (size_t)tap * CI * CO;
+  for (int e = lane; e < CI * CO; e += 32) atomicAdd(dst + e, sC[warp][e]);
+}
+
+// gb[o] += sum_s gy[s, o]
+template <int CO>
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16* __restrict__ gy, float* __restrict__ gb, int V) {
+  __shared__ float part[256 / CO][CO];
+  const int o = threadIdx.x % CO, r = threadIdx.x / CO;
+  constexpr int R = 256 / CO;
+  float acc = 0.f;
+  for (int s = blockIdx.x * R + r; s < V; s += gridDim.x * R) acc += __bfloat162float(gy[(size_t)s * CO + o]);
+  part[r][o] = acc;
+  __syncthreads();
+  if (r == 0) {
+    float t = 0.f;
+    for (int k = 0; k < R; ++k) t += part[k][o];
+    atomicAdd(gb + o, t);
+  }
+}
+
+// Adam on the FP32 master parameters; bf16 copies of the weights refreshed.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float c1, float c2, float eps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+// bf16 weights from the FP32 parameters; the last layer is widened from 8 to
+// 16 outputs with zero columns.
+__global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ W1, bf16* __restrict__ W2,
+                               bf16* __restrict__ W3, float* __restrict__ b1, float* __restrict__ b2,
+                               float* __restrict__ b3) {
+  const int n1 = 81 * kFeat * kHid, n2 = 81 * kHid * kHid, n3 = 81 * kHid * kOutPad;
+  const int o_b1 = n1, o_W2 = o_b1 + kHid, o_b2 = o_W2 + n2, o_W3 = o_b2 + kHid, o_b3 = o_W3 + 81 * kHid * kOut;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3 + kHid * 2 + kOutPad;
+       i += gridDim.x * blockDim.x) {
+    if (i < n1) {
+      W1[i] = __float2bfloat16_rn(p[i]);
+    } else if (i < n1 + n2) {
+      const int j = i - n1;
+      W2[j] = __float2bfloat16_rn(p[o_W2 + j]);
+    } else if (i < n1 + n2 + n3) {
+      const int j = i - n1 - n2;  // [tap][i][16]
+      const int o = j % kOutPad, ti = j / kOutPad;
+      W3[j] = __float2bfloat16_rn(o < kOut ? p[o_W3 + ti * kOut + o] : 0.f);
+    } else {
+      const int j = i - n1 - n2 - n3;
+      if (j < kHid)
+        b1[j] = p[o_b1 + j];
+      else if (j < 2 * kHid)
+        b2[j - kHid] = p[o_b2 + j - kHid];
+      else
+        b3[j - 2 * kHid] = (j - 2 * kHid) < kOut ? p[o_b3 + j - 2 * kHid] : 0.f;
+    }
+  }
+}
+
+// flat gradient (parameter layout) from the padded last-layer gradient
+__global__ void k_unpad_grad3(const float* __restrict__ gW3p, const float* __restrict__ gb3p, float* __restrict__ gW3,
+                              float* __restrict__ gb3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 81 * kHid * kOut) gW3[i] = gW3p[(i / kOut) * kOutPad + i % kOut];
+  if (i < kOut) gb3[i] = gb3p[i];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned nb128(int n) { return (unsigned)((n + 127) / 128); }
+
+cudaError_t launch_features(int nc, const void* U0, void* x, const Geom& geo, cudaStream_t s) {
+  const int V = (int)geo.V;
+  if (nc == 9)
+    k_features<9><<<nb128(V), 128, 0, s>>>(static_cast<const cx<float>*>(U0), static_cast<bf16*>(x), geo);
+  else
+    k_features<6><<<nb128(V), 128, 0, s>>>(static_cast<const cx<float>*>(U0), static_cast<bf16*>(x), geo);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_expmap(int nc, const float* c, int ldc, void* G, int V, cudaStream_t s) {
+  if (nc == 9)
+    k_expmap<9><<<nb128(V), 128, 0, s>>>(c, ldc, static_cast<cx<float>*>(G), V);
+  else
+    k_expmap<6><<<nb128(V), 128, 0, s>>>(c, ldc, static_cast<cx<float>*>(G), V);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_signal(const void* D, int V, float coef, void* gc, cudaStream_t s) {
+  k_signal<<<nb128(V), 128, 0, s>>>(static_cast<const cx<float>*>(D), V, coef, static_cast<bf16*>(gc));
+  return cudaPeekAtLastError();
+}
+
+// layer 1: 48 -> 32 (ReLU), 2: 32 -> 32 (ReLU), 3: 32 -> 16 (8 used, FP32 copy)
+cudaError_t launch_conv_fwd(int layer, const void* x, const void* W, const float* b, void* y, float* yf,
+                            const Geom& geo, cudaStream_t s) {
+  const unsigned nb = (unsigned)((geo.V / 16 + 3) / 4);
+  const bf16* xp = static_cast<const bf16*>(x);
+  const bf16* Wp = static_cast<const bf16*>(W);
+  bf16* yp = static_cast<bf16*>(y);
+  if (layer == 1)
+    k_conv_fwd<kFeat, kHid, true><<<nb, 128, 0, s>>>(xp, Wp, b, yp, yf, geo);
+  else if (layer == 2)
+    k_conv_fwd<kHid, kHid, true><<<nb, 128, 0, s>>>(xp, Wp, b, yp, yf, geo);
+  else
+    k_conv_fwd<kHid, kOutPad, false><<<nb, 128, 0, s>>>(xp, Wp, b, yp, yf, geo);
+  return cudaPeekAtLastError();
+}
+
+// gradient with respect to the input of layer 3 (32 <- 16) or 2 (32 <- 32),
+// masked by the ReLU of the layer below (a)
+cudaError_t launch_conv_bwd_data(int layer, const void* gy, const void* W, const void* a, void* gx,
+                                 const Geom& geo, cudaStream_t s) {
+  const unsigned nb = (unsigned)((geo.V / 16 + 3) / 4);
+  const bf16* gyp = static_cast<const bf16*>(gy);
+  const bf16* Wp = static_cast<const bf16*>(W);
+  const bf16* ap = static_cast<const bf16*>(a);
+  bf16* gxp = static_cast<bf16*>(gx);
+  if (layer == 3)
+    k_conv_bwd_data<kHid, kOutPad><<<nb, 128, 0, s>>>(gyp, Wp, ap, gxp, geo);
+  else
+    k_conv_bwd_data<kHid, kHid><<<nb, 128, 0, s>>>(gyp, Wp, ap, gxp, geo);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_conv_bwd_weight(int layer, const void* x, const void* gy, float* gW, const Geom& geo,
+                                   cudaStream_t s) {
+  const int chunks = (int)(geo.V / 16);
+  const int cpw = 8;  // 16-site chunks per warp
+  dim3 grid((unsigned)((chunks + 4 * cpw - 1) / (4 * cpw)), 81);
+  const bf16* xp = static_cast<const bf16*>(x);
+  const bf16* gyp = static_cast<const bf16*>(gy);
+  if (layer == 1)
+    k_conv_bwd_weight<kFeat, kHid><<<grid, 128, 0, s>>>(xp, gyp, gW, geo, cpw);
+  else if (layer == 2)
+    k_conv_bwd_weight<kHid, kHid><<<grid, 128, 0, s>>>(xp, gyp, gW, geo, cpw);
+  else
+    k_conv_bwd_weight<kHid, kOutPad><<<grid, 128, 0, s>>>(xp, gyp, gW, geo, cpw);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_bias_grad(int co, const void* gy, float* gb, int V, cudaStream_t s) {
+  const bf16* g = static_cast<const bf16*>(gy);
+  if (co == kHid)
+    k_bias_grad<kHid><<<120, 256, 0, s>>>(g, gb, V);
+  else
+    k_bias_grad<kOutPad><<<120, 256, 0, s>>>(g, gb, V);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float c1,
+                        float c2, float eps, cudaStream_t s) {
+  k_adam<<<(n + 255) / 256, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, c1, c2, eps);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_pack_weights(const float* p, void* W1, void* W2, void* W3, float* b1, float* b2, float* b3,
+                                cudaStream_t s) {
+  k_pack_weights<<<256, 256, 0, s>>>(p, static_cast<bf16*>(W1), static_cast<bf16*>(W2), static_cast<bf16*>(W3), b1,
+                                     b2, b3);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_unpad_grad3(const float* gW3p, const float* gb3p, float* gW3, float* gb3, cudaStream_t s) {
+  k_unpad_grad3<<<nb128(81 * kHid * kOut), 128, 0, s>>>(gW3p, gb3p, gW3, gb3);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace warm
+}  // namespace lgf

@@ -655,6 +655,135 @@ int run_members(lgf_batch b, const std::vector<int>& members, const std::vector<
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// learned warm start
+// ---------------------------------------------------------------------------
+struct lgf_net_ctx {
+  int device = 0;
+  float* p = nullptr;  // FP32 master parameters [W1 b1 W2 b2 W3 b3]
+  float* m = nullptr;
+  float* v = nullptr;
+  float* g = nullptr;  // gradient in the same layout
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  void* W3 = nullptr;  // bf16, last layer 16 wide
+  float* b1 = nullptr;
+  float* b2 = nullptr;
+  float* b3 = nullptr;
+  float* gW3p = nullptr;  // padded last-layer gradient
+  float* gb3p = nullptr;
+  int64_t vmax = 0;
+  void *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *y3 = nullptr, *gc = nullptr, *ga2 = nullptr, *ga1 = nullptr;
+  float* c = nullptr;  // FP32 [V][16] outputs of the last layer
+  void* G0 = nullptr;  // FP32 9 planes: g0 for the training signal
+  long long step = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+  std::string err;
+};
+
+namespace {
+
+constexpr int kW1 = 81 * 48 * 32, kW2 = 81 * 32 * 32, kW3 = 81 * 32 * 8;
+constexpr int kOB1 = kW1, kOW2 = kOB1 + 32, kOB2 = kOW2 + kW2, kOW3 = kOB2 + 32, kOB3 = kOW3 + kW3;
+
+int nfail(lgf_net n, int code, const std::string& msg) {
+  if (n) n->err = msg;
+  else g_last_create_error = msg;
+  return code;
+}
+
+#define LGF_NCUDA(n, call)                                                                                  \
+  do {                                                                                                      \
+    cudaError_t e_ = (call);                                                                                \
+    if (e_ != cudaSuccess) return nfail((n), LGF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* net_alloc(lgf_net n, size_t bytes) {
+  void* q = nullptr;
+  if (g_alloc.alloc) {
+    q = g_alloc.alloc(bytes, n->device, nullptr, g_alloc.user);
+  } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    q = nullptr;
+  }
+  if (q) n->allocs.push_back({q, bytes});
+  return q;
+}
+
+void net_free(lgf_net n, void* q) {
+  for (size_t i = 0; i < n->allocs.size(); ++i)
+    if (n->allocs[i].first == q) {
+      if (g_alloc.free_fn)
+        g_alloc.free_fn(q, n->allocs[i].second, n->device, nullptr, g_alloc.user);
+      else
+        cudaFree(q);
+      n->allocs.erase(n->allocs.begin() + i);
+      return;
+    }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) of a counter, then Box-Muller
+uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double normal_at(uint64_t seed, uint64_t i) {
+  const uint64_t k = seed * 0x100000000ull + i;
+  const double u1 = ((double)(splitmix64(2 * k) >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(splitmix64(2 * k + 1) >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+int net_pack(lgf_net n, cudaStream_t s) {
+  LGF_NCUDA(n, warm::launch_pack_weights(n->p, n->W1, n->W2, n->W3, n->b1, n->b2, n->b3, s));
+  return LGF_OK;
+}
+
+int net_buffers(lgf_net n, int64_t V) {
+  if (V <= n->vmax) return LGF_OK;
+  for (void* q : {n->x0, n->a1, n->a2, n->y3, n->gc, n->ga2, n->ga1, (void*)n->c, n->G0})
+    if (q) net_free(n, q);
+  const size_t b = 2;  // bytes per bf16
+  n->x0 = net_alloc(n, (size_t)V * 48 * b);
+  n->a1 = net_alloc(n, (size_t)V * 32 * b);
+  n->a2 = net_alloc(n, (size_t)V * 32 * b);
+  n->y3 = net_alloc(n, (size_t)V * 16 * b);
+  n->gc = net_alloc(n, (size_t)V * 16 * b);
+  n->ga2 = net_alloc(n, (size_t)V * 32 * b);
+  n->ga1 = net_alloc(n, (size_t)V * 32 * b);
+  n->c = static_cast<float*>(net_alloc(n, (size_t)V * 16 * sizeof(float)));
+  n->G0 = net_alloc(n, (size_t)V * 9 * 8);
+  if (!n->x0 || !n->a1 || !n->a2 || !n->y3 || !n->gc || !n->ga2 || !n->ga1 || !n->c || !n->G0) {
+    n->vmax = 0;
+    return nfail(n, LGF_ERR_OOM, "device allocation of the network activations failed");
+  }
+  n->vmax = V;
+  return LGF_OK;
+}
+
+int net_check_handle(lgf_net n, lgf_handle h) {
+  if (!n || !h) return LGF_ERR_ARG;
+  if (!h->mixed || !h->e32.grep || h->cur != &h->e32)
+    return nfail(n, LGF_ERR_ARG, "the warm start needs an FP32 handle in gauge representation before its FP64 tail");
+  if (!h->loaded) return nfail(n, LGF_ERR_ARG, "no links loaded");
+  if (h->V % 16 != 0) return nfail(n, LGF_ERR_ARG, "the lattice volume must be a multiple of 16");
+  return net_buffers(n, h->V);
+}
+
+int net_forward(lgf_net n, lgf_handle h) {
+  cudaStream_t s = h->stream;
+  LGF_NCUDA(n, warm::launch_features(h->e32.nc, h->e32.U, n->x0, h->geo, s));
+  LGF_NCUDA(n, warm::launch_conv_fwd(1, n->x0, n->W1, n->b1, n->a1, nullptr, h->geo, s));
+  LGF_NCUDA(n, warm::launch_conv_fwd(2, n->a1, n->W2, n->b2, n->a2, nullptr, h->geo, s));
+  LGF_NCUDA(n, warm::launch_conv_fwd(3, n->a2, n->W3, n->b3, n->y3, n->c, h->geo, s));
+  h->launches += 4;
+  return LGF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lgf_set_allocator(lgf_alloc_fn alloc, lgf_free_fn free_fn, void* user) {
@@ -1157,6 +1286,153 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
 }
 
 const char* lgf_batch_last_error(lgf_batch b) { return b ? b->err.c_str() : ""; }
+
+int lgf_net_param_count(void) { return warm::kParams; }
+
+int lgf_net_create(unsigned long long seed, lgf_net* out) {
+  if (!out) return LGF_ERR_ARG;
+  *out = nullptr;
+  lgf_net_ctx* n = new (std::nothrow) lgf_net_ctx();
+  if (!n) return nfail(nullptr, LGF_ERR_OOM, "host allocation failed");
+  if (cudaGetDevice(&n->device) != cudaSuccess) {
+    delete n;
+    return nfail(nullptr, LGF_ERR_CUDA, "no CUDA device");
+  }
+  const size_t P = warm::kParams;
+  n->p = static_cast<float*>(net_alloc(n, P * 4));
+  n->m = static_cast<float*>(net_alloc(n, P * 4));
+  n->v = static_cast<float*>(net_alloc(n, P * 4));
+  n->g = static_cast<float*>(net_alloc(n, P * 4));
+  n->W1 = net_alloc(n, (size_t)kW1 * 2);
+  n->W2 = net_alloc(n, (size_t)kW2 * 2);
+  n->W3 = net_alloc(n, (size_t)81 * 32 * 16 * 2);
+  n->b1 = static_cast<float*>(net_alloc(n, 32 * 4));
+  n->b2 = static_cast<float*>(net_alloc(n, 32 * 4));
+  n->b3 = static_cast<float*>(net_alloc(n, 16 * 4));
+  n->gW3p = static_cast<float*>(net_alloc(n, (size_t)81 * 32 * 16 * 4));
+  n->gb3p = static_cast<float*>(net_alloc(n, 16 * 4));
+  if (!n->p || !n->m || !n->v || !n->g || !n->W1 || !n->W2 || !n->W3 || !n->b1 || !n->b2 || !n->b3 || !n->gW3p ||
+      !n->gb3p) {
+    std::string msg = "device allocation of the network failed";
+    lgf_net_destroy(n);
+    return nfail(nullptr, LGF_ERR_OOM, msg);
+  }
+  // He-normal initialisation; the last layer 100x smaller so that g0 starts
+  // close to the identity (the warm start starts as "no warm start")
+  std::vector<float> hp(P, 0.0f);
+  const double s1 = sqrt(2.0 / (81.0 * 48)), s2 = sqrt(2.0 / (81.0 * 32)), s3 = 0.01 * sqrt(1.0 / (81.0 * 32));
+  for (int i = 0; i < kW1; ++i) hp[i] = (float)(s1 * normal_at(seed, i));
+  for (int i = 0; i < kW2; ++i) hp[kOW2 + i] = (float)(s2 * normal_at(seed, kOW2 + i));
+  for (int i = 0; i < kW3; ++i) hp[kOW3 + i] = (float)(s3 * normal_at(seed, kOW3 + i));
+  int rc = lgf_net_set_params(n, hp.data());
+  if (rc) {
+    std::string msg = n->err;
+    lgf_net_destroy(n);
+    return nfail(nullptr, rc, msg);
+  }
+  *out = n;
+  return LGF_OK;
+}
+
+int lgf_net_destroy(lgf_net n) {
+  if (!n) return LGF_ERR_ARG;
+  cudaDeviceSynchronize();
+  while (!n->allocs.empty()) net_free(n, n->allocs.back().first);
+  delete n;
+  return LGF_OK;
+}
+
+int lgf_net_get_params(lgf_net n, float* host) {
+  if (!n || !host) return LGF_ERR_ARG;
+  LGF_NCUDA(n, cudaMemcpy(host, n->p, (size_t)warm::kParams * 4, cudaMemcpyDeviceToHost));
+  return LGF_OK;
+}
+
+int lgf_net_set_params(lgf_net n, const float* host) {
+  if (!n || !host) return LGF_ERR_ARG;
+  const size_t P = warm::kParams;
+  LGF_NCUDA(n, cudaMemcpy(n->p, host, P * 4, cudaMemcpyHostToDevice));
+  LGF_NCUDA(n, cudaMemset(n->m, 0, P * 4));
+  LGF_NCUDA(n, cudaMemset(n->v, 0, P * 4));
+  n->step = 0;
+  int rc = net_pack(n, nullptr);
+  if (rc) return rc;
+  LGF_NCUDA(n, cudaDeviceSynchronize());
+  return LGF_OK;
+}
+
+int lgf_net_forward(lgf_net n, lgf_handle h, float* host_c) {
+  int rc = net_check_handle(n, h);
+  if (!rc) rc = net_forward(n, h);
+  if (rc) return rc;
+  if (host_c) {
+    // [V][16] FP32 on the device -> [V][8] on the host
+    LGF_NCUDA(n, cudaMemcpy2DAsync(host_c, 8 * sizeof(float), n->c, 16 * sizeof(float), 8 * sizeof(float),
+                                   (size_t)h->V, cudaMemcpyDeviceToHost, h->stream));
+  }
+  LGF_NCUDA(n, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+int lgf_net_train_step(lgf_net n, lgf_handle h, double lr, double* F_out, float* host_grad) {
+  int rc = net_check_handle(n, h);
+  if (!rc) rc = net_forward(n, h);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  const int V = (int)h->V;
+  // g0 and the gradient of the transformed links (gauge representation, G = g0)
+  LGF_NCUDA(n, warm::launch_expmap(h->e32.nc, n->c, 16, n->G0, V, s));
+  rc = reset_state(h, -1.0, 0, false);
+  if (rc) return nfail(n, rc, h->err);
+  LGF_NCUDA(n, launch_gradient_grep(h->e32.nc, h->e32.U, n->G0, h->e32.D, h->partial, h->geo, h->st, 0, s));
+  LGF_NCUDA(n, warm::launch_signal(h->e32.D, V, (float)(-1.0 / (24.0 * (double)V)), n->gc, s));
+  const size_t P = warm::kParams;
+  LGF_NCUDA(n, cudaMemsetAsync(n->g, 0, P * 4, s));
+  LGF_NCUDA(n, cudaMemsetAsync(n->gW3p, 0, (size_t)81 * 32 * 16 * 4, s));
+  LGF_NCUDA(n, cudaMemsetAsync(n->gb3p, 0, 16 * 4, s));
+  // layer 3 (a2 -> c)
+  LGF_NCUDA(n, warm::launch_conv_bwd_weight(3, n->a2, n->gc, n->gW3p, h->geo, s));
+  LGF_NCUDA(n, warm::launch_bias_grad(16, n->gc, n->gb3p, V, s));
+  LGF_NCUDA(n, warm::launch_conv_bwd_data(3, n->gc, n->W3, n->a2, n->ga2, h->geo, s));
+  // layer 2 (a1 -> a2)
+  LGF_NCUDA(n, warm::launch_conv_bwd_weight(2, n->a1, n->ga2, n->g + kOW2, h->geo, s));
+  LGF_NCUDA(n, warm::launch_bias_grad(32, n->ga2, n->g + kOB2, V, s));
+  LGF_NCUDA(n, warm::launch_conv_bwd_data(2, n->ga2, n->W2, n->a1, n->ga1, h->geo, s));
+  // layer 1 (x0 -> a1)
+  LGF_NCUDA(n, warm::launch_conv_bwd_weight(1, n->x0, n->ga1, n->g, h->geo, s));
+  LGF_NCUDA(n, warm::launch_bias_grad(32, n->ga1, n->g + kOB1, V, s));
+  LGF_NCUDA(n, warm::launch_unpad_grad3(n->gW3p, n->gb3p, n->g + kOW3, n->g + kOB3, s));
+  h->launches += 14;
+  if (host_grad) LGF_NCUDA(n, cudaMemcpyAsync(host_grad, n->g, P * 4, cudaMemcpyDeviceToHost, s));
+  if (lr > 0.0) {
+    n->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 / (1.0 - pow(b1, (double)n->step)));
+    const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)n->step)));
+    LGF_NCUDA(n, warm::launch_adam(n->p, n->g, n->m, n->v, (int)P, (float)lr, (float)b1, (float)b2, c1, c2, 1e-12f, s));
+    rc = net_pack(n, s);
+    if (rc) return rc;
+    h->launches += 2;
+  }
+  rc = sync_state(h);
+  if (rc) return nfail(n, rc, h->err);
+  if (F_out) *F_out = h->st_host->F;
+  return LGF_OK;
+}
+
+int lgf_net_warm_start(lgf_net n, lgf_handle h) {
+  int rc = net_check_handle(n, h);
+  if (rc) return rc;
+  if (h->total_updates != 0) return nfail(n, LGF_ERR_ARG, "apply the warm start right after lgf_load_links");
+  rc = net_forward(n, h);
+  if (rc) return rc;
+  LGF_NCUDA(n, warm::launch_expmap(h->e32.nc, n->c, 16, h->G, (int)h->V, h->stream));
+  h->launches += 1;
+  LGF_NCUDA(n, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+const char* lgf_net_last_error(lgf_net n) { return n ? n->err.c_str() : g_last_create_error.c_str(); }
 
 int lgf_history(lgf_handle h, double* theta_out, int cap, int* n_out) {
   if (!h) return LGF_ERR_ARG;

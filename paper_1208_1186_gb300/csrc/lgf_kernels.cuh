@@ -96,6 +96,27 @@ cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V,
                          const DevState* st, cudaStream_t s);
 cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s);
 
+// learned warm start (k_warm.cu): features, BF16 tensor-core convolutions,
+// exp map, training signal, Adam
+namespace warm {
+constexpr int kParams = 81 * 48 * 32 + 32 + 81 * 32 * 32 + 32 + 81 * 32 * 8 + 8;
+cudaError_t launch_features(int nc, const void* U0, void* x, const Geom& geo, cudaStream_t s);
+cudaError_t launch_expmap(int nc, const float* c, int ldc, void* G, int V, cudaStream_t s);
+cudaError_t launch_signal(const void* D, int V, float coef, void* gc, cudaStream_t s);
+cudaError_t launch_conv_fwd(int layer, const void* x, const void* W, const float* b, void* y, float* yf,
+                            const Geom& geo, cudaStream_t s);
+cudaError_t launch_conv_bwd_data(int layer, const void* gy, const void* W, const void* a, void* gx,
+                                 const Geom& geo, cudaStream_t s);
+cudaError_t launch_conv_bwd_weight(int layer, const void* x, const void* gy, float* gW, const Geom& geo,
+                                   cudaStream_t s);
+cudaError_t launch_bias_grad(int co, const void* gy, float* gb, int V, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float c1,
+                        float c2, float eps, cudaStream_t s);
+cudaError_t launch_pack_weights(const float* p, void* W1, void* W2, void* W3, float* b1, float* b2, float* b3,
+                                cudaStream_t s);
+cudaError_t launch_unpad_grad3(const float* gW3p, const float* gb3p, float* gW3, float* gb3, cudaStream_t s);
+}  // namespace warm
+
 // text returned by lgf_last_error(NULL) on this host thread
 void set_global_error(const std::string& msg);
 

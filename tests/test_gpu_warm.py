@@ -1,0 +1,172 @@
+"""The learned warm start on the GPU against its FP64 oracle
+(oracle/warm_start_oracle.py).
+
+Tolerances: features, activations and weights are BF16 on the GPU.  The
+oracle side rounds its features, its weights and every activation to BF16 at
+the same points, so what remains is FP32 (GPU) versus FP64 (oracle)
+accumulation and FP32 links: the outputs c agree to ~1e-3 relative (norm),
+and the occasional BF16 rounding-boundary flip of a feature bounds it at 1e-2.
+Gradients pass through BF16 upstream signals as well: each layer's weight
+gradient must agree to 5e-2 relative (norm) and point the same way (cosine
+> 0.99).  A bias gradient is the sum of the upstream gradient over all sites;
+for the last layer that sum telescopes to zero (sum_x Delta(x) = 0 on a
+periodic lattice), so biases are compared against 1e-2 of the sum of the
+absolute values that cancel, not relative to their own size.
+
+Learning rates: Adam moves every weight by about lr per step and ~2600
+weights feed each output coefficient, so lr = 1e-5 keeps the change of g0 per
+step small."""
+import numpy as np
+import pytest
+
+import lgf_inputs as I
+from oracle import lgf_oracle as O
+from oracle import warm_start_oracle as WO
+
+pytestmark = pytest.mark.gpu
+
+N1, N2, N3 = 81 * 48 * 32, 81 * 32 * 32, 81 * 32 * 8
+
+
+@pytest.fixture(scope="module")
+def lgf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1208_1186_gb300 as P
+    from paper_1208_1186_gb300.build import build
+    build()
+    return P
+
+
+def bf16(x):
+    """Round to bfloat16 (nearest even) and back, as the GPU stores."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def unpack(p):
+    p = p.astype(np.float64)
+    o = 0
+    W1 = p[o:o + N1].reshape(81, 48, 32); o += N1
+    b1 = p[o:o + 32]; o += 32
+    W2 = p[o:o + N2].reshape(81, 32, 32); o += N2
+    b2 = p[o:o + 32]; o += 32
+    W3 = p[o:o + N3].reshape(81, 32, 8); o += N3
+    b3 = p[o:o + 8]
+    return [(W1, b1), (W2, b2), (W3, b3)]
+
+
+def oracle_forward_bf16(U32, params):
+    """The oracle network with BF16 storage of features, weights, activations."""
+    (W1, b1), (W2, b2), (W3, b3) = params
+    x0 = bf16(WO.features(U32))
+    z1 = WO.conv(x0, bf16(W1), b1); a1 = bf16(np.maximum(z1, 0))
+    z2 = WO.conv(a1, bf16(W2), b2); a2 = bf16(np.maximum(z2, 0))
+    c = WO.conv(a2, bf16(W3), b3)
+    return c, (x0, z1, a1, z2, a2), [(bf16(W1), b1), (bf16(W2), b2), (bf16(W3), b3)]
+
+
+def _setup(lgf, dims, seed):
+    U = I.synthetic_config(dims, seed=seed, link_scale=0.5)
+    U32 = U.astype(np.complex64).astype(np.complex128)  # the FP32 links the GPU holds
+    gf = lgf.GaugeFixer(dims, "f32")
+    gf.load_links(U)
+    net = lgf.WarmStartNet(seed=seed)
+    rng = np.random.default_rng(seed)
+    p = np.concatenate([0.05 * rng.standard_normal(N1), 0.05 * rng.standard_normal(32),
+                        0.05 * rng.standard_normal(N2), 0.05 * rng.standard_normal(32),
+                        0.05 * rng.standard_normal(N3), 0.05 * rng.standard_normal(8)]).astype(np.float32)
+    net.set_params(p)
+    return U, U32, gf, net, p
+
+
+def relnorm(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_forward_matches_oracle(lgf):
+    dims = (4, 4, 4, 4)
+    U, U32, gf, net, p = _setup(lgf, dims, 11)
+    try:
+        c = net.forward(gf)
+        c_ref, _, _ = oracle_forward_bf16(U32, unpack(p))
+        assert relnorm(c, c_ref) < 1e-2
+    finally:
+        net.close(); gf.close()
+
+
+def test_gradients_match_oracle(lgf):
+    dims = (4, 4, 4, 8)
+    U, U32, gf, net, p = _setup(lgf, dims, 12)
+    try:
+        c = net.forward(gf).astype(np.float64)
+        F, grad = net.train_step(gf, 0.0, want_grad=True)
+        # loss and signal of the GPU's own outputs, in FP64
+        L, gc = WO.loss_and_signal(U32, c)
+        assert F == pytest.approx(-L, rel=1e-5)
+        _, acts, pb = oracle_forward_bf16(U32, unpack(p))
+        x0, z1, a1, z2, a2 = acts
+        # the GPU stores the signal and the upstream gradients in BF16
+        gc16 = bf16(gc)
+        ga2, gW3, gb3 = WO.conv_backward(a2, pb[2][0], gc16)
+        gz2 = bf16(ga2 * (a2 > 0))
+        ga1, gW2, gb2 = WO.conv_backward(a1, pb[1][0], gz2)
+        gz1 = bf16(ga1 * (a1 > 0))
+        _, gW1, gb1 = WO.conv_backward(x0, pb[0][0], gz1)
+        got = unpack(grad)
+        ups = [gz1, gz2, gc16]
+        for (gW, gb), (rW, rb), up in zip(got, [(gW1, gb1), (gW2, gb2), (gW3, gb3)], ups):
+            assert relnorm(gW, rW) < 5e-2
+            cos = float(np.sum(gW * rW) / (np.linalg.norm(gW) * np.linalg.norm(rW)))
+            assert cos > 0.99
+            scale = np.abs(up).sum(axis=(0, 1, 2, 3))[: rb.size]
+            assert np.all(np.abs(gb - rb) <= 1e-2 * scale + 1e-12)
+    finally:
+        net.close(); gf.close()
+
+
+def test_training_raises_F(lgf):
+    dims = (8, 8, 8, 8)
+    U = I.synthetic_config(dims, seed=21, link_scale=0.5)
+    with lgf.GaugeFixer(dims, "f32") as gf:
+        gf.load_links(U)
+        net = lgf.WarmStartNet(seed=3)
+        try:
+            F0, _ = net.train_step(gf, 1e-5)
+            Fs = [net.train_step(gf, 1e-5)[0] for _ in range(30)]
+        finally:
+            net.close()
+    assert F0 == pytest.approx(O.functional(U)[0], rel=1e-3)  # g0 starts near the identity
+    assert max(Fs[-5:]) > F0 + 1e-3
+
+
+def test_warm_started_fix_converges_and_reports_gain(lgf):
+    dims = (8, 8, 8, 8)
+    train = [I.synthetic_config(dims, seed=100 + k, link_scale=0.5) for k in range(4)]
+    Ue = I.synthetic_config(dims, seed=200, link_scale=0.5)
+    net = lgf.WarmStartNet(seed=5)
+    try:
+        with lgf.GaugeFixer(dims, "f32") as gf:
+            for _ in range(10):
+                for U in train:
+                    gf.load_links(U)
+                    net.train_step(gf, 1e-5)
+        with lgf.GaugeFixer(dims, "f32") as gf:
+            gf.load_links(Ue)
+            it_plain, conv_p = gf.fix(1e-15, 2000)
+            F_plain = gf.functional()[0]
+            gf.load_links(Ue)
+            net.warm_start(gf)
+            F_start = gf.functional()[0]
+            it_warm, conv_w = gf.fix(1e-15, 2000)
+            F_warm, th = gf.functional()
+    finally:
+        net.close()
+    assert conv_p and conv_w and th < 1e-15
+    same_copy = abs(F_warm - F_plain) < 1e-12 * abs(F_plain)
+    print(f"\nwarm start on 8^4: F {O.functional(Ue)[0]:.6f} -> {F_start:.6f} before fixing; "
+          f"iterations plain {it_plain}, warm {it_warm}; final F plain {F_plain:.15f}, "
+          f"warm {F_warm:.15f} ({'same' if same_copy else 'different'} Gribov copy)")
+    assert F_start > O.functional(Ue)[0]
