@@ -54,6 +54,13 @@ WORKLOADS["batch64-f32"] = dict(
     batch=64, dtype="f32", link_scale=0.5, gauge_scale=1.0, seed=0, alpha=0.08, tol=1e-15, max_iter=5000,
     desc="64 configs (16 each of 16^4, 24^3x48, 32^3x8, 20^4; seeds 0..63) fixed together from CUDA graphs, "
          "FP32 + FP64 tail to theta<1e-15, link scale 0.5, FFT pipeline autotuned per shape")
+WORKLOADS["warmstart-f32"] = dict(
+    warm=True, dtype="f32", link_scale=0.5, gauge_scale=1.0, alpha=0.08, tol=1e-15, max_iter=5000,
+    train_dims=(16, 16, 16, 16), train_n=512, train_seed=1000, epochs=1, lr=1e-5,
+    eval_dims=(24, 24, 24, 24), eval_n=8, eval_seed=5000,
+    desc="learned warm start: 4D conv net (3 layers, 32 channels, 3^4 taps, BF16 weights, FP32 accumulation) "
+         "trained on 16^4 configs (maximising F of the warm-started links), evaluated on 24^4 configs: "
+         "iterations and time to theta<1e-15 with and without the warm start")
 DEFAULT_WORKLOAD = "32^4-f32"
 KERNEL_SOURCES = {"update": "k_links.cu", "gradient": "k_links.cu", "build_g": "k_links.cu",
                   "accumulate": "k_links.cu", "fft_xy": "k_fft_plane.cu", "fft_zt": "k_fft_plane.cu",
@@ -481,6 +488,91 @@ def run_batch(args, W):
     }
 
 
+def run_warm(args, W):
+    """C5: train the warm-start network on the GPU, then compare fixes of
+    unseen larger configurations with and without it."""
+    import numpy as np
+    import torch
+
+    import paper_1208_1186_gb300 as lgf
+    from lgf_inputs import torch_gen
+
+    torch.cuda.set_device(0)
+    ntr = args.train_n if args.train_n else W["train_n"]
+    net = lgf.WarmStartNet(seed=0)
+    gf = lgf.GaugeFixer(W["train_dims"], W["dtype"], alpha=W["alpha"])
+    Vt = int(np.prod(W["train_dims"]))
+    F_first, F_last = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    for ep in range(W["epochs"]):
+        for k in range(ntr):
+            u = torch_gen.synthetic_config(W["train_dims"], seed=W["train_seed"] + k, link_scale=W["link_scale"],
+                                           gauge_scale=W["gauge_scale"], device="cuda")
+            gf.load_links(u)
+            F, _ = net.train_step(gf, W["lr"])
+            steps += 1
+            (F_first if k < 16 and ep == 0 else F_last if k >= ntr - 16 else []).append(F)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    gf.close()
+    # evaluation on unseen configurations of another size
+    ge = lgf.GaugeFixer(W["eval_dims"], W["dtype"], alpha=W["alpha"])
+    rows = []
+    for k in range(W["eval_n"]):
+        u = torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] + k, link_scale=W["link_scale"],
+                                       gauge_scale=W["gauge_scale"], device="cuda")
+        ge.load_links(u)
+        F0 = ge.functional()[0]
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        it_p, cp = ge.fix(W["tol"], W["max_iter"])
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - a
+        Fp = ge.functional()[0]
+        ge.load_links(u)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        net.warm_start(ge)
+        torch.cuda.synchronize()
+        tw0 = time.perf_counter() - a
+        Fw0 = ge.functional()[0]
+        a = time.perf_counter()
+        it_w, cw = ge.fix(W["tol"], W["max_iter"])
+        torch.cuda.synchronize()
+        tw = time.perf_counter() - a + tw0
+        Fw, thw = ge.functional()
+        rows.append(dict(F_start=F0, F_warm_start=Fw0, it_plain=it_p, it_warm=it_w, t_plain=tp, t_warm=tw,
+                         t_inference=tw0, F_plain=Fp, F_warm=Fw, converged=bool(cp and cw),
+                         same_copy=bool(abs(Fw - Fp) <= 1e-12 * abs(Fp))))
+    ge.close()
+    net.close()
+    Ve = int(np.prod(W["eval_dims"]))
+    mean = lambda key: float(np.mean([r[key] for r in rows]))
+    it_p, it_w = mean("it_plain"), mean("it_warm")
+    return {
+        "metric": METRIC, "value": round(Ve * it_w / mean("t_warm"), 1), "unit": METRIC, "n_gpus": 1,
+        "steps": steps, "warmup": 0, "ms_per_step": round(train_s / max(steps, 1) * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+        "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
+        "config": {"workload": W["desc"], "train_lattice": list(W["train_dims"]), "train_configs": ntr,
+                   "epochs": W["epochs"], "lr": W["lr"], "eval_lattice": list(W["eval_dims"]),
+                   "eval_configs": W["eval_n"]},
+        "training": {"seconds": round(train_s, 2), "train_steps": steps,
+                     "mean_F_warm_first16": round(float(np.mean(F_first)), 6) if F_first else None,
+                     "mean_F_warm_last16": round(float(np.mean(F_last)), 6) if F_last else None},
+        "evaluation": {"iterations_plain": it_p, "iterations_warm": it_w,
+                       "iteration_gain": round(it_p - it_w, 3),
+                       "seconds_plain": round(mean("t_plain"), 5), "seconds_warm": round(mean("t_warm"), 5),
+                       "seconds_inference": round(mean("t_inference"), 5),
+                       "F_before": mean("F_start"), "F_after_warm_start": mean("F_warm_start"),
+                       "all_converged": all(r["converged"] for r in rows),
+                       "same_gribov_copy": sum(r["same_copy"] for r in rows), "per_config": rows},
+        "e2e": None, "e2e_note": "see the 32^4 line", "roofline": None,
+    }
+
+
 def run_reference(args, W):
     """The oracle as it stands, on host cores, each step a bounded sample."""
     import numpy as np
@@ -531,6 +623,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--train-n", type=int, default=0, help="warm-start workload: training configurations")
     ap.add_argument("--link-update", type=int, default=0, choices=[0, 1],
                     help="FP32 storage: 0 gauge representation (default), 1 links updated in place")
     args = ap.parse_args()
@@ -539,11 +632,13 @@ def main():
         args.warmup = 3
     W = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if "batch" in W:
+        if "batch" in W or "warm" in W:
             W = WORKLOADS[DEFAULT_WORKLOAD]
         line = run_reference(args, W)
     elif "batch" in W:
         line = run_batch(args, W)
+    elif "warm" in W:
+        line = run_warm(args, W)
     else:
         line = run_ours(args, W)
     if line is not None:
