@@ -278,6 +278,8 @@ def run_ours(args, W):
     gauge_rep = W["dtype"].startswith("f32") and args.link_update == 0
     if W["dtype"].startswith("f32"):
         gf.set_param(6, args.link_update)  # LGF_LINK_UPDATE
+        if args.tail_theta > 0:
+            gf.set_param(2, args.tail_theta)  # LGF_TAIL_THETA
     gf.load_links(Ud)
     smi = ClockSampler(gpu_id_for_smi(torch)) if rank == 0 else None
     try:
@@ -315,6 +317,14 @@ def run_ours(args, W):
         fix_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
         split = gf.fix_split()
         F, theta = gf.functional()
+        # the same fix once more with per-kernel events, for the breakdown
+        gf.load_links(Ud)
+        torch.cuda.synchronize()
+        gf.profile(True)
+        gf.fix(W["tol"], W["max_iter"])
+        fix_prof = {k: round(v[0], 3) for k, v in gf.profile_read().items() if v[1]}
+        fix_launches = {k: v[1] for k, v in gf.profile_read().items() if v[1]}
+        gf.profile(False)
 
         # end to end through the public API from pinned host memory
         pinned = torch.empty(U.shape + (2,), dtype=torch.float64, pin_memory=True)
@@ -388,7 +398,8 @@ def run_ours(args, W):
         "kernels": kernels,
         "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 4), "iterations": iters,
                           "fp32_iterations": split[0], "fp64_iterations": split[1], "converged": conv,
-                          "F": F, "theta": theta},
+                          "F": F, "theta": theta,
+                          "kernel_ms_profiled_run": fix_prof, "kernel_launches_profiled_run": fix_launches},
         "e2e": {"value": round(V * iters_e2e * world / e2e_s, 1), "unit": METRIC, "seconds": round(e2e_s, 4),
                 "what": "lgf_load_links(pinned host) + lgf_fix(theta<tol) + lgf_store_links(pinned host)",
                 "h2d_bytes_per_step": round(h2d / max(iters_e2e, 1), 1),
@@ -624,6 +635,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--train-n", type=int, default=0, help="warm-start workload: training configurations")
+    ap.add_argument("--tail-theta", type=float, default=0.0, help="theta at which the FP32 phase hands over")
     ap.add_argument("--link-update", type=int, default=0, choices=[0, 1],
                     help="FP32 storage: 0 gauge representation (default), 1 links updated in place")
     args = ap.parse_args()

@@ -71,7 +71,8 @@ enum lgf_param {
   LGF_ALPHA = 0,        /* step size alpha (default 0.08)                       */
   LGF_CHECK_EVERY = 1,  /* lgf_fix: iterations queued between host checks (32)  */
   LGF_TAIL_THETA = 2,   /* mixed precision: theta at which the FP32 phase hands
-                           over to the FP64 tail (default 1e-11)                */
+                           over to the FP64 tail (default 1e-12, just above
+                           where FP32 rounding stalls the FP32 phase)          */
   LGF_TAIL_MAX_FP32 = 3, /* mixed precision: cap on FP32 iterations (default: all) */
   LGF_REUNIT_FP64 = 4,   /* FP32 storage: reunitarise g in FP64 arithmetic (0/1,
                             default 0: g is stored in FP32, so FP64 arithmetic
@@ -81,6 +82,12 @@ enum lgf_param {
                             per-axis register passes, else shared-memory
                             Stockham planes; 1 Stockham planes; 2 per-axis
                             passes; 3 register planes (1 where not available) */
+  LGF_TAIL_MODE = 7,     /* mixed precision: 0 (default) finishes with the
+                            defect-correction tail when the FP32 phase reached
+                            theta < 1e-8 (FP64 links, gradient and F/theta;
+                            FP32 acceleration and step, g = 1 + eps with eps
+                            the exponential to second order); 1 always uses
+                            the plain FP64 iteration                          */
   LGF_LINK_UPDATE = 6    /* FP32 storage, from the next load: 0 (default) keeps
                             the loaded links and applies each update to the
                             accumulated gauge transformation G, forming

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "LGF_OK", -1: "LGF_ERR_ARG", -2: "LGF_ERR_CUDA", -3: "LGF_ERR
                 -4: "LGF_ERR_NOT_CONVERGED", -5: "LGF_ERR_NONFINITE", -6: "LGF_ERR_TIMEOUT"}
 
 LGF_ALPHA, LGF_CHECK_EVERY, LGF_TAIL_THETA, LGF_TAIL_MAX_FP32 = 0, 1, 2, 3
-LGF_REUNIT_FP64, LGF_FFT_PIPELINE, LGF_LINK_UPDATE = 4, 5, 6
+LGF_REUNIT_FP64, LGF_FFT_PIPELINE, LGF_LINK_UPDATE, LGF_TAIL_MODE = 4, 5, 6, 7
 
 # every symbol include/lgf.h declares: name -> (restype, argtypes)
 _P = ctypes.c_void_p

@@ -73,11 +73,13 @@ struct lgf_ctx {
   cudaStream_t stream = nullptr;
   double alpha = 0.08;
   int check_every = 32;
-  double tail_theta = 1e-11;
+  double tail_theta = 1e-12;
   long long tail_max32 = -1;
   bool reunit_fp64 = false;   // FP32 storage: reunitarise g in FP64 arithmetic
   int fft_pipeline = 0;       // 0 auto, 1 Stockham planes, 2 axis passes, 3 register planes
   bool explicit_fp32 = false; // FP32 engine: update the links in place instead of G (from the next load)
+  int tail_mode = 0;          // 0: defect-correction tail when the FP32 phase reached 1e-8, 1: plain FP64
+  bool defect = false;        // the FP64 engine runs the defect-correction tail
 
   Geom geo{};
   Engine e64, e32;
@@ -347,6 +349,16 @@ int queue_gradient(lgf_handle h, Engine& e, int mode) {
 // G U_loaded G^dagger up to FP32 rounding.
 int queue_iteration(lgf_handle h, Engine& e) {
   cudaStream_t s = h->stream;
+  if (h->defect && &e == &h->e64) {
+    // defect-correction tail: FP64 links, FP32 acceleration and step
+    Engine& f = h->e32;
+    LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient_tail(e.U, f.D, h->partial, h->geo, h->st, 1, s));
+    int rc = queue_accelerate(h, f, h->st);
+    if (rc) return rc;
+    LGF_LAUNCH(h, LGF_K_BUILD_G, launch_tail_step(f.D, f.g, h->V, 0.5 * h->alpha, h->st, s));
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_update(e.U, f.g, h->geo, h->st, s));
+    return LGF_OK;
+  }
   int rc = queue_gradient(h, e, 1);
   if (!rc) rc = queue_accelerate(h, e, h->st);
   if (rc) return rc;
@@ -371,12 +383,20 @@ int run_fix(lgf_handle h, Engine& e, double tol, int max_iter, bool stall_check,
   int rc = reset_state(h, tol, max_iter, true);
   if (rc) return rc;
   long long queued = 0;
-  double last_theta = INFINITY;
-  int stalls = 0;
+  // queue length: 8 iterations first, then as many as the measured contraction
+  // rate predicts are still needed (+1), at most LGF_CHECK_EVERY; iterations
+  // queued past the stop decision cost only empty launches, but they do cost
+  int k = h->check_every < 8 ? h->check_every : 8;
+  double prev_theta = -1.0;
+  int prev_iters = 0;
+  // stall (FP32 phase): theta has not halved over >= 8 iterations below 1e-6
+  double ref_theta = INFINITY;
+  int ref_iters = 0;
   *converged = false;
   for (;;) {
     const long long room = (long long)max_iter + 1 - queued;
-    const int k = (int)(room < h->check_every ? room : h->check_every);
+    if (k > room) k = (int)room;
+    if (k < 1) k = 1;
     for (int i = 0; i < k; ++i) {
       rc = queue_iteration(h, e);
       if (rc) return rc;
@@ -387,17 +407,26 @@ int run_fix(lgf_handle h, Engine& e, double tol, int max_iter, bool stall_check,
     const DevState& s = *h->st_host;
     if (s.nonfinite) return fail(h, LGF_ERR_NONFINITE, "F or theta is not finite (non-SU(3) or NaN input links?)");
     if (s.done || queued >= (long long)max_iter + 1) break;
-    if (stall_check) {
-      if (s.theta > 0.5 * last_theta) {
-        if (++stalls >= 2) {
-          // hand over: stop the FP32 phase at the next reduce
-          break;
-        }
-      } else {
-        stalls = 0;
+    if (stall_check && s.theta < 1e-6) {
+      if (s.theta > 0.5 * ref_theta && s.iters - ref_iters >= 8) break;  // hand over to the tail
+      if (s.theta <= 0.5 * ref_theta || ref_theta == INFINITY) {
+        ref_theta = s.theta;
+        ref_iters = s.iters;
       }
-      last_theta = s.theta;
     }
+    // predict the iterations still needed from the last interval
+    int next = h->check_every;
+    const int dn = s.iters - prev_iters;
+    if (prev_theta > 0.0 && dn > 0 && s.theta < prev_theta && s.theta > 0.0) {
+      const double r = pow(s.theta / prev_theta, 1.0 / dn);
+      if (r < 0.999) {
+        const double need = log(tol / s.theta) / log(r);
+        next = need < 1.0 ? 1 : (int)ceil(need) + 1;
+      }
+    }
+    k = next < h->check_every ? next : h->check_every;
+    prev_theta = s.theta;
+    prev_iters = s.iters;
   }
   const DevState& s = *h->st_host;
   *done_iters = s.iters;
@@ -974,6 +1003,9 @@ int lgf_set_param(lgf_handle h, int key, double value) {
     case LGF_LINK_UPDATE:
       h->explicit_fp32 = value != 0.0;
       return LGF_OK;
+    case LGF_TAIL_MODE:
+      h->tail_mode = value != 0.0 ? 1 : 0;
+      return LGF_OK;
     default:
       return fail(h, LGF_ERR_ARG, "unknown parameter key");
   }
@@ -986,6 +1018,7 @@ static int load_from_device_aos(lgf_handle h, const double* aos) {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(4, h->e32.nc, aos, h->e32.U, V, 4, h->stream));
     LGF_LAUNCH(h, LGF_K_OTHER, launch_set_identity(4, h->e32.nc, h->G, V, h->stream));
     h->e32.grep = !h->explicit_fp32;
+    h->defect = false;
     h->cur = &h->e32;
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
@@ -1069,6 +1102,7 @@ int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out) {
     LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
     h->cur = &h->e64;
+    h->defect = (h->tail_mode == 0) && h->st_host->theta < 1e-8;
   }
   const int left = max_iter - n1;
   rc = run_fix(h, *h->cur, theta_tol, left, false, &n2, &conv);
@@ -1257,6 +1291,7 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
       } while (0);
       h->stream = saved;
       h->cur = &h->e64;
+      h->defect = (h->tail_mode == 0) && h->st_host->theta < 1e-8;
       tail.push_back(i);
     } else {
       h->last_n64 = n1[i];

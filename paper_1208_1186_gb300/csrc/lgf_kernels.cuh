@@ -96,6 +96,13 @@ cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V,
                          const DevState* st, cudaStream_t s);
 cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s);
 
+// FP64 tail by defect correction (k_tail.cu): FP64 links, FP32 FFT and step
+cudaError_t launch_gradient_tail(const void* U64, void* D32, double2* partial, const Geom& geo, DevState* st,
+                                 int mode, cudaStream_t s);
+cudaError_t launch_tail_step(const void* D32, void* eps, int64_t V, double half_alpha, const DevState* st,
+                             cudaStream_t s);
+cudaError_t launch_tail_update(void* U64, const void* eps, const Geom& geo, const DevState* st, cudaStream_t s);
+
 // learned warm start (k_warm.cu): features, BF16 tensor-core convolutions,
 // exp map, training signal, Adam
 namespace warm {

@@ -279,3 +279,22 @@ def test_full_size_32_4_fp32_tail(lgf):
     # Landau condition from the oracle's own gradient of the result
     assert O.functional(out)[1] < 1e-15
     assert F > O.functional(U)[0]
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (12, 12, 32, 8)])
+def test_both_fp64_tails_reach_the_oracle_functional(lgf, dims):
+    """LGF_TAIL_MODE 0 (defect-correction tail: FP64 links and sums, FP32
+    acceleration and step) and 1 (plain FP64 iteration) end at the oracle's
+    FP64 functional to 1e-12 relative, with theta < 1e-15."""
+    U, ref = _oracle_fix(dims, 2, 0.5, 1e-15)
+    res = {}
+    for mode in (0, 1):
+        with lgf.GaugeFixer(dims, "f32") as gf:
+            gf.set_param(7, mode)  # LGF_TAIL_MODE
+            gf.load_links(U)
+            iters, conv = gf.fix(1e-15, 2000)
+            F, th = gf.functional()
+            res[mode] = (iters, gf.fix_split(), F)
+        assert conv and th < 1e-15
+        assert F == pytest.approx(ref["F"], rel=1e-12)
+    assert res[0][1][0] == res[1][1][0]  # the same FP32 phase
