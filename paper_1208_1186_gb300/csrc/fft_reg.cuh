@@ -11,9 +11,13 @@
 //
 // With L a template constant every loop unrolls and every index, radix and
 // twiddle index is a compile-time constant: the line stays in registers.
-// Twiddles W_L^m = exp(-2 pi i m / L) come from a per-axis table in shared
-// memory (all threads read the same entry: broadcast).
+// Twiddles W_L^m = exp(-2 pi i m / L) are compile-time constants (every
+// stage index is a template constant), so they become instruction immediates
+// or constant-bank operands: no table, no shared-memory loads, no registers.
+// Multiples of a quarter turn are exact sign/swap operations.
 #pragma once
+
+#include <type_traits>
 
 #include "lgf_common.cuh"
 
@@ -46,6 +50,99 @@ constexpr int digit_rev(int L, int p) {
   return k;
 }
 
+// ---------------------------------------------------------------------------
+// cos and sin of 2 pi m / L at compile time.  The angle is reduced to the first
+// octant with exact integer arithmetic (8 m = o L + rem), then a Taylor series
+// on [0, pi/4] (terms beyond x^25 / 25! are below 1e-27) gives the value to a
+// few units in the last place of double; octant symmetries give exact zeros,
+// ones and mirrored values.
+// ---------------------------------------------------------------------------
+constexpr double kTwoPiOver8 = 0.78539816339744830961566084581987572;  // pi / 4
+
+constexpr double poly_sin(double x) {
+  double term = x, sum = x;
+  for (int n = 1; n <= 12; ++n) {
+    term *= -x * x / (double)((2 * n) * (2 * n + 1));
+    sum += term;
+  }
+  return sum;
+}
+
+constexpr double poly_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n <= 12; ++n) {
+    term *= -x * x / (double)((2 * n - 1) * (2 * n));
+    sum += term;
+  }
+  return sum;
+}
+
+// {cos, sin} of 2 pi m / L; which = 0 for cos, 1 for sin
+constexpr double turn_cs(int m, int L, int which) {
+  m = ((m % L) + L) % L;
+  const int e = 8 * m, o = e / L, rem = e - o * L;
+  const double phi = kTwoPiOver8 * (double)rem / (double)L;        // o pi/4 + phi
+  const double psi = kTwoPiOver8 * (double)(L - rem) / (double)L;  // (o+1) pi/4 - psi
+  const bool zero = rem == 0;
+  const double cp = zero ? 1.0 : poly_cos(phi), sp = zero ? 0.0 : poly_sin(phi);
+  const double cq = poly_cos(psi), sq = poly_sin(psi);
+  double c = 0.0, s = 0.0;
+  switch (o) {
+    case 0: c = cp; s = sp; break;
+    case 1: c = sq; s = cq; break;
+    case 2: c = -sp; s = cp; break;
+    case 3: c = -cq; s = sq; break;
+    case 4: c = -cp; s = -sp; break;
+    case 5: c = -sq; s = -cq; break;
+    case 6: c = sp; s = -cp; break;
+    default: c = cq; s = -sq; break;
+  }
+  return which == 0 ? c : s;
+}
+
+template <int L, int M>
+struct Twiddle {  // W_L^M = exp(-2 pi i M / L)
+  static constexpr int m = ((M % L) + L) % L;
+  static constexpr bool quarter = (4 * m) % L == 0;  // W in {1, -i, -1, i}
+  static constexpr int q = quarter ? 4 * m / L : -1;
+  static constexpr double re = turn_cs(m, L, 0);
+  static constexpr double im = -turn_cs(m, L, 1);
+};
+
+// v * W_L^M (CONJ: v * conj(W_L^M))
+template <class T, int L, int M, bool CONJ>
+__device__ __forceinline__ cx<T> mul_tw(cx<T> v) {
+  using W = Twiddle<L, M>;
+  if constexpr (W::quarter) {
+    constexpr int q = CONJ ? (4 - W::q) % 4 : W::q;  // W = (-i)^q
+    if constexpr (q == 0) return v;
+    else if constexpr (q == 1) return mk<T>(v.im, -v.re);
+    else if constexpr (q == 2) return mk<T>(-v.re, -v.im);
+    else return mk<T>(-v.im, v.re);
+  } else {
+    constexpr T wr = (T)W::re;
+    constexpr T wi = CONJ ? (T)-W::im : (T)W::im;
+    return mk<T>(fmaT(v.re, wr, -v.im * wi), fmaT(v.re, wi, v.im * wr));
+  }
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// 4 sin^2(pi k / L) (the lattice momentum squared of one axis), for the
+// frequency k held at position P after the forward transform
+template <int L, int P>
+struct MomentumSq {
+  static constexpr double s = turn_cs(digit_rev(L, P), 2 * L, 1);  // sin(2 pi k / (2 L))
+  static constexpr double value = 4.0 * s * s;
+};
+
 template <class T>
 __device__ __forceinline__ cx<T> mul_i(cx<T> a, bool neg) {  // neg ? -i*a : +i*a
   return neg ? mk<T>(a.im, -a.re) : mk<T>(-a.im, a.re);
@@ -66,8 +163,8 @@ __device__ __forceinline__ void dft(cx<T>* v) {
     v[1] = d02 + d13;
     v[3] = d02 - d13;
   } else if constexpr (R == 3) {
-    const T h = (T)0.5;
-    const T s = (T)0.86602540378443864676;  // sin(2 pi / 3)
+    constexpr T h = (T)0.5;
+    constexpr T s = (T)turn_cs(1, 3, 1);  // sin(2 pi / 3)
     const cx<T> t1 = v[1] + v[2];
     const cx<T> t2 = scale(mul_i(v[1] - v[2], !INV), s);
     const cx<T> m = v[0] - scale(t1, h);
@@ -75,10 +172,8 @@ __device__ __forceinline__ void dft(cx<T>* v) {
     v[1] = m + t2;
     v[2] = m - t2;
   } else {  // R == 5
-    const T c1 = (T)0.30901699437494742410;   // cos(2 pi / 5)
-    const T c2 = (T)-0.80901699437494742410;  // cos(4 pi / 5)
-    const T s1 = (T)0.95105651629515357212;   // sin(2 pi / 5)
-    const T s2 = (T)0.58778525229247312917;   // sin(4 pi / 5)
+    constexpr T c1 = (T)turn_cs(1, 5, 0), c2 = (T)turn_cs(2, 5, 0);  // cos(2 pi / 5), cos(4 pi / 5)
+    constexpr T s1 = (T)turn_cs(1, 5, 1), s2 = (T)turn_cs(2, 5, 1);  // sin(2 pi / 5), sin(4 pi / 5)
     const cx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
     const cx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
     const cx<T> p1 = v[0] + scale(a1, c1) + scale(a2, c2);
@@ -95,59 +190,62 @@ __device__ __forceinline__ void dft(cx<T>* v) {
 
 // Forward stages on sub-transforms of length N (called with N = L).
 template <class T, int L, int N>
-__device__ __forceinline__ void dif_stages(cx<T>* a, const cx<T>* tw) {
+__device__ __forceinline__ void dif_stages(cx<T>* a) {
   if constexpr (N > 1) {
     constexpr int R = next_radix(N);
     constexpr int span = N / R;
 #pragma unroll
     for (int b = 0; b < L / N; ++b) {
-#pragma unroll
-      for (int k = 0; k < span; ++k) {
+      static_for<0, span>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
         cx<T> u[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) u[r] = a[b * N + k + r * span];
         dft<T, R, false>(u);
-#pragma unroll
-        for (int q = 0; q < R; ++q) a[b * N + k + q * span] = (q == 0 || k == 0) ? u[q] : u[q] * tw[q * k * (L / N)];
-      }
+        a[b * N + k] = u[0];
+        static_for<1, R>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          a[b * N + k + q * span] = mul_tw<T, L, q * k * (L / N), false>(u[q]);
+        });
+      });
     }
-    dif_stages<T, L, span>(a, tw);
+    dif_stages<T, L, span>(a);
   }
 }
 
 // Inverse stages: the innermost forward stage is undone first.
 template <class T, int L, int N>
-__device__ __forceinline__ void dit_inv_stages(cx<T>* a, const cx<T>* tw) {
+__device__ __forceinline__ void dit_inv_stages(cx<T>* a) {
   if constexpr (N > 1) {
     constexpr int R = next_radix(N);
     constexpr int span = N / R;
-    dit_inv_stages<T, L, span>(a, tw);
+    dit_inv_stages<T, L, span>(a);
 #pragma unroll
     for (int b = 0; b < L / N; ++b) {
-#pragma unroll
-      for (int k = 0; k < span; ++k) {
+      static_for<0, span>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
         cx<T> u[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const cx<T> v = a[b * N + k + q * span];
-          u[q] = (q == 0 || k == 0) ? v : mul_cj(v, tw[q * k * (L / N)]);
-        }
+        u[0] = a[b * N + k];
+        static_for<1, R>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          u[q] = mul_tw<T, L, q * k * (L / N), true>(a[b * N + k + q * span]);
+        });
         dft<T, R, true>(u);
 #pragma unroll
         for (int r = 0; r < R; ++r) a[b * N + k + r * span] = u[r];
-      }
+      });
     }
   }
 }
 
 template <class T, int L>
-__device__ __forceinline__ void forward(cx<T>* a, const cx<T>* tw) {
-  dif_stages<T, L, L>(a, tw);
+__device__ __forceinline__ void forward(cx<T>* a) {
+  dif_stages<T, L, L>(a);
 }
 
 template <class T, int L>
-__device__ __forceinline__ void inverse(cx<T>* a, const cx<T>* tw) {
-  dit_inv_stages<T, L, L>(a, tw);
+__device__ __forceinline__ void inverse(cx<T>* a) {
+  dit_inv_stages<T, L, L>(a);
 }
 
 }  // namespace regfft

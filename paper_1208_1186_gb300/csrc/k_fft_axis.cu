@@ -29,22 +29,15 @@ constexpr int xpass_lines() {
   return (L * (int)sizeof(cx<T>) > 256) ? 64 : 128;
 }
 
-template <class T>
-__device__ __forceinline__ void load_tw(cx<T>* dst, const cx<T>* __restrict__ src, int L) {
-  for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
-}
-
 // One thread per x-line; the block's lines are a contiguous chunk of D.
 template <class T, int L, bool INV>
 __global__ void __launch_bounds__(128) k_xpass(cx<T>* __restrict__ D, int64_t total_lines,
-                                               const cx<T>* __restrict__ tw, const DevState* __restrict__ st) {
+                                               const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   constexpr int NL = xpass_lines<T, L>();
   constexpr int P = L + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tws = tile + NL * P;
-  load_tw(tws, tw, L);
   const int64_t g0 = (int64_t)blockIdx.x * NL;
   const int nl = (int)((total_lines - g0) < NL ? (total_lines - g0) : NL);
   cx<T>* chunk = D + g0 * L;
@@ -69,9 +62,9 @@ __global__ void __launch_bounds__(128) k_xpass(cx<T>* __restrict__ D, int64_t to
 #pragma unroll
     for (int p = 0; p < L; ++p) v[p] = row[p];
     if (INV)
-      regfft::inverse<T, L>(v, tws);
+      regfft::inverse<T, L>(v);
     else
-      regfft::forward<T, L>(v, tws);
+      regfft::forward<T, L>(v);
 #pragma unroll
     for (int p = 0; p < L; ++p) row[p] = v[p];
   }
@@ -96,11 +89,8 @@ constexpr int pass_min_blocks() {
 
 template <class T, int L, bool INV>
 __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_strided(cx<T>* __restrict__ D, int64_t V, int64_t S,
-                                                 const cx<T>* __restrict__ tw, const DevState* __restrict__ st) {
+                                                 const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
-  __shared__ cx<T> tws[kMaxL];
-  load_tw(tws, tw, L);
-  __syncthreads();
   // 32-bit offsets: 4 V < 2^31 for extents <= 64
   const int nl = (int)(V / L);  // lines per field
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,9 +102,9 @@ __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_strided(cx<T>*
 #pragma unroll
   for (int p = 0; p < L; ++p) v[p] = line[p * Si];
   if (INV)
-    regfft::inverse<T, L>(v, tws);
+    regfft::inverse<T, L>(v);
   else
-    regfft::forward<T, L>(v, tws);
+    regfft::forward<T, L>(v);
 #pragma unroll
   for (int p = 0; p < L; ++p) line[p * Si] = v[p];
 }
@@ -127,12 +117,9 @@ __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_strided(cx<T>*
 template <class T, int L>
 __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_tpass(cx<T>* __restrict__ D, int64_t V, int Lx, int Ly,
                                                const T* __restrict__ kfac, const float* __restrict__ s2p,
-                                               float c_over_V, const cx<T>* __restrict__ tw,
-                                               const DevState* __restrict__ st) {
+                                               float c_over_V, const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
-  __shared__ cx<T> tws[kMaxL];
   __shared__ float s2t[kMaxL];
-  load_tw(tws, tw, L);
   if (sizeof(T) == 4)
     for (int i = threadIdx.x; i < L; i += blockDim.x) s2t[i] = s2p[3 * kMaxL + i];
   __syncthreads();
@@ -144,7 +131,7 @@ __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_tpass(cx<T>* _
   cx<T> v[L];
 #pragma unroll
   for (int p = 0; p < L; ++p) v[p] = line[p * S];
-  regfft::forward<T, L>(v, tws);
+  regfft::forward<T, L>(v);
   if constexpr (sizeof(T) == 4) {
     const int x = l % Lx, y = (l / Lx) % Ly, z = l / (Lx * Ly);
     const float a = __ldg(s2p + x) + __ldg(s2p + kMaxL + y) + __ldg(s2p + 2 * kMaxL + z);
@@ -158,14 +145,14 @@ __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_tpass(cx<T>* _
 #pragma unroll
     for (int p = 0; p < L; ++p) v[p] = scale(v[p], __ldg(kfac + (l + p * S)));
   }
-  regfft::inverse<T, L>(v, tws);
+  regfft::inverse<T, L>(v);
 #pragma unroll
   for (int p = 0; p < L; ++p) line[p * S] = v[p];
 }
 
 template <class T, int L>
 size_t xpass_smem() {
-  return ((size_t)xpass_lines<T, L>() * (L + 1) + kMaxL) * sizeof(cx<T>);
+  return (size_t)xpass_lines<T, L>() * (L + 1) * sizeof(cx<T>);
 }
 
 #define LGF_AXIS_LENGTHS(X) X(4) X(6) X(8) X(12) X(16) X(20) X(24) X(32) X(48) X(64)
@@ -177,35 +164,34 @@ constexpr bool reg_ok(int L) {
 }
 
 template <class T, int L>
-cudaError_t xpass_launch(void* D, int64_t V, const void* tw, int inverse, const DevState* st, cudaStream_t s) {
+cudaError_t xpass_launch(void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s) {
   const int64_t total = 4 * (V / L);
   constexpr int NL = xpass_lines<T, L>();
   const unsigned nb = (unsigned)((total + NL - 1) / NL);
   const size_t sm = xpass_smem<T, L>();
   if (inverse)
-    k_xpass<T, L, true><<<nb, 128, sm, s>>>(static_cast<cx<T>*>(D), total, static_cast<const cx<T>*>(tw), st);
+    k_xpass<T, L, true><<<nb, 128, sm, s>>>(static_cast<cx<T>*>(D), total, st);
   else
-    k_xpass<T, L, false><<<nb, 128, sm, s>>>(static_cast<cx<T>*>(D), total, static_cast<const cx<T>*>(tw), st);
+    k_xpass<T, L, false><<<nb, 128, sm, s>>>(static_cast<cx<T>*>(D), total, st);
   return cudaPeekAtLastError();
 }
 
 template <class T, int L>
-cudaError_t strided_launch(void* D, int64_t V, int64_t S, const void* tw, int inverse, const DevState* st,
-                           cudaStream_t s) {
+cudaError_t strided_launch(void* D, int64_t V, int64_t S, int inverse, const DevState* st, cudaStream_t s) {
   const unsigned nb = (unsigned)((4 * (V / L) + 127) / 128);
   if (inverse)
-    k_strided<T, L, true><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, S, static_cast<const cx<T>*>(tw), st);
+    k_strided<T, L, true><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, S, st);
   else
-    k_strided<T, L, false><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, S, static_cast<const cx<T>*>(tw), st);
+    k_strided<T, L, false><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, S, st);
   return cudaPeekAtLastError();
 }
 
 template <class T, int L>
 cudaError_t tpass_launch(void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V,
-                         const void* tw, const DevState* st, cudaStream_t s) {
+                         const DevState* st, cudaStream_t s) {
   const unsigned nb = (unsigned)((4 * (V / L) + 127) / 128);
   k_tpass<T, L><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V,
-                                   static_cast<const cx<T>*>(tw), st);
+                                   st);
   return cudaPeekAtLastError();
 }
 
@@ -248,24 +234,23 @@ cudaError_t axis_pass_init() {
   return e;
 }
 
-cudaError_t launch_xpass(int prec, int L, void* D, int64_t V, const void* tw, int inverse, const DevState* st,
-                         cudaStream_t s) {
-#define LGF_CASE(N)                                                          \
-  case N:                                                                    \
-    if (prec == 4) return xpass_launch<float, N>(D, V, tw, inverse, st, s);  \
-    if constexpr (N <= 32) return xpass_launch<double, N>(D, V, tw, inverse, st, s); \
+cudaError_t launch_xpass(int prec, int L, void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s) {
+#define LGF_CASE(N)                                                                \
+  case N:                                                                          \
+    if (prec == 4) return xpass_launch<float, N>(D, V, inverse, st, s);            \
+    if constexpr (N <= 32) return xpass_launch<double, N>(D, V, inverse, st, s);   \
     break;
   switch (L) { LGF_AXIS_LENGTHS(LGF_CASE) }
 #undef LGF_CASE
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const void* tw, int inverse,
-                           const DevState* st, cudaStream_t s) {
-#define LGF_CASE(N)                                                                    \
-  case N:                                                                              \
-    if (prec == 4) return strided_launch<float, N>(D, V, S, tw, inverse, st, s);       \
-    if constexpr (N <= 32) return strided_launch<double, N>(D, V, S, tw, inverse, st, s); \
+cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, int inverse, const DevState* st,
+                           cudaStream_t s) {
+#define LGF_CASE(N)                                                                  \
+  case N:                                                                            \
+    if (prec == 4) return strided_launch<float, N>(D, V, S, inverse, st, s);         \
+    if constexpr (N <= 32) return strided_launch<double, N>(D, V, S, inverse, st, s); \
     break;
   switch (L) { LGF_AXIS_LENGTHS(LGF_CASE) }
 #undef LGF_CASE
@@ -273,11 +258,11 @@ cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const
 }
 
 cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p,
-                         float c_over_V, const void* tw, const DevState* st, cudaStream_t s) {
-#define LGF_CASE(N)                                                                                 \
-  case N:                                                                                           \
-    if (prec == 4) return tpass_launch<float, N>(D, V, Lx, Ly, kfac, s2p, c_over_V, tw, st, s);     \
-    if constexpr (N <= 32) return tpass_launch<double, N>(D, V, Lx, Ly, kfac, s2p, c_over_V, tw, st, s); \
+                         float c_over_V, const DevState* st, cudaStream_t s) {
+#define LGF_CASE(N)                                                                             \
+  case N:                                                                                       \
+    if (prec == 4) return tpass_launch<float, N>(D, V, Lx, Ly, kfac, s2p, c_over_V, st, s);     \
+    if constexpr (N <= 32) return tpass_launch<double, N>(D, V, Lx, Ly, kfac, s2p, c_over_V, st, s); \
     break;
   switch (L) { LGF_AXIS_LENGTHS(LGF_CASE) }
 #undef LGF_CASE

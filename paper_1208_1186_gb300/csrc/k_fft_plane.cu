@@ -6,7 +6,8 @@
 //   -> k_plane_xy(inv)
 //
 // k_plane_xy: one CTA per (z, t) plane; the four fields of the plane
-// (4 LX LY complex) are staged in shared memory; one thread per x-line does
+// (4 LX LY complex) are staged in shared memory by asynchronous copies (no
+// register staging, all loads in flight at once); one thread per x-line does
 // the x transforms, then one thread per y-line the y transforms.
 // k_plane_zt: one CTA per (field, y, run of BX consecutive x) with the whole
 // (z, t) plane of that run in shared memory; z lines, then t lines (forward,
@@ -24,25 +25,25 @@ namespace lgf {
 
 namespace {
 
-template <class T>
-__device__ __forceinline__ void load_tw_p(cx<T>* dst, const cx<T>* __restrict__ src, int L) {
-  for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
-}
-
 template <int LX, int LY>
 constexpr int xy_threads() {
   return 4 * (LX > LY ? LX : LY);
 }
 
+// resident CTAs per SM asked of the register allocator: 4 x 128 threads at
+// up to 128 registers for lines up to 32 complex in FP32
+template <class T, int LX>
+constexpr int xy_min_blocks() {
+  return (sizeof(T) == 4 && LX <= 32) ? 4 : 1;
+}
+
 template <class T, int LX, int LY>
 constexpr size_t xy_smem_bytes() {
-  return ((size_t)4 * LY * (LX + 1) + LX + LY) * sizeof(cx<T>);
+  return (size_t)4 * LY * (LX + 1) * sizeof(cx<T>);
 }
 
 template <class T, int LX, int LY, bool INV>
-__global__ void __launch_bounds__(xy_threads<LX, LY>()) k_plane_xy(cx<T>* __restrict__ D, int V,
-                                                                   const cx<T>* __restrict__ twx_g,
-                                                                   const cx<T>* __restrict__ twy_g,
+__global__ void __launch_bounds__(xy_threads<LX, LY>(), xy_min_blocks<T, LX>()) k_plane_xy(cx<T>* __restrict__ D, int V,
                                                                    const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   constexpr int NT = xy_threads<LX, LY>();
@@ -50,29 +51,17 @@ __global__ void __launch_bounds__(xy_threads<LX, LY>()) k_plane_xy(cx<T>* __rest
   constexpr int N = LX * LY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);  // [f][y][x], row pitch P
-  cx<T>* twx = tile + 4 * LY * P;
-  cx<T>* twy = twx + LX;
-  load_tw_p(twx, twx_g, LX);
-  load_tw_p(twy, twy_g, LY);
   const int plane = blockIdx.x * N;
   // stage the 4 planes (each contiguous in its field)
   static_assert((4 * N) % NT == 0, "tile must split evenly over the threads");
   constexpr int PER = 4 * N / NT;
-  {
-    cx<T> r[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + NT * k;
-      const int f = i / N, q = i % N;
-      r[k] = D[f * V + plane + q];
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + NT * k;
-      const int f = i / N, q = i % N;
-      tile[(f * LY + q / LX) * P + q % LX] = r[k];
-    }
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + NT * k;
+    const int f = i / N, q = i % N;
+    cp_async_elem(tile + ((f * LY + q / LX) * P + q % LX), D + (f * V + plane + q));
   }
+  cp_async_wait_all();
   __syncthreads();
   if (threadIdx.x < 4 * LY) {  // x lines
     cx<T>* row = tile + threadIdx.x * P;
@@ -80,9 +69,9 @@ __global__ void __launch_bounds__(xy_threads<LX, LY>()) k_plane_xy(cx<T>* __rest
 #pragma unroll
     for (int p = 0; p < LX; ++p) v[p] = row[p];
     if (INV)
-      regfft::inverse<T, LX>(v, twx);
+      regfft::inverse<T, LX>(v);
     else
-      regfft::forward<T, LX>(v, twx);
+      regfft::forward<T, LX>(v);
 #pragma unroll
     for (int p = 0; p < LX; ++p) row[p] = v[p];
   }
@@ -94,9 +83,9 @@ __global__ void __launch_bounds__(xy_threads<LX, LY>()) k_plane_xy(cx<T>* __rest
 #pragma unroll
     for (int p = 0; p < LY; ++p) v[p] = col[p * P];
     if (INV)
-      regfft::inverse<T, LY>(v, twy);
+      regfft::inverse<T, LY>(v);
     else
-      regfft::forward<T, LY>(v, twy);
+      regfft::forward<T, LY>(v);
 #pragma unroll
     for (int p = 0; p < LY; ++p) col[p * P] = v[p];
   }
@@ -131,20 +120,25 @@ constexpr int zt_threads() {
   return zt_bx<T>() * (LZ > LT ? LZ : LT);
 }
 
+// z-t lines hold a whole t line through the forward transform, the factor and
+// the inverse: 3 CTAs per SM (up to 168 registers) for FP32 lines up to 32
+template <class T, int LZ, int LT>
+constexpr int zt_min_blocks() {
+  return (sizeof(T) == 4 && LZ <= 32 && LT <= 32) ? 3 : 1;
+}
+
 template <class T, int LZ, int LT>
 constexpr size_t zt_smem_bytes() {
-  return ((size_t)zt_pitch<T, LZ>() * LT + LZ + LT) * sizeof(cx<T>);
+  return (size_t)zt_pitch<T, LZ>() * LT * sizeof(cx<T>);
 }
 
 // FP32: factor from s2p[axis][position] (4 sin^2 at the digit-reversed
 // frequency) and c_over_V = p2_max / V, 0 at k = 0.  FP64: per-site table
 // kfac (an FP64 division per mode would be slow on this GPU).
 template <class T, int LZ, int LT>
-__global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __restrict__ D, int Lx, int Ly,
+__global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, LT>()) k_plane_zt(cx<T>* __restrict__ D, int Lx, int Ly,
                                                                       const T* __restrict__ kfac,
                                                                       const float* __restrict__ s2p, float c_over_V,
-                                                                      const cx<T>* __restrict__ twz_g,
-                                                                      const cx<T>* __restrict__ twt_g,
                                                                       const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   constexpr int BX = zt_bx<T>();
@@ -153,10 +147,6 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __r
   constexpr int N = BX * LZ * LT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);  // [t][z][xb], t pitch PT
-  cx<T>* twz = tile + PT * LT;
-  cx<T>* twt = twz + LZ;
-  load_tw_p(twz, twz_g, LZ);
-  load_tw_p(twt, twt_g, LT);
   const int nxr = Lx / BX;
   const int x0 = (blockIdx.x % nxr) * BX;
   const int y = blockIdx.x / nxr;
@@ -166,21 +156,13 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __r
   cx<T>* Df = D + (f * V + x0 + Lx * y);
   static_assert(N % NT == 0, "tile must split evenly over the threads");
   constexpr int PER = N / NT;
-  {
-    cx<T> r[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + NT * k;
-      const int xb = i % BX, q = i / BX;  // q = z + LZ t
-      r[k] = Df[xb + LxLy * q];
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + NT * k;
-      const int xb = i % BX, q = i / BX;
-      tile[(q / LZ) * PT + (q % LZ) * BX + xb] = r[k];
-    }
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x + NT * k;
+    const int xb = i % BX, q = i / BX;  // q = z + LZ t
+    cp_async_elem(tile + ((q / LZ) * PT + (q % LZ) * BX + xb), Df + (xb + LxLy * q));
   }
+  cp_async_wait_all();
   __syncthreads();
   // forward z: lines (xb, t)
   if (threadIdx.x < BX * LT) {
@@ -189,7 +171,7 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __r
     cx<T> v[LZ];
 #pragma unroll
     for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
-    regfft::forward<T, LZ>(v, twz);
+    regfft::forward<T, LZ>(v);
 #pragma unroll
     for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
   }
@@ -201,23 +183,25 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __r
     cx<T> v[LT];
 #pragma unroll
     for (int p = 0; p < LT; ++p) v[p] = line[p * PT];
-    regfft::forward<T, LT>(v, twt);
+    regfft::forward<T, LT>(v);
     const int x = x0 + xb;
     if constexpr (sizeof(T) == 4) {
+      // the t contribution at each position is a compile-time constant
       const float a = __ldg(s2p + x) + __ldg(s2p + kMaxL + y) + __ldg(s2p + 2 * kMaxL + z);
       const bool origin = (x | y | z) == 0;
-#pragma unroll
-      for (int p = 0; p < LT; ++p) {
-        float kf = c_over_V * __frcp_rn(a + __ldg(s2p + 3 * kMaxL + p));
+      regfft::static_for<0, LT>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        constexpr float s2t = (float)regfft::MomentumSq<LT, p>::value;
+        float kf = c_over_V * __frcp_rn(a + s2t);
         if (p == 0 && origin) kf = 0.0f;
         v[p] = scale(v[p], (T)kf);
-      }
+      });
     } else {
       const T* kl = kfac + (x + Lx * (y + Ly * z));
 #pragma unroll
       for (int p = 0; p < LT; ++p) v[p] = scale(v[p], __ldg(kl + p * (LxLy * LZ)));
     }
-    regfft::inverse<T, LT>(v, twt);
+    regfft::inverse<T, LT>(v);
 #pragma unroll
     for (int p = 0; p < LT; ++p) line[p * PT] = v[p];
   }
@@ -229,7 +213,7 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>()) k_plane_zt(cx<T>* __r
     cx<T> v[LZ];
 #pragma unroll
     for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
-    regfft::inverse<T, LZ>(v, twz);
+    regfft::inverse<T, LZ>(v);
 #pragma unroll
     for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
   }
@@ -256,28 +240,24 @@ namespace {
   X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(32, 8) X(32, 16) X(16, 32)
 
 template <class T, int L>
-cudaError_t xy_launch(void* D, int64_t V, const void* twx, const void* twy, int inverse, const DevState* st,
-                      cudaStream_t s, int Lz, int Lt) {
+cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s, int Lz, int Lt) {
   const unsigned nb = (unsigned)(Lz * Lt);
   constexpr int NT = xy_threads<L, L>();
   constexpr size_t sm = xy_smem_bytes<T, L, L>();
   const auto Dp = static_cast<cx<T>*>(D);
-  const auto a = static_cast<const cx<T>*>(twx);
-  const auto b = static_cast<const cx<T>*>(twy);
   if (inverse)
-    k_plane_xy<T, L, L, true><<<nb, NT, sm, s>>>(Dp, (int)V, a, b, st);
+    k_plane_xy<T, L, L, true><<<nb, NT, sm, s>>>(Dp, (int)V, st);
   else
-    k_plane_xy<T, L, L, false><<<nb, NT, sm, s>>>(Dp, (int)V, a, b, st);
+    k_plane_xy<T, L, L, false><<<nb, NT, sm, s>>>(Dp, (int)V, st);
   return cudaPeekAtLastError();
 }
 
 template <class T, int LZ, int LT>
-cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V, const void* twz,
-                      const void* twt, const DevState* st, cudaStream_t s) {
+cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V, const DevState* st,
+                      cudaStream_t s) {
   dim3 grid((unsigned)((Lx / zt_bx<T>()) * Ly), 4);
   k_plane_zt<T, LZ, LT><<<grid, zt_threads<T, LZ, LT>(), zt_smem_bytes<T, LZ, LT>(), s>>>(
-      static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, static_cast<const cx<T>*>(twz),
-      static_cast<const cx<T>*>(twt), st);
+      static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, st);
   return cudaPeekAtLastError();
 }
 
@@ -338,12 +318,12 @@ cudaError_t plane_pipeline_init() {
   return e;
 }
 
-cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, const void* twx, const void* twy,
-                            int inverse, const DevState* st, cudaStream_t s) {
+cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, int inverse, const DevState* st,
+                            cudaStream_t s) {
 #define LGF_XY32(N) \
-  if (L == N) return xy_launch<float, N>(D, V, twx, twy, inverse, st, s, Lz, Lt);
+  if (L == N) return xy_launch<float, N>(D, V, inverse, st, s, Lz, Lt);
 #define LGF_XY64(N) \
-  if (L == N) return xy_launch<double, N>(D, V, twx, twy, inverse, st, s, Lz, Lt);
+  if (L == N) return xy_launch<double, N>(D, V, inverse, st, s, Lz, Lt);
   if (prec == 4) {
     LGF_XY_F32(LGF_XY32)
   } else {
@@ -355,11 +335,11 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
 }
 
 cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
-                            float c_over_V, const void* twz, const void* twt, const DevState* st, cudaStream_t s) {
+                            float c_over_V, const DevState* st, cudaStream_t s) {
 #define LGF_ZT32(A, B) \
-  if (Lz == A && Lt == B) return zt_launch<float, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, twz, twt, st, s);
+  if (Lz == A && Lt == B) return zt_launch<float, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, st, s);
 #define LGF_ZT64(A, B) \
-  if (Lz == A && Lt == B) return zt_launch<double, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, twz, twt, st, s);
+  if (Lz == A && Lt == B) return zt_launch<double, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, st, s);
   if (prec == 4) {
     LGF_ZT_F32(LGF_ZT32)
   } else {

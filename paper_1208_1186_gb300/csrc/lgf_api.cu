@@ -304,26 +304,21 @@ int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
   cudaStream_t s = h->stream;
   const int pipe = pick_pipeline(h, e);
   if (pipe == 3) {
-    const char* tw = static_cast<const char*>(e.tw);
-    const size_t tws = (size_t)kMaxL * e.cbytes();
     const int* L = h->L;
-    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], tw, tw + tws, 0, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V,
-                                                tw + 2 * tws, tw + 3 * tws, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], tw, tw + tws, 1, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 1, st, s));
   } else if (pipe == 2) {
     const int64_t V = h->V;
     const int64_t Sy = h->L[0], Sz = (int64_t)h->L[0] * h->L[1];
-    const char* tw = static_cast<const char*>(e.tw);
-    const size_t tws = (size_t)kMaxL * e.cbytes();
-    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, tw, 0, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, tw + tws, 0, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, tw + 2 * tws, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, 0, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, 0, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_T, launch_tpass(e.prec, h->L[3], e.D, V, h->L[0], h->L[1], e.kfac, e.s2p, e.c_over_V,
-                                            tw + 3 * tws, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, tw + 2 * tws, 1, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, tw + tws, 1, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, tw, 1, st, s));
+                                            st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[2], e.D, V, Sz, 1, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_strided(e.prec, h->L[1], e.D, V, Sy, 1, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_AXIS, launch_xpass(e.prec, h->L[0], e.D, V, 1, st, s));
   } else {
     LGF_LAUNCH(h, LGF_K_FFT_XY, launch_fft_xy(e.prec, e.D, e.fg, e.tw, 0, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_fft_zt(e.prec, e.D, e.fg, e.tw, h->sin2, st, s));

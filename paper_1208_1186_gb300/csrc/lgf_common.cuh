@@ -78,6 +78,18 @@ __device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
   return mk<float>(v.x, v.y);
 }
 
+// asynchronous global -> shared copy of one complex element (8 or 16 bytes,
+// both addresses aligned to the element); complete after cp_async_wait_all
+template <class T>
+__device__ __forceinline__ void cp_async_elem(cx<T>* sdst, const cx<T>* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (sizeof(cx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // 3x3 complex matrices
 // ---------------------------------------------------------------------------

@@ -69,24 +69,23 @@ cudaError_t launch_unpack_fields(int prec, const void* D, double* out, int64_t V
 // to 64 (FP32) with radices 4, 2, 3, 5
 bool axis_pass_supported(int prec, int L);
 cudaError_t axis_pass_init();
-cudaError_t launch_xpass(int prec, int L, void* D, int64_t V, const void* tw, int inverse, const DevState* st,
-                         cudaStream_t s);
-cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, const void* tw, int inverse,
-                           const DevState* st, cudaStream_t s);
+cudaError_t launch_xpass(int prec, int L, void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s);
+cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, int inverse, const DevState* st,
+                           cudaStream_t s);
 // FP64: factor from the per-site table kfac; FP32: from s2p[axis][position]
 // (4 sin^2 at the digit-reversed frequency) and c_over_V = p2_max / V
 cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p,
-                         float c_over_V, const void* tw, const DevState* st, cudaStream_t s);
+                         float c_over_V, const DevState* st, cudaStream_t s);
 
 // three-pass plane pipeline with register FFTs (k_fft_plane.cu): x-y plane
 // (Lx = Ly) and z-t plane (fwd, acceleration factor, inv) kernels for a list
 // of instantiated shapes
 bool plane_pipeline_supported(int prec, int Lx, int Ly, int Lz, int Lt);
 cudaError_t plane_pipeline_init();
-cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, const void* twx, const void* twy,
-                            int inverse, const DevState* st, cudaStream_t s);
+cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, int inverse, const DevState* st,
+                            cudaStream_t s);
 cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
-                            float c_over_V, const void* twz, const void* twt, const DevState* st, cudaStream_t s);
+                            float c_over_V, const DevState* st, cudaStream_t s);
 
 // FP32 engine in gauge representation (k_gauge_rep.cu): links formed on the
 // fly as G U0 G^dagger; the update acts on G
