@@ -42,6 +42,10 @@ __device__ __forceinline__ M3<T> load_rw(const cx<T>* base, int64_t V, int64_t s
   return m;
 }
 
+// Grid-stride loop over sites with two CTAs per SM: each thread sums its
+// sites' F and theta terms in FP64 and the block reduction (two barriers)
+// runs once per CTA instead of once per 256 sites.  The site-to-thread map
+// and the summation order are fixed by the grid, so results are reproducible.
 template <class T, int NC>
 __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* __restrict__ U0,
                                                                 const cx<T>* __restrict__ G, cx<T>* __restrict__ D,
@@ -49,9 +53,9 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
                                                                 DevState* st, int mode, double normF, double normT) {
   if (mode == 1 && st->done) return;
   const int V = (int)geo.V;  // 36 V < 2^31 for extents <= 64
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  T fsum = 0, tsum = 0;
-  if (s < V) {
+  double fs = 0.0, ts = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+    T fsum, tsum;
     int c[4];
     site_coords_i(geo.L, s, c);
     M3<T> B, C;
@@ -98,8 +102,10 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
     D[2 * V + s] = d12;
     D[3 * V + s] = mk<T>(i0, i1);
     tsum = 2 * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
+    fs += (double)fsum;
+    ts += (double)tsum;
   }
-  grid_reduce<T>(fsum, tsum, partial, st, normF, normT, mode);
+  grid_reduce<double>(fs, ts, partial, st, normF, normT, mode);
 }
 
 // g from the accelerated gradient; G <- g G unless G is null; g stored if
@@ -167,12 +173,27 @@ __global__ void __launch_bounds__(256) k_materialize(const cx<T>* __restrict__ U
 
 inline unsigned nblocks(int64_t n, int thr) { return (unsigned)((n + thr - 1) / thr); }
 
+// multiprocessors of the current device (queried once)
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, m = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) ==
+                                                   cudaSuccess && m > 0)
+      n = m;
+    else
+      return 1;
+  }
+  return n;
+}
+
 }  // namespace
 
 cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D, double2* partial, const Geom& geo,
                                  DevState* st, int mode, cudaStream_t s) {
   const double nF = 1.0 / (12.0 * (double)geo.V), nT = 1.0 / (3.0 * (double)geo.V);
-  const unsigned nb = (unsigned)((geo.V + kGrepThreads - 1) / kGrepThreads);
+  const int64_t full = (geo.V + kGrepThreads - 1) / kGrepThreads;
+  const unsigned nb = (unsigned)(full < 2 * sm_count() ? full : 2 * sm_count());
   if (nc == 9)
     k_gradient_grep<float, 9><<<nb, kGrepThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
                                                           static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
