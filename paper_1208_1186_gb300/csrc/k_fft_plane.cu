@@ -10,8 +10,10 @@
 // register staging, all loads in flight at once); one thread per x-line does
 // the x transforms, then one thread per y-line the y transforms.
 // k_plane_zt: one CTA per (field, y, run of BX consecutive x) with the whole
-// (z, t) plane of that run in shared memory; z lines, then t lines (forward,
-// acceleration factor, inverse in registers), then z lines again.
+// (z, t) plane of that run in shared memory; z lines loaded from global memory
+// into registers and transformed, t lines (forward, acceleration factor,
+// inverse in registers), then z lines again, stored from registers: four
+// shared-memory accesses per element.
 //
 // Frequencies are left in digit-reversed order by the forward transforms and
 // taken in that order by the inverse ones, so the acceleration factor is
@@ -24,6 +26,9 @@
 namespace lgf {
 
 namespace {
+
+// x-y planes with L dividing 32 take the warp-tile kernel
+constexpr bool kXyWarpTiles = true;
 
 template <int LX, int LY>
 constexpr int xy_threads() {
@@ -98,6 +103,62 @@ __global__ void __launch_bounds__(xy_threads<LX, LY>(), xy_min_blocks<T, LX>()) 
   }
 }
 
+// x-y planes with L dividing 32: a group of L lanes owns one (plane, field)
+// tile from its load to its store, so a warp needs no CTA barrier and warps
+// overlap their loads with one another's transforms.  Lane r loads y-line r
+// straight into registers (for each y the group reads one contiguous row),
+// transforms it, and one pass through shared memory hands it x-line r; a
+// second pass turns the rows back into coalesced stores.  (The two 1D
+// transforms commute, so y before x gives the same 2D transform.)  Four
+// shared-memory accesses per element; one warp per CTA, 32 / L tiles per warp.
+template <class T, int L>
+constexpr int xyw_smem_bytes() {
+  return (32 / L) * L * (L + 1) * (int)sizeof(cx<T>);
+}
+
+template <class T, int L, bool INV>
+__global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int V, int ntiles,
+                                                      const DevState* __restrict__ st) {
+  static_assert(32 % L == 0, "a warp holds whole tiles");
+  if (st != nullptr && st->done) return;
+  constexpr int G = 32 / L, P = L + 1, N = L * L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = threadIdx.x / L, r = threadIdx.x % L;
+  const int tile_id = blockIdx.x * G + g;  // = 4 plane + field
+  // a group past the last tile idles but still takes part in every __syncwarp
+  const bool active = tile_id < ntiles;
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw) + g * L * P;
+  cx<T>* src = D + (active ? (tile_id & 3) * V + (tile_id >> 2) * N : 0);
+  if (active) {  // y-line r from global, transformed, into column r
+    cx<T> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = src[p * L + r];
+    if (INV)
+      regfft::inverse<T, L>(v);
+    else
+      regfft::forward<T, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[p * P + r] = v[p];
+  }
+  __syncwarp();
+  if (active) {  // x-line r from row r
+    cx<T> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = tile[r * P + p];
+    if (INV)
+      regfft::inverse<T, L>(v);
+    else
+      regfft::forward<T, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[r * P + p] = v[p];
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < L; ++k) src[k * L + r] = tile[k * P + r];
+  }
+}
+
 // x-run width of a z-t tile: 32 bytes of consecutive complex numbers
 template <class T>
 constexpr int zt_bx() {
@@ -124,7 +185,7 @@ constexpr int zt_threads() {
 // the inverse: 3 CTAs per SM (up to 168 registers) for FP32 lines up to 32
 template <class T, int LZ, int LT>
 constexpr int zt_min_blocks() {
-  return (sizeof(T) == 4 && LZ <= 32 && LT <= 32) ? 3 : 1;
+  return (sizeof(T) == 4 && LZ <= 32 && LT <= 32) ? 4 : 1;
 }
 
 template <class T, int LZ, int LT>
@@ -144,7 +205,6 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, 
   constexpr int BX = zt_bx<T>();
   constexpr int NT = zt_threads<T, LZ, LT>();
   constexpr int PT = zt_pitch<T, LZ>();
-  constexpr int N = BX * LZ * LT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);  // [t][z][xb], t pitch PT
   const int nxr = Lx / BX;
@@ -154,23 +214,18 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, 
   const int LxLy = Lx * Ly;
   const int V = LxLy * LZ * LT;
   cx<T>* Df = D + (f * V + x0 + Lx * y);
-  static_assert(N % NT == 0, "tile must split evenly over the threads");
-  constexpr int PER = N / NT;
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int i = threadIdx.x + NT * k;
-    const int xb = i % BX, q = i / BX;  // q = z + LZ t
-    cp_async_elem(tile + ((q / LZ) * PT + (q % LZ) * BX + xb), Df + (xb + LxLy * q));
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // forward z: lines (xb, t)
+  // forward z: line (xb, t) straight from global memory (for each z a warp
+  // reads BX consecutive x at 32 / BX values of t: whole 32-byte sectors)
   if (threadIdx.x < BX * LT) {
     const int xb = threadIdx.x % BX, t = threadIdx.x / BX;
     cx<T>* line = tile + t * PT + xb;
+    const cx<T>* g = Df + (xb + LxLy * LZ * t);
     cx<T> v[LZ];
 #pragma unroll
-    for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
+    for (int p = 0; p < LZ; ++p) {  // running pointer: one address register
+      v[p] = *g;
+      g += LxLy;
+    }
     regfft::forward<T, LZ>(v);
 #pragma unroll
     for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
@@ -192,7 +247,7 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, 
       regfft::static_for<0, LT>([&](auto pc) {
         constexpr int p = decltype(pc)::value;
         constexpr float s2t = (float)regfft::MomentumSq<LT, p>::value;
-        float kf = c_over_V * __frcp_rn(a + s2t);
+        float kf = c_over_V * rcp_approx(a + s2t);
         if (p == 0 && origin) kf = 0.0f;
         v[p] = scale(v[p], (T)kf);
       });
@@ -206,23 +261,20 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, 
     for (int p = 0; p < LT; ++p) line[p * PT] = v[p];
   }
   __syncthreads();
-  // inverse z
+  // inverse z, stored straight to global memory
   if (threadIdx.x < BX * LT) {
     const int xb = threadIdx.x % BX, t = threadIdx.x / BX;
-    cx<T>* line = tile + t * PT + xb;
+    const cx<T>* line = tile + t * PT + xb;
+    cx<T>* g = Df + (xb + LxLy * LZ * t);
     cx<T> v[LZ];
 #pragma unroll
     for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
     regfft::inverse<T, LZ>(v);
 #pragma unroll
-    for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int i = threadIdx.x + NT * k;
-    const int xb = i % BX, q = i / BX;
-    Df[xb + LxLy * q] = tile[(q / LZ) * PT + (q % LZ) * BX + xb];
+    for (int p = 0; p < LZ; ++p) {
+      *g = v[p];
+      g += LxLy;
+    }
   }
 }
 
@@ -241,6 +293,17 @@ namespace {
 
 template <class T, int L>
 cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s, int Lz, int Lt) {
+  if constexpr (32 % L == 0 && kXyWarpTiles) {
+    const int ntiles = 4 * Lz * Lt;
+    const unsigned nb = (unsigned)((ntiles + 32 / L - 1) / (32 / L));
+    constexpr int sm = xyw_smem_bytes<T, L>();
+    const auto Dp = static_cast<cx<T>*>(D);
+    if (inverse)
+      k_plane_xy_warp<T, L, true><<<nb, 32, sm, s>>>(Dp, (int)V, ntiles, st);
+    else
+      k_plane_xy_warp<T, L, false><<<nb, 32, sm, s>>>(Dp, (int)V, ntiles, st);
+    return cudaPeekAtLastError();
+  }
   const unsigned nb = (unsigned)(Lz * Lt);
   constexpr int NT = xy_threads<L, L>();
   constexpr size_t sm = xy_smem_bytes<T, L, L>();
@@ -263,6 +326,14 @@ cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2
 
 template <class T, int L>
 cudaError_t xy_attr() {
+  if constexpr (32 % L == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_plane_xy_warp<T, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         xyw_smem_bytes<T, L>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_plane_xy_warp<T, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               xyw_smem_bytes<T, L>());
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = cudaFuncSetAttribute(k_plane_xy<T, L, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)xy_smem_bytes<T, L, L>());
   if (e == cudaSuccess)

@@ -78,6 +78,15 @@ __device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
   return mk<float>(v.x, v.y);
 }
 
+// hardware reciprocal approximation (PTX rcp.approx.ftz.f32: at most 1 ulp
+// from the exact reciprocal, subnormals flushed); used for the Fourier
+// acceleration factor, a preconditioner whose last bit does not matter
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // asynchronous global -> shared copy of one complex element (8 or 16 bytes,
 // both addresses aligned to the element); complete after cp_async_wait_all
 template <class T>
