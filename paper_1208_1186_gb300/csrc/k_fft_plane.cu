@@ -50,6 +50,7 @@ constexpr size_t xy_smem_bytes() {
 template <class T, int LX, int LY, bool INV>
 __global__ void __launch_bounds__(xy_threads<LX, LY>(), xy_min_blocks<T, LX>()) k_plane_xy(cx<T>* __restrict__ D, int V,
                                                                    const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   constexpr int NT = xy_threads<LX, LY>();
   constexpr int P = LX + 1;
@@ -120,6 +121,7 @@ template <class T, int L, bool INV>
 __global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int V, int ntiles,
                                                       const DevState* __restrict__ st) {
   static_assert(32 % L == 0, "a warp holds whole tiles");
+  pdl_wait();
   if (st != nullptr && st->done) return;
   constexpr int G = 32 / L, P = L + 1, N = L * L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,6 +203,7 @@ __global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, 
                                                                       const T* __restrict__ kfac,
                                                                       const float* __restrict__ s2p, float c_over_V,
                                                                       const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   constexpr int BX = zt_bx<T>();
   constexpr int NT = zt_threads<T, LZ, LT>();
@@ -298,30 +301,23 @@ cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaS
     const unsigned nb = (unsigned)((ntiles + 32 / L - 1) / (32 / L));
     constexpr int sm = xyw_smem_bytes<T, L>();
     const auto Dp = static_cast<cx<T>*>(D);
-    if (inverse)
-      k_plane_xy_warp<T, L, true><<<nb, 32, sm, s>>>(Dp, (int)V, ntiles, st);
-    else
-      k_plane_xy_warp<T, L, false><<<nb, 32, sm, s>>>(Dp, (int)V, ntiles, st);
-    return cudaPeekAtLastError();
+    if (inverse) return launch_pdl(k_plane_xy_warp<T, L, true>, nb, 32, sm, s, Dp, (int)V, ntiles, st);
+    return launch_pdl(k_plane_xy_warp<T, L, false>, nb, 32, sm, s, Dp, (int)V, ntiles, st);
   }
   const unsigned nb = (unsigned)(Lz * Lt);
   constexpr int NT = xy_threads<L, L>();
   constexpr size_t sm = xy_smem_bytes<T, L, L>();
   const auto Dp = static_cast<cx<T>*>(D);
-  if (inverse)
-    k_plane_xy<T, L, L, true><<<nb, NT, sm, s>>>(Dp, (int)V, st);
-  else
-    k_plane_xy<T, L, L, false><<<nb, NT, sm, s>>>(Dp, (int)V, st);
-  return cudaPeekAtLastError();
+  if (inverse) return launch_pdl(k_plane_xy<T, L, L, true>, nb, NT, sm, s, Dp, (int)V, st);
+  return launch_pdl(k_plane_xy<T, L, L, false>, nb, NT, sm, s, Dp, (int)V, st);
 }
 
 template <class T, int LZ, int LT>
 cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V, const DevState* st,
                       cudaStream_t s) {
   dim3 grid((unsigned)((Lx / zt_bx<T>()) * Ly), 4);
-  k_plane_zt<T, LZ, LT><<<grid, zt_threads<T, LZ, LT>(), zt_smem_bytes<T, LZ, LT>(), s>>>(
-      static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, st);
-  return cudaPeekAtLastError();
+  return launch_pdl(k_plane_zt<T, LZ, LT>, grid, zt_threads<T, LZ, LT>(), zt_smem_bytes<T, LZ, LT>(), s,
+                    static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, st);
 }
 
 template <class T, int L>

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
                                                                 const cx<T>* __restrict__ G, cx<T>* __restrict__ D,
                                                                 double2* __restrict__ partial, const Geom geo,
                                                                 DevState* st, int mode, double normF, double normT) {
+  pdl_wait();
   if (mode == 1 && st->done) return;
   const int V = (int)geo.V;  // 36 V < 2^31 for extents <= 64
   double fs = 0.0, ts = 0.0;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
 template <class T, int NC, class RT>
 __global__ void __launch_bounds__(256) k_gstep(const cx<T>* __restrict__ D, cx<T>* G, cx<T>* __restrict__ g_out,
                                                int64_t V, double hd, const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
@@ -195,14 +197,10 @@ cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D,
   const int64_t full = (geo.V + kGrepThreads - 1) / kGrepThreads;
   const unsigned nb = (unsigned)(full < 2 * sm_count() ? full : 2 * sm_count());
   if (nc == 9)
-    k_gradient_grep<float, 9><<<nb, kGrepThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
-                                                          static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
-                                                          partial, geo, st, mode, nF, nT);
-  else
-    k_gradient_grep<float, 6><<<nb, kGrepThreads, 0, s>>>(static_cast<const cx<float>*>(U0),
-                                                          static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D),
-                                                          partial, geo, st, mode, nF, nT);
-  return cudaPeekAtLastError();
+    return launch_pdl(k_gradient_grep<float, 9>, nb, kGrepThreads, 0, s, static_cast<const cx<float>*>(U0),
+                      static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D), partial, geo, st, mode, nF, nT);
+  return launch_pdl(k_gradient_grep<float, 6>, nb, kGrepThreads, 0, s, static_cast<const cx<float>*>(U0),
+                    static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D), partial, geo, st, mode, nF, nT);
 }
 
 cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,
@@ -213,14 +211,14 @@ cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V,
   const unsigned nb = nblocks(V, 256);
   if (nc == 9) {
     if (reunit_fp64)
-      k_gstep<float, 9, double><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+      return launch_pdl(k_gstep<float, 9, double>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
     else
-      k_gstep<float, 9, float><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+      return launch_pdl(k_gstep<float, 9, float>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
   } else {
     if (reunit_fp64)
-      k_gstep<float, 6, double><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+      return launch_pdl(k_gstep<float, 6, double>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
     else
-      k_gstep<float, 6, float><<<nb, 256, 0, s>>>(Dp, Gp, gp, V, half_alpha, st);
+      return launch_pdl(k_gstep<float, 6, float>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
   }
   return cudaPeekAtLastError();
 }

@@ -11,6 +11,28 @@
 
 namespace lgf {
 
+// Launch with programmatic stream serialization: the kernel's launch overlaps
+// the previous kernel's drain; the kernel must begin with pdl_wait().
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+}  // namespace lgf
+
+namespace lgf {
+
 constexpr int kMaxL = 64;       // longest lattice extent the on-chip FFT takes
 constexpr int kMaxStages = 6;   // radix stages per axis (4^3 = 64)
 
