@@ -341,14 +341,27 @@ def run_ours(args, W):
         pinned = torch.empty(U.shape + (2,), dtype=torch.float64, pin_memory=True)
         hostU = pinned.numpy().view(np.complex128).reshape(U.shape)
         hostU[...] = U
-        hostOut = torch.empty_like(pinned).numpy().view(np.complex128).reshape(U.shape)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        gf.load_links(hostU)
-        iters_e2e, _ = gf.fix(W["tol"], W["max_iter"])
-        gf.store_links(hostOut)
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        # (empty_like would not pin the output buffer)
+        pinned_out = torch.empty(U.shape + (2,), dtype=torch.float64, pin_memory=True)
+        hostOut = pinned_out.numpy().view(np.complex128).reshape(U.shape)
+        hostOut[...] = 0  # touch every page before the timed region
+
+        def e2e_pass():
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            gf.load_links(hostU)
+            t1 = time.perf_counter()
+            n, _ = gf.fix(W["tol"], W["max_iter"])
+            t2 = time.perf_counter()
+            gf.store_links(hostOut)
+            t3 = time.perf_counter()
+            return n, t3 - t0, {"load_s": round(t1 - t0, 4), "fix_s": round(t2 - t1, 4),
+                                "store_s": round(t3 - t2, 4)}
+
+        _, _, e2e_warm_parts = e2e_pass()  # one untimed warm-up pass
+        iters_e2e, e2e_local, e2e_parts = e2e_pass()
+        e2e_s = max_over_ranks(e2e_local)
     finally:
         if smi:
             smi.stop()
@@ -416,6 +429,7 @@ def run_ours(args, W):
                           "kernel_ms_profiled_run": fix_prof, "kernel_launches_profiled_run": fix_launches},
         "e2e": {"value": round(V * iters_e2e * world / e2e_s, 1), "unit": METRIC, "seconds": round(e2e_s, 4),
                 "what": "lgf_load_links(pinned host) + lgf_fix(theta<tol) + lgf_store_links(pinned host)",
+                "parts": e2e_parts, "warmup_pass_parts": e2e_warm_parts,
                 "h2d_bytes_per_step": round(h2d / max(iters_e2e, 1), 1),
                 "d2h_bytes_per_step": round(d2h / max(iters_e2e, 1), 1)},
         "gpu_launches": launches,

@@ -150,6 +150,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_fft_xy(cx<T>* __restrict__ D, const __grid_constant__ FftGeom fg,
                                                 const cx<T>* __restrict__ tw, int inverse,
                                                 const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = fg.L[0], Ly = fg.L[1];
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(256) k_fft_zt(cx<T>* __restrict__ D, const __g
                                                 const cx<T>* __restrict__ tw,
                                                 const double* __restrict__ sin2,
                                                 const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = fg.L[0], Ly = fg.L[1], Lz = fg.L[2], Lt = fg.L[3];
@@ -305,10 +307,10 @@ cudaError_t launch_fft_xy(int prec, void* D, const FftGeom& fg, const void* tw, 
   dim3 grid(fg.L[2] * fg.L[3], 4);
   const int thr = fft_threads(fg.L[0] * fg.L[1]);
   if (prec == 8) {
-    k_fft_xy<double><<<grid, thr, fft_xy_smem(fg, 8), s>>>(static_cast<cx<double>*>(D), fg,
+    launch_pdl(k_fft_xy<double>, grid, thr, fft_xy_smem(fg, 8), s, static_cast<cx<double>*>(D), fg,
                                                            static_cast<const cx<double>*>(tw), inverse, st);
   } else {
-    k_fft_xy<float><<<grid, thr, fft_xy_smem(fg, 4), s>>>(static_cast<cx<float>*>(D), fg,
+    launch_pdl(k_fft_xy<float>, grid, thr, fft_xy_smem(fg, 4), s, static_cast<cx<float>*>(D), fg,
                                                           static_cast<const cx<float>*>(tw), inverse, st);
   }
   return cudaPeekAtLastError();
@@ -319,10 +321,10 @@ cudaError_t launch_fft_zt(int prec, void* D, const FftGeom& fg, const void* tw, 
   dim3 grid((fg.L[0] / fg.Bx) * fg.L[1]);
   const int thr = fft_threads(fg.Bx * fg.L[2] * fg.L[3]);
   if (prec == 8) {
-    k_fft_zt<double><<<grid, thr, fft_zt_smem(fg, 8), s>>>(static_cast<cx<double>*>(D), fg,
+    launch_pdl(k_fft_zt<double>, grid, thr, fft_zt_smem(fg, 8), s, static_cast<cx<double>*>(D), fg,
                                                            static_cast<const cx<double>*>(tw), sin2, st);
   } else {
-    k_fft_zt<float><<<grid, thr, fft_zt_smem(fg, 4), s>>>(static_cast<cx<float>*>(D), fg,
+    launch_pdl(k_fft_zt<float>, grid, thr, fft_zt_smem(fg, 4), s, static_cast<cx<float>*>(D), fg,
                                                           static_cast<const cx<float>*>(tw), sin2, st);
   }
   return cudaPeekAtLastError();

@@ -33,6 +33,7 @@ constexpr int xpass_lines() {
 template <class T, int L, bool INV>
 __global__ void __launch_bounds__(128) k_xpass(cx<T>* __restrict__ D, int64_t total_lines,
                                                const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   constexpr int NL = xpass_lines<T, L>();
   constexpr int P = L + 1;
@@ -90,6 +91,7 @@ constexpr int pass_min_blocks() {
 template <class T, int L, bool INV>
 __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_strided(cx<T>* __restrict__ D, int64_t V, int64_t S,
                                                  const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   // 32-bit offsets: 4 V < 2^31 for extents <= 64
   const int nl = (int)(V / L);  // lines per field
@@ -118,6 +120,7 @@ template <class T, int L>
 __global__ void __launch_bounds__(128, pass_min_blocks<T, L>()) k_tpass(cx<T>* __restrict__ D, int64_t V, int Lx, int Ly,
                                                const T* __restrict__ kfac, const float* __restrict__ s2p,
                                                float c_over_V, const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   __shared__ float s2t[kMaxL];
   if (sizeof(T) == 4)
@@ -170,9 +173,9 @@ cudaError_t xpass_launch(void* D, int64_t V, int inverse, const DevState* st, cu
   const unsigned nb = (unsigned)((total + NL - 1) / NL);
   const size_t sm = xpass_smem<T, L>();
   if (inverse)
-    k_xpass<T, L, true><<<nb, 128, sm, s>>>(static_cast<cx<T>*>(D), total, st);
+    launch_pdl(k_xpass<T, L, true>, nb, 128, sm, s, static_cast<cx<T>*>(D), total, st);
   else
-    k_xpass<T, L, false><<<nb, 128, sm, s>>>(static_cast<cx<T>*>(D), total, st);
+    launch_pdl(k_xpass<T, L, false>, nb, 128, sm, s, static_cast<cx<T>*>(D), total, st);
   return cudaPeekAtLastError();
 }
 
@@ -180,9 +183,9 @@ template <class T, int L>
 cudaError_t strided_launch(void* D, int64_t V, int64_t S, int inverse, const DevState* st, cudaStream_t s) {
   const unsigned nb = (unsigned)((4 * (V / L) + 127) / 128);
   if (inverse)
-    k_strided<T, L, true><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, S, st);
+    launch_pdl(k_strided<T, L, true>, nb, 128, 0, s, static_cast<cx<T>*>(D), V, S, st);
   else
-    k_strided<T, L, false><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, S, st);
+    launch_pdl(k_strided<T, L, false>, nb, 128, 0, s, static_cast<cx<T>*>(D), V, S, st);
   return cudaPeekAtLastError();
 }
 
@@ -190,8 +193,8 @@ template <class T, int L>
 cudaError_t tpass_launch(void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V,
                          const DevState* st, cudaStream_t s) {
   const unsigned nb = (unsigned)((4 * (V / L) + 127) / 128);
-  k_tpass<T, L><<<nb, 128, 0, s>>>(static_cast<cx<T>*>(D), V, Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V,
-                                   st);
+  launch_pdl(k_tpass<T, L>, nb, 128, 0, s, static_cast<cx<T>*>(D), V, Lx, Ly, static_cast<const T*>(kfac), s2p,
+             c_over_V, st);
   return cudaPeekAtLastError();
 }
 

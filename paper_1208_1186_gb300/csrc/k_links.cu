@@ -38,6 +38,7 @@ template <class T, int NC>
 __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restrict__ U, cx<T>* __restrict__ D,
                                                            double2* __restrict__ partial, const Geom geo,
                                                            DevState* st, int mode, double normF, double normT) {
+  pdl_wait();
   if (mode == 1 && st->done) return;
   const int64_t V = geo.V;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restri
 template <class T, int NC, class RT>
 __global__ void __launch_bounds__(256) k_build_g(const cx<T>* __restrict__ D, cx<T>* __restrict__ g, int64_t V,
                                                  double hd, const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
@@ -103,6 +105,7 @@ __global__ void __launch_bounds__(256) k_build_g(const cx<T>* __restrict__ D, cx
 template <class T, int NC>
 __global__ void __launch_bounds__(256) k_update(cx<T>* U, const cx<T>* __restrict__ g, const Geom geo,
                                                 const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   const int64_t V = geo.V;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -156,6 +159,7 @@ __global__ void k_soa_to_aos(const cx<T>* __restrict__ U, double* __restrict__ a
 template <class T, int NC>
 __global__ void __launch_bounds__(256) k_accumulate(cx<T>* G, const cx<T>* __restrict__ g, int64_t V,
                                                     const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
@@ -234,8 +238,8 @@ cudaError_t launch_gradient(int prec, int nc, const void* U, void* D, double2* p
   const unsigned nb = (unsigned)gradient_blocks(geo.V);
   const double nF = 1.0 / (12.0 * (double)geo.V), nT = 1.0 / (3.0 * (double)geo.V);
   LGF_DISPATCH(prec, nc,
-               (k_gradient<T, NC><<<nb, kGradThreads, 0, s>>>(static_cast<const cx<T>*>(U), static_cast<cx<T>*>(D),
-                                                              partial, geo, st, mode, nF, nT)));
+               (launch_pdl(k_gradient<T, NC>, nb, kGradThreads, 0, s, static_cast<const cx<T>*>(U),
+                           static_cast<cx<T>*>(D), partial, geo, st, mode, nF, nT)));
   return cudaPeekAtLastError();
 }
 
@@ -243,15 +247,15 @@ cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, 
                            bool reunit_fp64, const DevState* st, cudaStream_t s) {
   if (prec == 4 && !reunit_fp64) {
     if (nc == 9)
-      k_build_g<float, 9, float><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<float>*>(D),
+      launch_pdl(k_build_g<float, 9, float>, blocks_for(V, 256), 256, 0, s, static_cast<const cx<float>*>(D),
                                                                    static_cast<cx<float>*>(g), V, half_alpha, st);
     else
-      k_build_g<float, 6, float><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<float>*>(D),
+      launch_pdl(k_build_g<float, 6, float>, blocks_for(V, 256), 256, 0, s, static_cast<const cx<float>*>(D),
                                                                    static_cast<cx<float>*>(g), V, half_alpha, st);
     return cudaPeekAtLastError();
   }
   LGF_DISPATCH(prec, nc,
-               (k_build_g<T, NC, double><<<blocks_for(V, 256), 256, 0, s>>>(
+               (launch_pdl(k_build_g<T, NC, double>, blocks_for(V, 256), 256, 0, s, 
                    static_cast<const cx<T>*>(D), static_cast<cx<T>*>(g), V, half_alpha, st)));
   return cudaPeekAtLastError();
 }
@@ -259,7 +263,7 @@ cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, 
 cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& geo, const DevState* st,
                           cudaStream_t s) {
   LGF_DISPATCH(prec, nc,
-               (k_update<T, NC><<<blocks_for(geo.V, 256), 256, 0, s>>>(static_cast<cx<T>*>(U),
+               (launch_pdl(k_update<T, NC>, blocks_for(geo.V, 256), 256, 0, s, static_cast<cx<T>*>(U),
                                                                        static_cast<const cx<T>*>(g), geo, st)));
   return cudaPeekAtLastError();
 }
@@ -280,7 +284,7 @@ cudaError_t launch_soa_to_aos(int prec, int nc, const void* U, double* aos, int6
 cudaError_t launch_accumulate(int prec, int nc, void* G, const void* g, int64_t V, const DevState* st,
                               cudaStream_t s) {
   LGF_DISPATCH(prec, nc,
-               (k_accumulate<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<cx<T>*>(G),
+               (launch_pdl(k_accumulate<T, NC>, blocks_for(V, 256), 256, 0, s, static_cast<cx<T>*>(G),
                                                                        static_cast<const cx<T>*>(g), V, st)));
   return cudaPeekAtLastError();
 }

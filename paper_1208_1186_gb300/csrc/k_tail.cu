@@ -29,6 +29,7 @@ namespace {
 __global__ void __launch_bounds__(256) k_gradient_tail(const cx<double>* __restrict__ U, cx<float>* __restrict__ D,
                                                        double2* __restrict__ partial, const Geom geo, DevState* st,
                                                        int mode, double normF, double normT) {
+  pdl_wait();
   if (mode == 1 && st->done) return;
   const int V = (int)geo.V;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) k_gradient_tail(const cx<double>* __restr
 // eps = X + X^2 / 2, X = h Delta~ (traceless anti-Hermitian), 9 FP32 planes
 __global__ void __launch_bounds__(256) k_tail_step(const cx<float>* __restrict__ D, cx<float>* __restrict__ eps,
                                                    int V, float h, const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(256) k_tail_step(const cx<float>* __restrict__
 // U_mu(x) += eps(x) U + U eps(x+mu)^dag + eps(x) U eps(x+mu)^dag
 __global__ void __launch_bounds__(256) k_tail_update(cx<double>* U, const cx<float>* __restrict__ eps, const Geom geo,
                                                      const DevState* __restrict__ st) {
+  pdl_wait();
   if (st != nullptr && st->done) return;
   const int V = (int)geo.V;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,21 +139,21 @@ __global__ void __launch_bounds__(256) k_tail_update(cx<double>* U, const cx<flo
 cudaError_t launch_gradient_tail(const void* U64, void* D32, double2* partial, const Geom& geo, DevState* st,
                                  int mode, cudaStream_t s) {
   const unsigned nb = (unsigned)((geo.V + 255) / 256);
-  k_gradient_tail<<<nb, 256, 0, s>>>(static_cast<const cx<double>*>(U64), static_cast<cx<float>*>(D32), partial, geo,
-                                     st, mode, 1.0 / (12.0 * (double)geo.V), 1.0 / (3.0 * (double)geo.V));
+  launch_pdl(k_gradient_tail, nb, 256, 0, s, static_cast<const cx<double>*>(U64), static_cast<cx<float>*>(D32),
+             partial, geo, st, mode, 1.0 / (12.0 * (double)geo.V), 1.0 / (3.0 * (double)geo.V));
   return cudaPeekAtLastError();
 }
 
 cudaError_t launch_tail_step(const void* D32, void* eps, int64_t V, double half_alpha, const DevState* st,
                              cudaStream_t s) {
-  k_tail_step<<<(unsigned)((V + 255) / 256), 256, 0, s>>>(static_cast<const cx<float>*>(D32),
+  launch_pdl(k_tail_step, (unsigned)((V + 255) / 256), 256, 0, s, static_cast<const cx<float>*>(D32),
                                                           static_cast<cx<float>*>(eps), (int)V, (float)half_alpha,
                                                           st);
   return cudaPeekAtLastError();
 }
 
 cudaError_t launch_tail_update(void* U64, const void* eps, const Geom& geo, const DevState* st, cudaStream_t s) {
-  k_tail_update<<<(unsigned)((geo.V + 255) / 256), 256, 0, s>>>(static_cast<cx<double>*>(U64),
+  launch_pdl(k_tail_update, (unsigned)((geo.V + 255) / 256), 256, 0, s, static_cast<cx<double>*>(U64),
                                                                   static_cast<const cx<float>*>(eps), geo, st);
   return cudaPeekAtLastError();
 }
