@@ -64,7 +64,7 @@ WORKLOADS["warmstart-f32"] = dict(
 DEFAULT_WORKLOAD = "32^4-f32"
 KERNEL_SOURCES = {"update": "k_links.cu", "gradient": "k_links.cu", "build_g": "k_links.cu",
                   "accumulate": "k_links.cu", "fft_xy": "k_fft_plane.cu", "fft_zt": "k_fft_plane.cu",
-                  "fft_axis": "k_fft_axis.cu", "fft_t": "k_fft_axis.cu"}
+                  "fft_axis": "k_fft_axis.cu", "fft_t": "k_fft_axis.cu", "xy_gstep": "k_fft_plane.cu"}
 
 
 def log(*a):
@@ -80,6 +80,7 @@ def bytes_per_site(kernel: str, prec: int, r: int, gauge_rep: bool = False) -> f
         table = {
             "gradient": 5 * r + 8,   # own U0 links and own G in, packed gradient out
             "build_g": 8 + 2 * r,    # packed gradient in, G in and out (g never stored)
+            "xy_gstep": 8 + 2 * r,   # packed gradient in (inverse x-y FFT in shared memory), G in and out
         }
         if kernel in table:
             return table[kernel] * prec

@@ -182,7 +182,8 @@ enum lgf_kernel {
   LGF_K_ACCUMULATE = 6, /* mixed precision: G <- g G                        */
   LGF_K_OTHER = 7,      /* layout conversions, copies                       */
   LGF_K_FFT_T = 8,      /* t pass: forward t FFT, p2_max/p2, inverse t FFT  */
-  LGF_NUM_KERNELS = 9
+  LGF_K_XY_GSTEP = 9,   /* inverse x-y plane FFT fused with G <- g G        */
+  LGF_NUM_KERNELS = 10
 };
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream right

@@ -70,7 +70,7 @@ SIGNATURES = {
     "lgf_net_warm_start": (ctypes.c_int, [_P, _P]),
     "lgf_net_last_error": (ctypes.c_char_p, [_P]),
 }
-LGF_NUM_KERNELS = 9
+LGF_NUM_KERNELS = 10
 
 _lib = None
 

@@ -21,6 +21,7 @@
 // pipeline).  The packed gradient crosses memory three times per iteration
 // instead of seven.
 #include "fft_reg.cuh"
+#include "lgf_gstep.cuh"
 #include "lgf_kernels.cuh"
 
 namespace lgf {
@@ -29,6 +30,10 @@ namespace {
 
 // x-y planes with L dividing 32 take the warp-tile kernel
 constexpr bool kXyWarpTiles = true;
+// FP32 gauge representation: the inverse x-y pass is fused with the G update,
+// which loads G for kXyGstepSites sites at a time
+constexpr bool kFuseXyinvGstep = true;
+constexpr int kXyGstepSites = 4;
 
 template <int LX, int LY>
 constexpr int xy_threads() {
@@ -161,6 +166,79 @@ __global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int
   }
 }
 
+// Inverse x-y transform fused with the gauge step on G (FP32 gauge
+// representation).  One CTA of four warps per 32 / L planes: warp f inverse-
+// transforms field f of the CTA's planes exactly as k_plane_xy_warp does and
+// leaves Delta~ in shared memory (it is never written back: nothing reads it
+// after the update); after one CTA barrier the 128 threads apply the gauge
+// step to the planes' sites, Delta~ from shared memory, G streamed through
+// registers.  The G stream of some CTAs overlaps the transforms of others.
+template <int L, int NC, class RT, int KS>
+__global__ void __launch_bounds__(128) k_plane_xyinv_gstep(const cx<float>* __restrict__ D, cx<float>* G, int V,
+                                                           int nplanes, double hd, const DevState* __restrict__ st) {
+  static_assert(32 % L == 0, "a warp holds whole tiles");
+  pdl_wait();
+  if (st != nullptr && st->done) return;
+  constexpr int GP = 32 / L, P = L + 1, N = L * L, TS = L * P;  // planes per CTA, pitch, plane, tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tiles = reinterpret_cast<cx<float>*>(smem_raw);  // [field][plane of the CTA][y][x]
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / L, r = lane % L;
+  const int plane0 = blockIdx.x * GP;
+  const bool active = plane0 + g < nplanes;
+  cx<float>* tile = tiles + (f * GP + g) * TS;
+  if (active) {  // inverse y-line r from global memory into column r
+    const cx<float>* src = D + ((int64_t)f * V + (int64_t)(plane0 + g) * N);
+    cx<float> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = src[p * L + r];
+    regfft::inverse<float, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[p * P + r] = v[p];
+  }
+  __syncwarp();
+  if (active) {  // inverse x-line r in row r
+    cx<float> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = tile[r * P + p];
+    regfft::inverse<float, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[r * P + p] = v[p];
+  }
+  __syncthreads();
+  // KS sites per round: all their G loads are issued before any is used
+  // (G is read and written through the same pointer, so the compiler would
+  // not hoist a later site's loads above an earlier site's stores)
+  const RT h = (RT)hd;
+  const int np = nplanes - plane0 < GP ? nplanes - plane0 : GP;
+  const int ns = np * N;
+  const int64_t base = (int64_t)plane0 * N;
+  for (int q0 = threadIdx.x; q0 < ns; q0 += KS * blockDim.x) {
+    M3<float> Gk[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int q = q0 + k * blockDim.x;
+      if (q < ns) Gk[k] = gstep_load_G<float, NC>(G, V, base + q);
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int q = q0 + k * blockDim.x;
+      if (q < ns) {
+        const int gi = q / N, qq = q - gi * N;
+        const int o = gi * TS + (qq / L) * P + qq % L;
+        gstep_store<float, NC, RT>(
+            gstep_g<RT>(tiles[o], tiles[GP * TS + o], tiles[2 * GP * TS + o], tiles[3 * GP * TS + o], h), Gk[k], G,
+            V, base + q);
+      }
+    }
+  }
+}
+
+template <int L>
+constexpr size_t xyinv_gstep_smem() {
+  return (size_t)4 * (32 / L) * L * (L + 1) * sizeof(cx<float>);
+}
+
 // x-run width of a z-t tile: 32 bytes of consecutive complex numbers
 template <class T>
 constexpr int zt_bx() {
@@ -199,7 +277,8 @@ constexpr size_t zt_smem_bytes() {
 // frequency) and c_over_V = p2_max / V, 0 at k = 0.  FP64: per-site table
 // kfac (an FP64 division per mode would be slow on this GPU).
 template <class T, int LZ, int LT>
-__global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, LT>()) k_plane_zt(cx<T>* __restrict__ D, int Lx, int Ly,
+__global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, LT>())
+    k_plane_zt(cx<T>* __restrict__ D, int Lx, int Ly,
                                                                       const T* __restrict__ kfac,
                                                                       const float* __restrict__ s2p, float c_over_V,
                                                                       const DevState* __restrict__ st) {
@@ -320,6 +399,19 @@ cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2
                     static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, st);
 }
 
+template <int L>
+cudaError_t xyinv_gstep_launch(int nc, bool r64, const cx<float>* D, cx<float>* G, int V, int nplanes, double ha,
+                               const DevState* st, cudaStream_t s) {
+  const unsigned nb = (unsigned)((nplanes + 32 / L - 1) / (32 / L));
+  constexpr size_t sm = xyinv_gstep_smem<L>();
+  if (nc == 9) {
+    if (r64) return launch_pdl(k_plane_xyinv_gstep<L, 9, double, kXyGstepSites>, nb, 128, sm, s, D, G, V, nplanes, ha, st);
+    return launch_pdl(k_plane_xyinv_gstep<L, 9, float, kXyGstepSites>, nb, 128, sm, s, D, G, V, nplanes, ha, st);
+  }
+  if (r64) return launch_pdl(k_plane_xyinv_gstep<L, 6, double, kXyGstepSites>, nb, 128, sm, s, D, G, V, nplanes, ha, st);
+  return launch_pdl(k_plane_xyinv_gstep<L, 6, float, kXyGstepSites>, nb, 128, sm, s, D, G, V, nplanes, ha, st);
+}
+
 template <class T, int L>
 cudaError_t xy_attr() {
   if constexpr (32 % L == 0) {
@@ -399,6 +491,24 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
 #undef LGF_XY32
 #undef LGF_XY64
   return cudaErrorInvalidValue;
+}
+
+bool plane_xyinv_gstep_supported(int prec, int L) {
+  return kFuseXyinvGstep && prec == 4 && (L == 4 || L == 8 || L == 16 || L == 32);
+}
+
+cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int64_t V, int Lz, int Lt,
+                                     double half_alpha, bool reunit_fp64, const DevState* st, cudaStream_t s) {
+  const int nplanes = Lz * Lt;
+  const auto Dp = static_cast<const cx<float>*>(D);
+  const auto Gp = static_cast<cx<float>*>(G);
+  switch (L) {
+    case 4: return xyinv_gstep_launch<4>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 8: return xyinv_gstep_launch<8>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 16: return xyinv_gstep_launch<16>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 32: return xyinv_gstep_launch<32>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,

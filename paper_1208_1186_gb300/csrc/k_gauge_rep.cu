@@ -18,6 +18,7 @@
 //                    (10 SU(3) products per site instead of 16).
 //   k_gstep          g = reunitarised (1 + alpha/2 Delta~), G <- reunitarised g G.
 //   k_materialize    G(x) U0_mu(x) G(x+mu)^dag as host-layout FP64 links.
+#include "lgf_gstep.cuh"
 #include "lgf_kernels.cuh"
 #include "lgf_reduce.cuh"
 
@@ -118,34 +119,7 @@ __global__ void __launch_bounds__(256) k_gstep(const cx<T>* __restrict__ D, cx<T
   if (st != nullptr && st->done) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const RT h = (RT)hd;
-  const cx<RT> c0 = cvt<RT>(ldg(D + s));
-  const cx<RT> c1 = cvt<RT>(ldg(D + V + s));
-  const cx<RT> c2 = cvt<RT>(ldg(D + 2 * V + s));
-  const cx<RT> c3 = cvt<RT>(ldg(D + 3 * V + s));
-  M3<RT> g;
-  g.e[0][0] = mk<RT>(1, h * c3.re);
-  g.e[0][1] = scale(c0, h);
-  g.e[0][2] = scale(c1, h);
-  g.e[1][0] = mk<RT>(-h * c0.re, h * c0.im);
-  g.e[1][1] = mk<RT>(1, h * c3.im);
-  g.e[1][2] = scale(c2, h);
-  reunitarize(g);
-  if (g_out != nullptr) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) g_out[c * V + s] = cvt<T>(g.e[c / 3][c % 3]);
-  }
-  if (G == nullptr) return;
-  const M3<T> Gt = load_rw<T, NC>(G, V, s);
-  M3<RT> Gx, r;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Gx.e[i][j] = cvt<RT>(Gt.e[i][j]);
-  mm<RT, 2>(r, g, Gx);
-  reunitarize(r);
-#pragma unroll
-  for (int c = 0; c < NC; ++c) G[c * V + s] = cvt<T>(r.e[c / 3][c % 3]);
+  gstep_site<T, NC, RT>(ldg(D + s), ldg(D + V + s), ldg(D + 2 * V + s), ldg(D + 3 * V + s), (RT)hd, G, g_out, V, s);
 }
 
 // one thread per (site, mu): the current link in the host layout

@@ -355,7 +355,18 @@ int queue_iteration(lgf_handle h, Engine& e) {
     return LGF_OK;
   }
   int rc = queue_gradient(h, e, 1);
-  if (!rc) rc = queue_accelerate(h, e, h->st);
+  if (rc) return rc;
+  if (e.grep && pick_pipeline(h, e) == 3 && plane_xyinv_gstep_supported(e.prec, h->L[0])) {
+    // forward x-y, z-t, then the inverse x-y fused with G <- g G
+    const int* L = h->L;
+    LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 0, h->st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_ZT,
+               launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V, h->st, s));
+    LGF_LAUNCH(h, LGF_K_XY_GSTEP, launch_plane_xyinv_gstep(L[0], e.nc, e.D, h->G, h->V, L[2], L[3], 0.5 * h->alpha,
+                                                           h->reunit_fp64, h->st, s));
+    return LGF_OK;
+  }
+  rc = queue_accelerate(h, e, h->st);
   if (rc) return rc;
   if (e.grep) {
     LGF_LAUNCH(h, LGF_K_BUILD_G,
@@ -1504,8 +1515,8 @@ int lgf_profile_read(lgf_handle h, double* ms, long long* launches, int n) {
 }
 
 const char* lgf_kernel_name(int kind) {
-  static const char* names[LGF_NUM_KERNELS] = {"gradient", "fft_axis", "fft_xy", "fft_zt", "build_g",
-                                               "update",   "accumulate", "other", "fft_t"};
+  static const char* names[LGF_NUM_KERNELS] = {"gradient", "fft_axis",   "fft_xy", "fft_zt", "build_g",
+                                               "update",   "accumulate", "other",  "fft_t",  "xy_gstep"};
   return (kind >= 0 && kind < LGF_NUM_KERNELS) ? names[kind] : "";
 }
 

@@ -108,6 +108,11 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
                             cudaStream_t s);
 cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
                             float c_over_V, const DevState* st, cudaStream_t s);
+// inverse x-y pass fused with G <- g G (FP32 gauge representation; Lx = Ly
+// dividing 32)
+bool plane_xyinv_gstep_supported(int prec, int L);
+cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int64_t V, int Lz, int Lt,
+                                     double half_alpha, bool reunit_fp64, const DevState* st, cudaStream_t s);
 
 // FP32 engine in gauge representation (k_gauge_rep.cu): links formed on the
 // fly as G U0 G^dagger; the update acts on G
