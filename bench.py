@@ -206,7 +206,7 @@ def time_oracle(U, n: int, alpha: float) -> float:
 
 # ---------------------------------------------------------------------------
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-COMMON_SOURCES = ("lgf_common.cuh", "lgf_reduce.cuh", "lgf_kernels.cuh", "fft_reg.cuh")
+COMMON_SOURCES = ("lgf_common.cuh", "lgf_reduce.cuh", "lgf_kernels.cuh", "fft_reg.cuh", "lgf_gstep.cuh")
 
 
 def kernel_source_hash(kernel: str, gauge_rep: bool) -> str | None:
