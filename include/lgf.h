@@ -84,10 +84,13 @@ enum lgf_param {
                             passes; 3 register planes (1 where not available) */
   LGF_TAIL_MODE = 7,     /* mixed precision: 0 (default) finishes with the
                             defect-correction tail when the FP32 phase reached
-                            theta < 1e-8 (FP64 links, gradient and F/theta;
-                            FP32 acceleration and step, g = 1 + eps with eps
-                            the exponential to second order); 1 always uses
-                            the plain FP64 iteration                          */
+                            theta < 1e-8: FP32 acceleration and step, g = 1 +
+                            eps with eps the exponential to second order, the
+                            correction added to links held in double-float
+                            form (FP32 hi + lo, 48 bits; converted back to
+                            FP64 at the end); 2 the same tail on FP64 links;
+                            1 always uses the plain FP64 iteration.  Values
+                            other than 0, 1, 2 give LGF_ERR_ARG.              */
   LGF_LINK_UPDATE = 6    /* FP32 storage, from the next load: 0 (default) keeps
                             the loaded links and applies each update to the
                             accumulated gauge transformation G, forming

@@ -78,8 +78,11 @@ struct lgf_ctx {
   bool reunit_fp64 = false;   // FP32 storage: reunitarise g in FP64 arithmetic
   int fft_pipeline = 0;       // 0 auto, 1 Stockham planes, 2 axis passes, 3 register planes
   bool explicit_fp32 = false; // FP32 engine: update the links in place instead of G (from the next load)
-  int tail_mode = 0;          // 0: defect-correction tail when the FP32 phase reached 1e-8, 1: plain FP64
+  int tail_mode = 0;          // defect-correction tail when the FP32 phase reached 1e-8, with links in
+                              // double-float (0) or FP64 (2); 1: plain FP64
   bool defect = false;        // the FP64 engine runs the defect-correction tail
+  bool df = false;            // ... on the double-float links in Udf (converted back at the end)
+  void* Udf = nullptr;        // tail links in double-float: 36 V complex hi, then 36 V complex lo
 
   Geom geo{};
   Engine e64, e32;
@@ -327,6 +330,39 @@ int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
   return LGF_OK;
 }
 
+// FP64 tail start of a mixed handle after its FP32 phase: the gauge G
+// reunitarised in FP64, then the links rebuilt from the loaded input as
+// G U_loaded G^dagger.  The defect-correction tail (theta < 1e-8 at the
+// hand-over, tail modes 0 and 2) and, in mode 0, its double-float links are
+// chosen here.
+int queue_tail_start(lgf_handle h) {
+  const int64_t V = h->V;
+  LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
+  h->defect = h->tail_mode != 1 && h->st_host->theta < 1e-8;
+  h->df = h->defect && h->tail_mode == 0;
+  if (h->df) {
+    if (!h->Udf) {
+      h->Udf = dev_alloc(h, (size_t)2 * 36 * V * sizeof(float) * 2);
+      if (!h->Udf) return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail links failed");
+    }
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_start_df(h->Uorig, h->e64.g, h->Udf, h->geo, h->stream));
+  } else {
+    LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
+  }
+  h->cur = &h->e64;
+  return LGF_OK;
+}
+
+// After a double-float tail: its links into the FP64 engine, which holds the
+// handle's links from then on (a later lgf_fix continues in FP64).
+int finish_df_tail(lgf_handle h) {
+  if (!h->df) return LGF_OK;
+  LGF_LAUNCH(h, LGF_K_OTHER, launch_df_to_fp64(h->Udf, h->e64.U, h->V, h->stream));
+  h->df = false;
+  return LGF_OK;
+}
+
 // Gradient (+ F/theta reduction) of the engine's current links.
 int queue_gradient(lgf_handle h, Engine& e, int mode) {
   if (e.grep)
@@ -344,6 +380,16 @@ int queue_gradient(lgf_handle h, Engine& e, int mode) {
 // G U_loaded G^dagger up to FP32 rounding.
 int queue_iteration(lgf_handle h, Engine& e) {
   cudaStream_t s = h->stream;
+  if (h->defect && h->df && &e == &h->e64) {
+    // defect-correction tail on double-float links; FP32 acceleration and step
+    Engine& f = h->e32;
+    LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient_tail_df(h->Udf, f.D, h->partial, h->geo, h->st, 1, s));
+    int rc = queue_accelerate(h, f, h->st);
+    if (rc) return rc;
+    LGF_LAUNCH(h, LGF_K_BUILD_G, launch_tail_step(f.D, f.g, h->V, 0.5 * h->alpha, h->st, s));
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_update_df(h->Udf, f.g, h->geo, h->st, s));
+    return LGF_OK;
+  }
   if (h->defect && &e == &h->e64) {
     // defect-correction tail: FP64 links, FP32 acceleration and step
     Engine& f = h->e32;
@@ -1010,7 +1056,8 @@ int lgf_set_param(lgf_handle h, int key, double value) {
       h->explicit_fp32 = value != 0.0;
       return LGF_OK;
     case LGF_TAIL_MODE:
-      h->tail_mode = value != 0.0 ? 1 : 0;
+      if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(h, LGF_ERR_ARG, "tail mode must be 0, 1 or 2");
+      h->tail_mode = (int)value;
       return LGF_OK;
     default:
       return fail(h, LGF_ERR_ARG, "unknown parameter key");
@@ -1025,6 +1072,7 @@ static int load_from_device_aos(lgf_handle h, const double* aos) {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_set_identity(4, h->e32.nc, h->G, V, h->stream));
     h->e32.grep = !h->explicit_fp32;
     h->defect = false;
+    h->df = false;
     h->cur = &h->e32;
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
@@ -1091,7 +1139,6 @@ int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out) {
   int rc;
   if (h->mixed && h->cur == &h->e32) {
     // FP32 phase; G has been accumulated since the load
-    const int64_t V = h->V;
     const double tol32 = theta_tol > h->tail_theta ? theta_tol : h->tail_theta;
     int cap32 = max_iter;
     if (h->tail_max32 >= 0 && h->tail_max32 < cap32) cap32 = (int)h->tail_max32;
@@ -1103,15 +1150,13 @@ int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out) {
       if (iters_out) *iters_out = n1;
       return LGF_OK;
     }
-    // FP64 tail from the loaded links and the reunitarised accumulated G
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
-    LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
-    LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
-    h->cur = &h->e64;
-    h->defect = (h->tail_mode == 0) && h->st_host->theta < 1e-8;
+    rc = queue_tail_start(h);
+    if (rc) return rc;
   }
   const int left = max_iter - n1;
   rc = run_fix(h, *h->cur, theta_tol, left, false, &n2, &conv);
+  if (rc) return rc;
+  rc = finish_df_tail(h);
   if (rc) return rc;
   h->total_updates += n2;
   if (h->cur == &h->e64)
@@ -1285,19 +1330,11 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
       h->last_n32 = n1[i];
       if (h->st_host->theta < theta_tol) continue;
       // FP64 tail from the loaded links and the reunitarised accumulated G
-      const int64_t V = h->V;
       cudaStream_t saved = h->stream;
       h->stream = b->main;
-      rc = LGF_OK;
-      do {
-        LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
-        LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice,
-                                    h->stream));
-        LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
-      } while (0);
+      rc = queue_tail_start(h);
       h->stream = saved;
-      h->cur = &h->e64;
-      h->defect = (h->tail_mode == 0) && h->st_host->theta < 1e-8;
+      if (rc) return bfail(b, rc, h->err);
       tail.push_back(i);
     } else {
       h->last_n64 = n1[i];
@@ -1311,6 +1348,15 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
   std::vector<char> stall2(tail.size(), 0);
   rc = run_members(b, tail, tol2, cap2, stall2);
   if (rc) return rc;
+  for (int i : tail) {  // double-float tails back to FP64 links
+    lgf_handle h = b->h[i];
+    cudaStream_t saved = h->stream;
+    h->stream = b->main;
+    rc = finish_df_tail(h);
+    h->stream = saved;
+    if (rc) return bfail(b, rc, h->err);
+  }
+  LGF_BCUDA(b, cudaStreamSynchronize(b->main));
   for (int i : tail) {
     n2[i] = b->h[i]->st_host->iters;
     b->h[i]->last_n64 = n2[i];

@@ -122,6 +122,13 @@ cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V,
                          const DevState* st, cudaStream_t s);
 cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s);
 
+// FP64 tail by defect correction with double-float links (k_tail.cu): Udf
+// holds 36 V complex hi parts followed by 36 V complex lo parts
+cudaError_t launch_tail_start_df(const void* Uin64, const void* g64, void* Udf, const Geom& geo, cudaStream_t s);
+cudaError_t launch_gradient_tail_df(const void* Udf, void* D32, double2* partial, const Geom& geo, DevState* st,
+                                    int mode, cudaStream_t s);
+cudaError_t launch_tail_update_df(void* Udf, const void* eps, const Geom& geo, const DevState* st, cudaStream_t s);
+cudaError_t launch_df_to_fp64(const void* Udf, void* U64, int64_t V, cudaStream_t s);
 // FP64 tail by defect correction (k_tail.cu): FP64 links, FP32 FFT and step
 cudaError_t launch_gradient_tail(const void* U64, void* D32, double2* partial, const Geom& geo, DevState* st,
                                  int mode, cudaStream_t s);

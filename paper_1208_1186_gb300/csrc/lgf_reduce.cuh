@@ -14,19 +14,14 @@
 
 namespace lgf {
 
-// Sum (a, b) over the block; the result is valid in thread 0.
-template <class T>
-__device__ __forceinline__ void block_sum_mixed(T a, T b, double& ra, double& rb) {
+// Sum per-warp totals over the block in FP64, in warp order; the totals are
+// read from lane 0 of each warp and the result is valid in thread 0.
+__device__ __forceinline__ void block_sum_warp_totals(double wa, double wb, double& ra, double& rb) {
   __shared__ double sa[32], sb[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) {
-    sa[w] = (double)a;
-    sb[w] = (double)b;
+    sa[w] = wa;
+    sb[w] = wb;
   }
   __syncthreads();
   const int nw = (blockDim.x + 31) >> 5;
@@ -42,6 +37,17 @@ __device__ __forceinline__ void block_sum_mixed(T a, T b, double& ra, double& rb
   }
   ra = x;
   rb = y;
+}
+
+// Sum (a, b) over the block; the result is valid in thread 0.
+template <class T>
+__device__ __forceinline__ void block_sum_mixed(T a, T b, double& ra, double& rb) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  block_sum_warp_totals((double)a, (double)b, ra, rb);
 }
 
 // F, theta and the stop decision from the grid sums (one thread).
@@ -61,14 +67,11 @@ __device__ __forceinline__ void finish_reduction(DevState* st, double fs, double
   }
 }
 
-// Block partials -> grid result: every block stores its pair; the last block
-// to arrive adds all pairs in index order and finishes the reduction.
-// Must be called by every thread of every block.
-template <class T>
-__device__ __forceinline__ void grid_reduce(T fs, T ts, double2* __restrict__ partial, DevState* st, double normF,
-                                            double normT, int mode) {
-  double a, b;
-  block_sum_mixed<T>(fs, ts, a, b);
+// Block sums (valid in thread 0) -> grid result: every block stores its pair;
+// the last block to arrive adds all pairs in index order and finishes the
+// reduction.  Must be called by every thread of every block.
+__device__ __forceinline__ void grid_reduce_block_sums(double a, double b, double2* __restrict__ partial,
+                                                       DevState* st, double normF, double normT, int mode) {
   __shared__ int is_last;
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = make_double2(a, b);
@@ -85,12 +88,29 @@ __device__ __forceinline__ void grid_reduce(T fs, T ts, double2* __restrict__ pa
     x += p.x;
     y += p.y;
   }
-  __syncthreads();  // the shared scratch of block_sum_mixed is reused
+  __syncthreads();  // the shared scratch of the block sum is reused
   block_sum_mixed<double>(x, y, a, b);
   if (threadIdx.x == 0) {
     st->arrive = 0;
     finish_reduction(st, a, b, normF, normT, mode);
   }
+}
+
+// Per-thread terms -> grid result (warp sums in T, FP64 above the warp).
+template <class T>
+__device__ __forceinline__ void grid_reduce(T fs, T ts, double2* __restrict__ partial, DevState* st, double normF,
+                                            double normT, int mode) {
+  double a, b;
+  block_sum_mixed<T>(fs, ts, a, b);
+  grid_reduce_block_sums(a, b, partial, st, normF, normT, mode);
+}
+
+// Per-warp totals (valid in lane 0) -> grid result.
+__device__ __forceinline__ void grid_reduce_warp_totals(double wf, double wt, double2* __restrict__ partial,
+                                                        DevState* st, double normF, double normT, int mode) {
+  double a, b;
+  block_sum_warp_totals(wf, wt, a, b);
+  grid_reduce_block_sums(a, b, partial, st, normF, normT, mode);
 }
 
 }  // namespace lgf

@@ -286,18 +286,23 @@ def test_full_size_32_4_fp32_tail(lgf):
 
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (12, 12, 32, 8)])
 def test_both_fp64_tails_reach_the_oracle_functional(lgf, dims):
-    """LGF_TAIL_MODE 0 (defect-correction tail: FP64 links and sums, FP32
-    acceleration and step) and 1 (plain FP64 iteration) end at the oracle's
-    FP64 functional to 1e-12 relative, with theta < 1e-15."""
+    """LGF_TAIL_MODE 0 (defect-correction tail on double-float links), 2 (the
+    same tail on FP64 links) and 1 (plain FP64 iteration) all end at the
+    oracle's FP64 functional to 1e-12 relative, with theta < 1e-15."""
     U, ref = _oracle_fix(dims, 2, 0.5, 1e-15)
     res = {}
-    for mode in (0, 1):
+    for mode in (0, 2, 1):
         with lgf.GaugeFixer(dims, "f32") as gf:
             gf.set_param(7, mode)  # LGF_TAIL_MODE
             gf.load_links(U)
             iters, conv = gf.fix(1e-15, 2000)
             F, th = gf.functional()
-            res[mode] = (iters, gf.fix_split(), F)
+            res[mode] = (iters, gf.fix_split(), F, gf.store_links())
         assert conv and th < 1e-15
         assert F == pytest.approx(ref["F"], rel=1e-12)
-    assert res[0][1][0] == res[1][1][0]  # the same FP32 phase
+    assert res[0][1][0] == res[1][1][0] == res[2][1][0]  # the same FP32 phase
+    if res[0][1] == res[2][1]:
+        # the double-float and FP64 forms of the defect tail take the same
+        # steps: their FP32 corrections differ by at most an FP32 rounding of
+        # a correction (|eps| 2^-24 < 1e-11), their link storage by 2^-47
+        assert np.max(np.abs(res[0][3] - res[2][3])) < 1e-10
