@@ -28,7 +28,7 @@ namespace lgf {
 
 namespace {
 
-// x-y planes with L dividing 32 take the warp-tile kernel
+// x-y planes with L <= 32 take the warp-tile kernel
 constexpr bool kXyWarpTiles = true;
 // FP32 gauge representation: the inverse x-y pass is fused with the G update,
 // which loads G for kXyGstepSites sites at a time
@@ -109,14 +109,16 @@ __global__ void __launch_bounds__(xy_threads<LX, LY>(), xy_min_blocks<T, LX>()) 
   }
 }
 
-// x-y planes with L dividing 32: a group of L lanes owns one (plane, field)
+// x-y planes with L <= 32: a group of L lanes owns one (plane, field)
 // tile from its load to its store, so a warp needs no CTA barrier and warps
 // overlap their loads with one another's transforms.  Lane r loads y-line r
 // straight into registers (for each y the group reads one contiguous row),
 // transforms it, and one pass through shared memory hands it x-line r; a
 // second pass turns the rows back into coalesced stores.  (The two 1D
 // transforms commute, so y before x gives the same 2D transform.)  Four
-// shared-memory accesses per element; one warp per CTA, 32 / L tiles per warp.
+// shared-memory accesses per element; one warp per CTA, floor(32 / L) tiles
+// per warp (L <= 32; lanes past the last whole group idle through the
+// transforms).
 template <class T, int L>
 constexpr int xyw_smem_bytes() {
   return (32 / L) * L * (L + 1) * (int)sizeof(cx<T>);
@@ -125,16 +127,17 @@ constexpr int xyw_smem_bytes() {
 template <class T, int L, bool INV>
 __global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int V, int ntiles,
                                                       const DevState* __restrict__ st) {
-  static_assert(32 % L == 0, "a warp holds whole tiles");
+  static_assert(L <= 32, "a warp holds at least one tile");
   pdl_wait();
   if (st != nullptr && st->done) return;
   constexpr int G = 32 / L, P = L + 1, N = L * L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / L, r = threadIdx.x % L;
   const int tile_id = blockIdx.x * G + g;  // = 4 plane + field
-  // a group past the last tile idles but still takes part in every __syncwarp
-  const bool active = tile_id < ntiles;
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw) + g * L * P;
+  // a group past the last tile, or past the last whole group of the warp,
+  // idles but still takes part in every __syncwarp
+  const bool active = g < G && tile_id < ntiles;
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw) + (active ? g : 0) * L * P;
   cx<T>* src = D + (active ? (tile_id & 3) * V + (tile_id >> 2) * N : 0);
   if (active) {  // y-line r from global, transformed, into column r
     cx<T> v[L];
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int
 }
 
 // Inverse x-y transform fused with the gauge step on G (FP32 gauge
-// representation).  One CTA of four warps per 32 / L planes: warp f inverse-
+// representation).  One CTA of four warps per floor(32 / L) planes (L <= 32): warp f inverse-
 // transforms field f of the CTA's planes exactly as k_plane_xy_warp does and
 // leaves Delta~ in shared memory (it is never written back: nothing reads it
 // after the update); after one CTA barrier the 128 threads apply the gauge
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int
 template <int L, int NC, class RT, int KS>
 __global__ void __launch_bounds__(128) k_plane_xyinv_gstep(const cx<float>* __restrict__ D, cx<float>* G, int V,
                                                            int nplanes, double hd, const DevState* __restrict__ st) {
-  static_assert(32 % L == 0, "a warp holds whole tiles");
+  static_assert(L <= 32, "a warp holds at least one tile");
   pdl_wait();
   if (st != nullptr && st->done) return;
   constexpr int GP = 32 / L, P = L + 1, N = L * L, TS = L * P;  // planes per CTA, pitch, plane, tile
@@ -185,8 +188,8 @@ __global__ void __launch_bounds__(128) k_plane_xyinv_gstep(const cx<float>* __re
   const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / L, r = lane % L;
   const int plane0 = blockIdx.x * GP;
-  const bool active = plane0 + g < nplanes;
-  cx<float>* tile = tiles + (f * GP + g) * TS;
+  const bool active = g < GP && plane0 + g < nplanes;
+  cx<float>* tile = tiles + (f * GP + (active ? g : 0)) * TS;
   if (active) {  // inverse y-line r from global memory into column r
     const cx<float>* src = D + ((int64_t)f * V + (int64_t)(plane0 + g) * N);
     cx<float> v[L];
@@ -375,7 +378,7 @@ namespace {
 
 template <class T, int L>
 cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s, int Lz, int Lt) {
-  if constexpr (32 % L == 0 && kXyWarpTiles) {
+  if constexpr (L <= 32 && kXyWarpTiles) {
     const int ntiles = 4 * Lz * Lt;
     const unsigned nb = (unsigned)((ntiles + 32 / L - 1) / (32 / L));
     constexpr int sm = xyw_smem_bytes<T, L>();
@@ -414,7 +417,7 @@ cudaError_t xyinv_gstep_launch(int nc, bool r64, const cx<float>* D, cx<float>* 
 
 template <class T, int L>
 cudaError_t xy_attr() {
-  if constexpr (32 % L == 0) {
+  if constexpr (L <= 32) {
     cudaError_t e = cudaFuncSetAttribute(k_plane_xy_warp<T, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          xyw_smem_bytes<T, L>());
     if (e == cudaSuccess)
@@ -494,7 +497,13 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
 }
 
 bool plane_xyinv_gstep_supported(int prec, int L) {
-  return kFuseXyinvGstep && prec == 4 && (L == 4 || L == 8 || L == 16 || L == 32);
+  if (!kFuseXyinvGstep || prec != 4) return false;
+  switch (L) {
+    case 4: case 6: case 8: case 12: case 16: case 20: case 24: case 32:
+      return true;
+    default:
+      return false;
+  }
 }
 
 cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int64_t V, int Lz, int Lt,
@@ -504,8 +513,12 @@ cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int6
   const auto Gp = static_cast<cx<float>*>(G);
   switch (L) {
     case 4: return xyinv_gstep_launch<4>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 6: return xyinv_gstep_launch<6>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     case 8: return xyinv_gstep_launch<8>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 12: return xyinv_gstep_launch<12>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     case 16: return xyinv_gstep_launch<16>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 20: return xyinv_gstep_launch<20>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 24: return xyinv_gstep_launch<24>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     case 32: return xyinv_gstep_launch<32>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     default: return cudaErrorInvalidValue;
   }

@@ -109,7 +109,7 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
 cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
                             float c_over_V, const DevState* st, cudaStream_t s);
 // inverse x-y pass fused with G <- g G (FP32 gauge representation; Lx = Ly
-// dividing 32)
+// one of 4, 6, 8, 12, 16, 20, 24, 32)
 bool plane_xyinv_gstep_supported(int prec, int L);
 cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int64_t V, int Lz, int Lt,
                                      double half_alpha, bool reunit_fp64, const DevState* st, cudaStream_t s);

@@ -30,6 +30,9 @@ STEP_DIMS = [
     (32, 32, 8, 8),    # warp-tile x-y planes, one 32 x 32 tile per warp
     (16, 16, 32, 16),  # warp-tile x-y planes, two 16 x 16 tiles per warp
     (4, 4, 6, 6),      # warp-tile x-y planes, eight 4 x 4 tiles per warp
+    (20, 20, 4, 4),    # warp-tile x-y planes, one 20 x 20 tile per warp, 12 lanes idle
+    (24, 24, 6, 6),    # warp-tile x-y planes, one 24 x 24 tile per warp, 8 lanes idle
+    (6, 6, 6, 6),      # warp-tile x-y planes, five 6 x 6 tiles per warp, 2 lanes idle
     (6, 12, 4, 20),    # axis passes, radices 2, 3, 4, 5; V = 5760
     (20, 8, 24, 6),    # axis passes, V = 23040
     (4, 6, 10, 12),    # plane kernels (10); V = 2880, ragged last block
