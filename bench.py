@@ -475,6 +475,11 @@ def run_batch(args, W):
     Vtot = sum(int(np.prod(s)) for s in shapes)
     smi = ClockSampler(gpu_id_for_smi(torch))
     batch = lgf.GaugeBatch(fixers)
+    lanes = args.lanes
+    if lanes >= 0:
+        batch.set_lanes(lanes)
+    else:
+        lanes = batch.autotune(reps=4)
     try:
         batch.iterate(args.warmup)
         torch.cuda.synchronize()
@@ -501,9 +506,10 @@ def run_batch(args, W):
         f.close()
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
-    # gauge representation, FP32 18-real: gradient 368, FFT 3 passes x 64, G step 176 bytes/site
-    step_bytes = (bytes_per_site("gradient", 4, 18, True) + 3 * bytes_per_site("fft_xy", 4, 18)
-                  + bytes_per_site("build_g", 4, 18, True))
+    # gauge representation, FP32 18-real, every batch shape on the fused path:
+    # gradient 392, forward x-y 64, z-t 64, inverse x-y + G update 176 bytes/site
+    step_bytes = (bytes_per_site("gradient", 4, 18, True) + 2 * bytes_per_site("fft_xy", 4, 18)
+                  + bytes_per_site("xy_gstep", 4, 18, True))
     value = Vtot * args.steps / secs
     return {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": 1, "steps": args.steps,
@@ -511,7 +517,7 @@ def run_batch(args, W):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
         "config": {"workload": W["desc"], "members": n, "sites": Vtot, "storage": W["dtype"],
-                   "fft_pipeline_per_shape": tuned,
+                   "fft_pipeline_per_shape": tuned, "graph_lanes": lanes if args.lanes >= 0 else f"{lanes} (autotuned; 0 = one per member)",
                    "timing": "host wall clock around the synchronous lgf_batch_iterate (graph launches + checks)"},
         "roofline": {"bound": "hbm", "kernel": "whole step (graph-launched; per-kernel events are not recorded "
                                                 "inside graphs)",
@@ -665,6 +671,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--train-n", type=int, default=0, help="warm-start workload: training configurations")
     ap.add_argument("--tail-theta", type=float, default=0.0, help="theta at which the FP32 phase hands over")
+    ap.add_argument("--lanes", type=int, default=-1, help="batch workload: parallel graph lanes (0: one per member)")
     ap.add_argument("--link-update", type=int, default=0, choices=[0, 1],
                     help="FP32 storage: 0 gauge representation (default), 1 links updated in place")
     args = ap.parse_args()

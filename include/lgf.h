@@ -228,6 +228,19 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
 /* Text of the last error of a batch call. */
 const char* lgf_batch_last_error(lgf_batch b);
 
+/* Parallel branches of the batch's graphs: 0 (the default) gives every member
+ * its own branch; n > 0 spreads the members over n lanes (largest first, each
+ * onto the lane with the fewest sites so far), a lane running its members'
+ * iteration blocks one after another.  Fewer lanes keep fewer packed
+ * gradients competing for L2.  Not part of the paper's method. */
+int lgf_batch_set_lanes(lgf_batch b, int lanes);
+
+/* Lane autotuner: times one graph launch of reps iterations of every member
+ * for 1, 2, 4, 8, 16 lanes and one lane per member, keeps the fastest and
+ * stores it in *lanes_out (may be NULL).  The timed iterations are applied to
+ * the members' links (like warm-up iterations) and counted as updates. */
+int lgf_batch_autotune(lgf_batch b, int reps, int* lanes_out);
+
 /* Autotuner: time every FFT pipeline that applies to this lattice (x-y/z-t
  * register planes, per-axis register passes, shared-memory Stockham planes)
  * on each of the handle's engines, reps accelerations each, and use the

@@ -171,6 +171,17 @@ class GaugeBatch:
         if st != _lib.LGF_OK:
             raise LgfError(st, where, self.lib.lgf_batch_last_error(self.b).decode())
 
+    def set_lanes(self, lanes: int):
+        """Parallel graph branches: 0 one per member, n > 0 n lanes."""
+        self._check(self.lib.lgf_batch_set_lanes(self.b, int(lanes)), "lgf_batch_set_lanes")
+
+    def autotune(self, reps: int = 4) -> int:
+        """Time the lane counts on reps iterations (applied to the links) and
+        keep the fastest; returns it (0: one lane per member)."""
+        out = ctypes.c_int(0)
+        self._check(self.lib.lgf_batch_autotune(self.b, int(reps), ctypes.byref(out)), "lgf_batch_autotune")
+        return out.value
+
     def iterate(self, n: int):
         self._check(self.lib.lgf_batch_iterate(self.b, int(n)), "lgf_batch_iterate")
 

@@ -59,6 +59,8 @@ SIGNATURES = {
     "lgf_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int]),
     "lgf_batch_fix": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P, _P]),
     "lgf_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lgf_batch_set_lanes": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lgf_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lgf_autotune": (ctypes.c_int, [_P, ctypes.c_int, _IP]),
     "lgf_net_param_count": (ctypes.c_int, []),
     "lgf_net_create": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(_P)]),

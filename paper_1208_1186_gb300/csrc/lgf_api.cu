@@ -568,6 +568,7 @@ struct lgf_batch_ctx {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   int exec_k = 0;                     // iterations per member per graph launch
+  int lanes = 0;                      // parallel graph branches (0: one per member)
   std::vector<int> exec_members;      // members captured in exec
   std::vector<long long> exec_launches;  // kernels per member per graph launch
   std::string err;
@@ -601,23 +602,40 @@ int capture(lgf_batch b, const std::vector<int>& members, int k) {
   int rc = LGF_OK;
   cudaEventRecord(b->fork, b->main);
   b->exec_launches.assign(members.size(), 0);
-  for (size_t m = 0; m < members.size() && !rc; ++m) {
-    const int i = members[m];
-    lgf_handle h = b->h[i];
-    cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-    cudaStream_t saved = h->stream;
-    const bool prof = h->profiling;
-    h->stream = b->streams[i];
-    h->profiling = false;
-    const long long l0 = h->launches;
-    for (int j = 0; j < k && !rc; ++j) rc = queue_iteration(h, *h->cur);
-    b->exec_launches[m] = h->launches - l0;
-    h->launches = l0;
-    h->stream = saved;
-    h->profiling = prof;
-    if (rc) b->err = h->err;
-    cudaEventRecord(b->joins[i], b->streams[i]);
-    cudaStreamWaitEvent(b->main, b->joins[i], 0);
+  // lanes: members, largest first, each onto the lane with the fewest sites;
+  // a lane runs its members' iteration blocks one after another
+  const int nl = (b->lanes <= 0 || b->lanes > (int)members.size()) ? (int)members.size() : b->lanes;
+  std::vector<size_t> order(members.size());
+  for (size_t m = 0; m < order.size(); ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t c) { return b->h[members[a]]->V > b->h[members[c]]->V; });
+  std::vector<int64_t> load(nl, 0);
+  std::vector<std::vector<size_t>> lane(nl);
+  for (size_t m : order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lane[j].push_back(m);
+    load[j] += b->h[members[m]]->V;
+  }
+  for (int j = 0; j < nl && !rc; ++j) {
+    cudaStream_t ls = b->streams[j];
+    cudaStreamWaitEvent(ls, b->fork, 0);
+    for (size_t m : lane[j]) {
+      if (rc) break;
+      lgf_handle h = b->h[members[m]];
+      cudaStream_t saved = h->stream;
+      const bool prof = h->profiling;
+      h->stream = ls;
+      h->profiling = false;
+      const long long l0 = h->launches;
+      for (int it = 0; it < k && !rc; ++it) rc = queue_iteration(h, *h->cur);
+      b->exec_launches[m] = h->launches - l0;
+      h->launches = l0;
+      h->stream = saved;
+      h->profiling = prof;
+      if (rc) b->err = h->err;
+    }
+    cudaEventRecord(b->joins[j], ls);
+    cudaStreamWaitEvent(b->main, b->joins[j], 0);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->main, &g);
@@ -1373,6 +1391,72 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
 }
 
 const char* lgf_batch_last_error(lgf_batch b) { return b ? b->err.c_str() : ""; }
+
+int lgf_batch_autotune(lgf_batch b, int reps, int* lanes_out) {
+  if (!b || reps < 1) return LGF_ERR_ARG;
+  const int n = (int)b->h.size();
+  std::vector<int> all;
+  for (int i = 0; i < n; ++i) {
+    if (!b->h[i]->loaded) return bfail(b, LGF_ERR_ARG, "member " + std::to_string(i) + " has no links loaded");
+    cudaStreamSynchronize(b->h[i]->stream);
+    all.push_back(i);
+  }
+  std::vector<double> tol(n, -1.0);
+  std::vector<int> cap(n, 1 << 30);
+  int rc = reset_members(b, all, tol, cap);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return bfail(b, LGF_ERR_CUDA, "event creation failed");
+  }
+  const int cands[] = {1, 2, 4, 8, 16, 0};
+  int best = 0;
+  float best_ms = INFINITY;
+  const int saved = b->lanes;
+  for (int c : cands) {
+    if (c > n) continue;
+    b->lanes = c;
+    rc = capture(b, all, reps);
+    if (!rc) rc = launch_graph(b);  // warm-up
+    if (rc) break;
+    cudaEventRecord(e0, b->main);
+    rc = launch_graph(b);
+    if (rc) break;
+    cudaEventRecord(e1, b->main);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = bfail(b, LGF_ERR_CUDA, "graph launch failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graph(b);
+  if (rc) {
+    b->lanes = saved;
+    return rc;
+  }
+  b->lanes = best;
+  // the tuning iterations were applied: count them like any others
+  rc = read_members(b, all);
+  if (rc) return rc;
+  for (int i : all) b->h[i]->total_updates += b->h[i]->st_host->iters;
+  if (lanes_out) *lanes_out = best;
+  return LGF_OK;
+}
+
+int lgf_batch_set_lanes(lgf_batch b, int lanes) {
+  if (!b || lanes < 0) return LGF_ERR_ARG;
+  if (lanes != b->lanes) drop_graph(b);
+  b->lanes = lanes;
+  return LGF_OK;
+}
 
 int lgf_net_param_count(void) { return warm::kParams; }
 

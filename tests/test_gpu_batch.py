@@ -31,7 +31,10 @@ def _inputs():
     return [I.synthetic_config(d, seed=s, link_scale=0.5) for d, _, s in MEMBERS]
 
 
-def test_batch_fix_reproduces_individual_fixes(lgf):
+@pytest.mark.parametrize("lanes", [None, 1, 2])
+def test_batch_fix_reproduces_individual_fixes(lgf, lanes):
+    """Lanes change only how members' kernel chains share the GPU, never a
+    member's own arithmetic."""
     Us = _inputs()
     singles = []
     for (d, dt, _), U in zip(MEMBERS, Us):
@@ -44,6 +47,8 @@ def test_batch_fix_reproduces_individual_fixes(lgf):
         for f, U in zip(fixers, Us):
             f.load_links(U)
         with lgf.GaugeBatch(fixers) as b:
+            if lanes is not None:
+                b.set_lanes(lanes)
             its, convs = b.fix(1e-15, 2000)
         for k, f in enumerate(fixers):
             it, conv, split, links, (F, th) = singles[k]
@@ -98,3 +103,30 @@ def test_autotune_picks_an_available_pipeline(lgf, dims, dtype):
         F, th = gf.functional()
     assert conv and th < 1e-14
     assert F == pytest.approx(ref["F"], rel=1e-12)
+
+
+def test_batch_lane_autotuner_keeps_results(lgf):
+    """The lane autotuner returns one of its candidates; a fix after it (from
+    freshly loaded links) still reproduces the individual fixes."""
+    Us = _inputs()
+    singles = []
+    for (d, dt, _), U in zip(MEMBERS, Us):
+        with lgf.GaugeFixer(d, dt) as gf:
+            gf.load_links(U)
+            gf.fix(1e-15, 2000)
+            singles.append(gf.store_links())
+    fixers = [lgf.GaugeFixer(d, dt) for d, dt, _ in MEMBERS]
+    try:
+        for f, U in zip(fixers, Us):
+            f.load_links(U)
+        with lgf.GaugeBatch(fixers) as b:
+            lanes = b.autotune(reps=2)
+            assert lanes in (0, 1, 2, 4)  # candidates up to the member count (5)
+            for f, U in zip(fixers, Us):
+                f.load_links(U)
+            b.fix(1e-15, 2000)
+        for k, f in enumerate(fixers):
+            assert np.array_equal(f.store_links(), singles[k]), MEMBERS[k]
+    finally:
+        for f in fixers:
+            f.close()
