@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
                                                                 double2* __restrict__ partial, const Geom geo,
                                                                 DevState* st, int mode, double normF, double normT) {
   pdl_wait();
-  if (mode == 1 && st->done) return;
+  if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;  // 36 V < 2^31 for extents <= 64
   double fs = 0.0, ts = 0.0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restri
                                                            double2* __restrict__ partial, const Geom geo,
                                                            DevState* st, int mode, double normF, double normT) {
   pdl_wait();
-  if (mode == 1 && st->done) return;
+  if (queue_stopped(st, mode)) return;
   const int64_t V = geo.V;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   T fsum = 0, tsum = 0;

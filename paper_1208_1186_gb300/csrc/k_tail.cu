@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_gradient_tail(const cx<double>* __restr
                                                        double2* __restrict__ partial, const Geom geo, DevState* st,
                                                        int mode, double normF, double normT) {
   pdl_wait();
-  if (mode == 1 && st->done) return;
+  if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double fsum = 0.0, tsum = 0.0;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256) k_gradient_tail_df(const cx<float>* __res
                                                           double2* __restrict__ partial, const Geom geo, DevState* st,
                                                           int mode, double normF, double normT) {
   pdl_wait();
-  if (mode == 1 && st->done) return;
+  if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   df fsum = {0.f, 0.f};

@@ -281,6 +281,11 @@ struct DevState {
   int hist_cap;
   unsigned int arrive;  // blocks of the current gradient launch that are done
   double* hist;      // theta before update n, n < hist_cap
+  int stall;         // also stop once theta < 1e-6 has not halved within 8 updates
+  int stall_iters;   // update count at the reference theta
+  double stall_ref;  // reference theta of the stall rule (0: none yet)
+  int use_cond;      // the queue is a device-side graph loop: set its condition
+  unsigned long long cond;  // the loop's cudaGraphConditionalHandle
 };
 
 }  // namespace lgf

@@ -60,11 +60,31 @@ __device__ __forceinline__ void finish_reduction(DevState* st, double fs, double
   if (bad) st->nonfinite = 1;
   if (mode != 1) return;
   if (st->hist != nullptr && st->iters < st->hist_cap) st->hist[st->iters] = th;
-  if (bad || (st->tol >= 0.0 && th < st->tol) || st->iters >= st->max_iter) {
+  bool stop = bad || (st->tol >= 0.0 && th < st->tol) || st->iters >= st->max_iter;
+  if (!stop && st->stall && th < 1e-6) {
+    // the FP32 phase hands over once theta has not halved within 8 updates
+    if (st->stall_ref > 0.0 && th > 0.5 * st->stall_ref && st->iters - st->stall_iters >= 8) {
+      stop = true;
+    } else if (st->stall_ref == 0.0 || th <= 0.5 * st->stall_ref) {
+      st->stall_ref = th;
+      st->stall_iters = st->iters;
+    }
+  }
+  if (stop) {
     st->done = 1;
   } else {
     st->iters += 1;
   }
+  if (st->use_cond) cudaGraphSetConditional(st->cond, stop ? 0u : 1u);
+}
+
+// Gradient kernels of an iteration queue: true if the queue has stopped, so
+// the launch does nothing; in a device-side graph loop the first thread of
+// the grid also ends the loop (one caller of cudaGraphSetConditional).
+__device__ __forceinline__ bool queue_stopped(const DevState* st, int mode) {
+  if (mode != 1 || !st->done) return false;
+  if (st->use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(st->cond, 0u);
+  return true;
 }
 
 // Block sums (valid in thread 0) -> grid result: every block stores its pair;
