@@ -521,7 +521,7 @@ def run_batch(args, W):
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
         "config": {"workload": W["desc"], "members": n, "sites": Vtot, "storage": W["dtype"],
                    "fft_pipeline_per_shape": tuned, "graph_lanes": lanes if args.lanes >= 0 else f"{lanes} (autotuned; 0 = one per member)",
-                   "timing": "host wall clock around the synchronous lgf_batch_iterate (graph launches + checks)"},
+                   "timing": "host wall clock around the synchronous lgf_batch_iterate: one graph launch, every member looping on the device"},
         "roofline": {"bound": "hbm", "kernel": "whole step (graph-launched; per-kernel events are not recorded "
                                                 "inside graphs)",
                      "achieved": round(step_bytes * value / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",

@@ -69,7 +69,9 @@ enum lgf_status {
 
 enum lgf_param {
   LGF_ALPHA = 0,        /* step size alpha (default 0.08)                       */
-  LGF_CHECK_EVERY = 1,  /* lgf_fix: iterations queued between host checks (32)  */
+  LGF_CHECK_EVERY = 1,  /* lgf_fix under lgf_profile: at most this many iterations
+                           queued between host checks (32).  Without profiling
+                           each phase is one device-side graph loop.          */
   LGF_TAIL_THETA = 2,   /* mixed precision: theta at which the FP32 phase hands
                            over to the FP64 tail (default 1e-12, just above
                            where FP32 rounding stalls the FP32 phase)          */
@@ -144,9 +146,13 @@ int lgf_iterate(lgf_handle h, int n);
 /* Iterate until theta < theta_tol or max_iter updates have been applied.
  * *iters_out (may be NULL) receives the number of updates.  Returns LGF_OK,
  * LGF_ERR_NOT_CONVERGED or an error.  Mixed-precision handles run the FP32
- * phase down to LGF_TAIL_THETA, then rebuild the links in FP64 from the
- * loaded input and the accumulated gauge transformation and finish in FP64;
- * the links are FP64 from then on until the next load. */
+ * phase down to LGF_TAIL_THETA (or until theta below 1e-6 stops halving
+ * within 8 updates), then rebuild the links in FP64 from the loaded input and
+ * the accumulated gauge transformation and finish in FP64; the links are
+ * FP64 from then on until the next load.  Each phase runs as one CUDA graph
+ * launch with the loop on the device (the first call builds the graphs; the
+ * host waits once per phase); under lgf_profile the host queues the
+ * iterations instead.  Both stop at the same update. */
 int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out);
 
 /* F and theta of the current links (either pointer may be NULL). */
@@ -203,12 +209,13 @@ const char* lgf_kernel_name(int kind);
 
 /* ------------------------------------------------------------------------
  * Batches: several lattices (any sizes and storage types, one device) fixed
- * together.  Each host check launches one CUDA graph holding LGF_CHECK_EVERY
- * iterations of every member as independent branches, so small lattices
- * that cannot fill the GPU alone run concurrently; each member keeps its own
- * on-device stop decision, so converged members cost only empty launches.
- * Mixed-precision members run their FP32 phases together, then their FP64
- * tails together.  The batch borrows the handles (they must outlive it and
+ * together.  Each phase is one launch of one CUDA graph holding, for every
+ * member, a conditional while node around one of its iterations; each member
+ * loops on the device until its own stop decision, so converged members cost
+ * nothing further.  The members' loops run in parallel lanes (see
+ * lgf_batch_set_lanes), so lattices too small to fill the GPU alone run
+ * concurrently.  Mixed-precision members run their FP32 phases together, then
+ * their FP64 tails together.  The batch borrows the handles (they must outlive it and
  * must not be used concurrently with it) and runs on its own streams.
  * ------------------------------------------------------------------------ */
 typedef struct lgf_batch_ctx* lgf_batch;
