@@ -56,7 +56,7 @@ WORKLOADS["batch64-f32"] = dict(
          "FP32 + FP64 tail to theta<1e-15, link scale 0.5, FFT pipeline autotuned per shape")
 WORKLOADS["warmstart-f32"] = dict(
     warm=True, dtype="f32", link_scale=0.5, gauge_scale=1.0, alpha=0.08, tol=1e-15, max_iter=5000,
-    train_dims=(16, 16, 16, 16), train_n=512, train_seed=1000, epochs=1, lr=1e-5,
+    train_dims=(16, 16, 16, 16), train_n=2000, train_seed=1000, epochs=1, lr=1e-5,
     eval_dims=(24, 24, 24, 24), eval_n=8, eval_seed=5000,
     desc="learned warm start: 4D conv net (3 layers, 32 channels, 3^4 taps, BF16 weights, FP32 accumulation) "
          "trained on 16^4 configs (maximising F of the warm-started links), evaluated on 24^4 configs: "
@@ -568,6 +568,11 @@ def run_warm(args, W):
     gf.close()
     # evaluation on unseen configurations of another size
     ge = lgf.GaugeFixer(W["eval_dims"], W["dtype"], alpha=W["alpha"])
+    # one untimed fix first: it builds the handle's loop graphs, which both
+    # timed arms then share
+    ge.load_links(torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] - 1, link_scale=W["link_scale"],
+                                             gauge_scale=W["gauge_scale"], device="cuda"))
+    ge.fix(W["tol"], W["max_iter"])
     rows = []
     for k in range(W["eval_n"]):
         u = torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] + k, link_scale=W["link_scale"],
