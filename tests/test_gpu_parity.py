@@ -309,3 +309,46 @@ def test_both_fp64_tails_reach_the_oracle_functional(lgf, dims):
         # steps: their FP32 corrections differ by at most an FP32 rounding of
         # a correction (|eps| 2^-24 < 1e-11), their link storage by 2^-47
         assert np.max(np.abs(res[0][3] - res[2][3])) < 1e-10
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_device_loop_and_host_loop_stop_at_the_same_update(lgf, mode):
+    """lgf_fix runs each phase as a device-side graph loop, or (under
+    lgf_profile) as host-queued iterations; both apply the same on-device stop
+    rule, so they stop at the same update with bit-identical links."""
+    dims = (8, 8, 8, 8)
+    U = I.synthetic_config(dims, seed=5, link_scale=0.5)
+    out = []
+    for profiled in (False, True):
+        with lgf.GaugeFixer(dims, "f32") as gf:
+            gf.set_param(7, mode)  # LGF_TAIL_MODE
+            gf.load_links(U)
+            gf.profile(profiled)
+            it, conv = gf.fix(1e-15, 2000)
+            out.append((it, conv, gf.fix_split(), gf.store_links(), gf.history()))
+    assert out[0][:3] == out[1][:3]
+    assert np.array_equal(out[0][3], out[1][3])
+    assert np.array_equal(out[0][4], out[1][4])
+
+
+def test_fp32_stall_rule_hands_over_the_same_way_in_both_loops(lgf):
+    """With a hand-over threshold FP32 cannot reach, the FP32 phase ends by the
+    stall rule (theta below 1e-6 not halving within 8 updates), applied on
+    the device after every update; both loops hand over at the same update and
+    the tail still reaches the oracle's functional."""
+    dims = (8, 8, 8, 8)
+    U, ref = _oracle_fix(dims, 2, 0.5, 1e-15)
+    out = []
+    for profiled in (False, True):
+        with lgf.GaugeFixer(dims, "f32") as gf:
+            gf.set_param(2, 1e-16)  # LGF_TAIL_THETA below the FP32 floor
+            gf.load_links(U)
+            gf.profile(profiled)
+            it, conv = gf.fix(1e-15, 2000)
+            F, th = gf.functional()
+            out.append((it, gf.fix_split(), gf.store_links()))
+            assert conv and th < 1e-15
+            assert F == pytest.approx(ref["F"], rel=1e-12)
+    assert out[0][:2] == out[1][:2]
+    n32 = out[0][1][0]
+    assert 0 < n32 < 2000  # the FP32 phase stopped by the stall rule, not the budget
+    assert np.array_equal(out[0][2], out[1][2])
