@@ -122,28 +122,40 @@ __global__ void __launch_bounds__(256) k_gstep(const cx<T>* __restrict__ D, cx<T
   gstep_site<T, NC, RT>(ldg(D + s), ldg(D + V + s), ldg(D + 2 * V + s), ldg(D + 3 * V + s), (RT)hd, G, g_out, V, s);
 }
 
-// one thread per (site, mu): the current link in the host layout
+// one thread per (site, mu): the current link G(x) U0 G(x+mu)^dag in the host
+// layout, staged through shared memory like k_store_aos (the AoS side may be
+// host memory the device writes directly)
 template <class T, int NC>
-__global__ void __launch_bounds__(256) k_materialize(const cx<T>* __restrict__ U0, const cx<T>* __restrict__ G,
-                                                     double* __restrict__ aos, const Geom geo) {
+__global__ void __launch_bounds__(kStageMats) k_materialize(const cx<T>* __restrict__ U0, const cx<T>* __restrict__ G,
+                                                            double* __restrict__ aos, const Geom geo) {
+  __shared__ double sm[kStageMats * kStagePitch];
   const int64_t V = geo.V;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 4 * V) return;
-  const int64_t s = i >> 2;
-  const int mu = (int)(i & 3);
-  int c[4];
-  site_coords(geo, s, c);
-  const M3<T> u = load_m3<T, NC>(U0 + (int64_t)mu * NC * V, V, s);
-  const M3<T> gx = load_m3<T, NC>(G, V, s);
-  const M3<T> gf = load_m3<T, NC>(G, V, site_fwd(geo, s, c, mu));
-  M3<T> w, r;
-  mm<T, 3>(w, gx, u);
-  mm_dag<T, 3>(r, w, gf);
-  double* dst = aos + i * 18;
+  const int64_t first = (int64_t)blockIdx.x * kStageMats;
+  const int n = (int)(4 * V - first < kStageMats ? 4 * V - first : kStageMats);
+  if ((int)threadIdx.x < n) {
+    const int64_t i = first + threadIdx.x;
+    const int64_t s = i >> 2;
+    const int mu = (int)(i & 3);
+    int c[4];
+    site_coords(geo, s, c);
+    const M3<T> u = load_m3<T, NC>(U0 + (int64_t)mu * NC * V, V, s);
+    const M3<T> gx = load_m3<T, NC>(G, V, s);
+    const M3<T> gf = load_m3<T, NC>(G, V, site_fwd(geo, s, c, mu));
+    M3<T> w, r;
+    mm<T, 3>(w, gx, u);
+    mm_dag<T, 3>(r, w, gf);
+    double* d = sm + threadIdx.x * kStagePitch;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    dst[2 * q] = (double)r.e[q / 3][q % 3].re;
-    dst[2 * q + 1] = (double)r.e[q / 3][q % 3].im;
+    for (int q = 0; q < 9; ++q) {
+      d[2 * q] = (double)r.e[q / 3][q % 3].re;
+      d[2 * q + 1] = (double)r.e[q / 3][q % 3].im;
+    }
+  }
+  __syncthreads();
+  double2* dst = reinterpret_cast<double2*>(aos + first * 18);
+  for (int j = threadIdx.x; j < n * 9; j += blockDim.x) {
+    const int m = (2 * j) / 18, k = (2 * j) - m * 18;
+    dst[j] = make_double2(sm[m * kStagePitch + k], sm[m * kStagePitch + k + 1]);
   }
 }
 
@@ -198,13 +210,13 @@ cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V,
 }
 
 cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s) {
-  const unsigned nb = nblocks(4 * geo.V, 256);
+  const unsigned nb = nblocks(4 * geo.V, kStageMats);
   if (nc == 9)
-    k_materialize<float, 9><<<nb, 256, 0, s>>>(static_cast<const cx<float>*>(U0), static_cast<const cx<float>*>(G),
-                                                aos, geo);
+    k_materialize<float, 9><<<nb, kStageMats, 0, s>>>(static_cast<const cx<float>*>(U0),
+                                                       static_cast<const cx<float>*>(G), aos, geo);
   else
-    k_materialize<float, 6><<<nb, 256, 0, s>>>(static_cast<const cx<float>*>(U0), static_cast<const cx<float>*>(G),
-                                                aos, geo);
+    k_materialize<float, 6><<<nb, kStageMats, 0, s>>>(static_cast<const cx<float>*>(U0),
+                                                       static_cast<const cx<float>*>(G), aos, geo);
   return cudaPeekAtLastError();
 }
 

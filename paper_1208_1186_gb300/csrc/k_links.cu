@@ -140,6 +140,77 @@ __global__ void k_aos_to_soa(const double* __restrict__ aos, cx<T>* __restrict__
   for (int c = 0; c < NC; ++c) U[((int64_t)mu * NC + c) * V + s] = mk<T>((T)src[2 * c], (T)src[2 * c + 1]);
 }
 
+// ---------------------------------------------------------------------------
+// Link loads and stores in the host layout (AoS, 18 doubles per link, 4 links
+// per site), staged through shared memory.  A CTA moves one contiguous chunk
+// of kStageMats links with 16-byte accesses; the staged rows have a pitch of
+// 19 doubles, which makes the per-thread 8-byte reads conflict-free.  The AoS
+// side may be host memory that the device reads or writes directly (pinned
+// memory over NVLink-C2C): every byte crosses once, coalesced.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stage_in(const double* __restrict__ aos, double* sm, int64_t first, int n) {
+  const double2* src = reinterpret_cast<const double2*>(aos + first * 18);
+  for (int j = threadIdx.x; j < n * 9; j += blockDim.x) {
+    const double2 v = src[j];  // doubles 2j and 2j+1 of the chunk: one link, entries k and k+1
+    const int m = (2 * j) / 18, k = (2 * j) - m * 18;
+    sm[m * kStagePitch + k] = v.x;
+    sm[m * kStagePitch + k + 1] = v.y;
+  }
+}
+
+__device__ __forceinline__ void stage_out(const double* sm, double* __restrict__ aos, int64_t first, int n) {
+  double2* dst = reinterpret_cast<double2*>(aos + first * 18);
+  for (int j = threadIdx.x; j < n * 9; j += blockDim.x) {
+    const int m = (2 * j) / 18, k = (2 * j) - m * 18;
+    dst[j] = make_double2(sm[m * kStagePitch + k], sm[m * kStagePitch + k + 1]);
+  }
+}
+
+// AoS links -> FP64 SoA (NC64 planes per direction, 0: none) and FP32 SoA
+// (NC32 planes, 0: none), one read of the input
+template <int NC64, int NC32>
+__global__ void __launch_bounds__(kStageMats) k_load_aos(const double* __restrict__ aos, cx<double>* __restrict__ U64,
+                                                         cx<float>* __restrict__ U32, int64_t V) {
+  __shared__ double sm[kStageMats * kStagePitch];
+  const int64_t first = (int64_t)blockIdx.x * kStageMats;
+  const int n = (int)(4 * V - first < kStageMats ? 4 * V - first : kStageMats);
+  stage_in(aos, sm, first, n);
+  __syncthreads();
+  if ((int)threadIdx.x >= n) return;
+  const int64_t i = first + threadIdx.x;
+  const int64_t s = i >> 2;
+  const int mu = (int)(i & 3);
+  const double* m = sm + threadIdx.x * kStagePitch;
+#pragma unroll
+  for (int c = 0; c < NC64; ++c) U64[((int64_t)mu * NC64 + c) * V + s] = mk<double>(m[2 * c], m[2 * c + 1]);
+#pragma unroll
+  for (int c = 0; c < NC32; ++c)
+    U32[((int64_t)mu * NC32 + c) * V + s] = mk<float>((float)m[2 * c], (float)m[2 * c + 1]);
+}
+
+// SoA links (rows 1-2 rebuilt for NC = 6) -> AoS doubles
+template <class T, int NC>
+__global__ void __launch_bounds__(kStageMats) k_store_aos(const cx<T>* __restrict__ U, double* __restrict__ aos,
+                                                          int64_t V) {
+  __shared__ double sm[kStageMats * kStagePitch];
+  const int64_t first = (int64_t)blockIdx.x * kStageMats;
+  const int n = (int)(4 * V - first < kStageMats ? 4 * V - first : kStageMats);
+  if ((int)threadIdx.x < n) {
+    const int64_t i = first + threadIdx.x;
+    const int64_t s = i >> 2;
+    const int mu = (int)(i & 3);
+    const M3<T> m = load_m3<T, NC>(U + (int64_t)mu * NC * V, V, s);
+    double* d = sm + threadIdx.x * kStagePitch;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      d[2 * c] = (double)m.e[c / 3][c % 3].re;
+      d[2 * c + 1] = (double)m.e[c / 3][c % 3].im;
+    }
+  }
+  __syncthreads();
+  stage_out(sm, aos, first, n);
+}
+
 template <class T, int NC>
 __global__ void k_soa_to_aos(const cx<T>* __restrict__ U, double* __restrict__ aos, int64_t V, int nmu) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,6 +342,24 @@ cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& 
 cudaError_t launch_aos_to_soa(int prec, int nc, const double* aos, void* U, int64_t V, int nmu, cudaStream_t s) {
   LGF_DISPATCH(prec, nc,
                (k_aos_to_soa<T, NC><<<blocks_for(nmu * V, 256), 256, 0, s>>>(aos, static_cast<cx<T>*>(U), V, nmu)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_load_aos(int nc64, int nc32, const double* aos, void* U64, void* U32, int64_t V, cudaStream_t s) {
+  const unsigned nb = blocks_for(4 * V, kStageMats);
+  auto d = static_cast<cx<double>*>(U64);
+  auto f = static_cast<cx<float>*>(U32);
+  if (nc64 == 9 && nc32 == 9) k_load_aos<9, 9><<<nb, kStageMats, 0, s>>>(aos, d, f, V);
+  else if (nc64 == 9 && nc32 == 6) k_load_aos<9, 6><<<nb, kStageMats, 0, s>>>(aos, d, f, V);
+  else if (nc64 == 9 && nc32 == 0) k_load_aos<9, 0><<<nb, kStageMats, 0, s>>>(aos, d, f, V);
+  else if (nc64 == 6 && nc32 == 0) k_load_aos<6, 0><<<nb, kStageMats, 0, s>>>(aos, d, f, V);
+  else return cudaErrorInvalidValue;
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_store_aos(int prec, int nc, const void* U, double* aos, int64_t V, cudaStream_t s) {
+  const unsigned nb = blocks_for(4 * V, kStageMats);
+  LGF_DISPATCH(prec, nc, (k_store_aos<T, NC><<<nb, kStageMats, 0, s>>>(static_cast<const cx<T>*>(U), aos, V)));
   return cudaPeekAtLastError();
 }
 

@@ -1166,14 +1166,21 @@ static int load_from_device_aos(lgf_handle h, const double* aos) {
   // the FP32 engine's update mode is fixed at the load; loop bodies captured
   // for the other mode are dropped
   if (h->mixed && h->e32.grep != !h->explicit_fp32) drop_loops(h);
+  const bool staged = ((uintptr_t)aos & 15) == 0;  // 16-byte copies of the input chunks
   if (h->mixed) {
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, 9, aos, h->Uorig, V, 4, h->stream));
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(4, h->e32.nc, aos, h->e32.U, V, 4, h->stream));
+    if (staged) {  // one read of the input for both copies
+      LGF_LAUNCH(h, LGF_K_OTHER, launch_load_aos(9, h->e32.nc, aos, h->Uorig, h->e32.U, V, h->stream));
+    } else {
+      LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, 9, aos, h->Uorig, V, 4, h->stream));
+      LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(4, h->e32.nc, aos, h->e32.U, V, 4, h->stream));
+    }
     LGF_LAUNCH(h, LGF_K_OTHER, launch_set_identity(4, h->e32.nc, h->G, V, h->stream));
     h->e32.grep = !h->explicit_fp32;
     h->defect = false;
     h->df = false;
     h->cur = &h->e32;
+  } else if (staged) {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_load_aos(h->e64.nc, 0, aos, h->e64.U, nullptr, V, h->stream));
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
   }
@@ -1183,8 +1190,23 @@ static int load_from_device_aos(lgf_handle h, const double* aos) {
   return LGF_OK;
 }
 
+// Device address of host memory the GPU reads and writes directly (pinned,
+// registered with CUDA, 16-byte aligned), or null: the link load and store
+// then move the host array once, inside their layout kernels, instead of a
+// staging copy plus a device-side conversion.
+static double* host_direct(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || ((uintptr_t)a.devicePointer & 15) != 0) return nullptr;
+  return static_cast<double*>(a.devicePointer);
+}
+
 int lgf_load_links(lgf_handle h, const double* host_aos) {
   if (!h || !host_aos) return LGF_ERR_ARG;
+  if (const double* direct = host_direct(host_aos)) return load_from_device_aos(h, direct);
   int rc = ensure_staging(h);
   if (rc) return rc;
   LGF_CUDA(h, cudaMemcpyAsync(h->staging, host_aos, (size_t)h->V * 72 * sizeof(double), cudaMemcpyHostToDevice,
@@ -1200,15 +1222,20 @@ int lgf_load_links_device(lgf_handle h, const double* dev_aos) {
 int lgf_store_links(lgf_handle h, double* host_aos) {
   if (!h || !host_aos) return LGF_ERR_ARG;
   if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
-  int rc = ensure_staging(h);
-  if (rc) return rc;
+  double* direct = host_direct(host_aos);
+  if (!direct) {
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+  }
+  double* dst = direct ? direct : h->staging;
   Engine& e = *h->cur;
   if (e.grep)
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, h->staging, h->geo, h->stream));
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, dst, h->geo, h->stream));
   else
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(e.prec, e.nc, e.U, h->staging, h->V, 4, h->stream));
-  LGF_CUDA(h, cudaMemcpyAsync(host_aos, h->staging, (size_t)h->V * 72 * sizeof(double), cudaMemcpyDeviceToHost,
-                              h->stream));
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos(e.prec, e.nc, e.U, dst, h->V, h->stream));
+  if (!direct)
+    LGF_CUDA(h, cudaMemcpyAsync(host_aos, h->staging, (size_t)h->V * 72 * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
   LGF_CUDA(h, cudaStreamSynchronize(h->stream));
   return LGF_OK;
 }

@@ -77,6 +77,13 @@ cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& 
 // host [s][mu][3][3] complex128 layout (on the device) <-> SoA storage
 // (nmu matrices per site: 4 for links, 1 for a gauge field)
 cudaError_t launch_aos_to_soa(int prec, int nc, const double* aos, void* U, int64_t V, int nmu, cudaStream_t s);
+// host-layout link load/store staged through shared memory (k_links.cu); the
+// AoS pointer may be host memory the device can access (16-byte aligned).
+// Load: nc64 (9 or 6, FP64) and nc32 (9, 6 or 0, FP32) SoA outputs from one read.
+constexpr int kStageMats = 256;   // links per CTA
+constexpr int kStagePitch = 19;   // doubles per staged link
+cudaError_t launch_load_aos(int nc64, int nc32, const double* aos, void* U64, void* U32, int64_t V, cudaStream_t s);
+cudaError_t launch_store_aos(int prec, int nc, const void* U, double* aos, int64_t V, cudaStream_t s);
 cudaError_t launch_soa_to_aos(int prec, int nc, const void* U, double* aos, int64_t V, int nmu, cudaStream_t s);
 // G <- reunitarised g G (storage precision); FP64 reunitarised copy of G
 cudaError_t launch_accumulate(int prec, int nc, void* G, const void* g, int64_t V, const DevState* st,

@@ -352,3 +352,34 @@ def test_fp32_stall_rule_hands_over_the_same_way_in_both_loops(lgf):
     n32 = out[0][1][0]
     assert 0 < n32 < 2000  # the FP32 phase stopped by the stall rule, not the budget
     assert np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f32_r12"])
+def test_pinned_host_buffers_match_pageable_ones(lgf, dtype):
+    """Loads from and stores to pinned host memory go straight through the
+    layout kernels (the device reads and writes the host array); pageable
+    arrays go through a staging copy.  Both give bit-identical links, after
+    iterations (FP32: links formed from G) and after a fix (FP64 links)."""
+    import torch
+    dims = (8, 8, 8, 8)
+    U = I.synthetic_config(dims, seed=7, link_scale=0.5)
+    pin_in = torch.empty(U.shape + (2,), dtype=torch.float64, pin_memory=True)
+    pin_out = torch.empty(U.shape + (2,), dtype=torch.float64, pin_memory=True)
+    assert pin_in.is_pinned() and pin_out.is_pinned()
+    hin = pin_in.numpy().view(np.complex128).reshape(U.shape)
+    hout = pin_out.numpy().view(np.complex128).reshape(U.shape)
+    hin[...] = U
+    with lgf.GaugeFixer(dims, dtype) as a, lgf.GaugeFixer(dims, dtype) as b:
+        a.load_links(U)
+        b.load_links(hin)
+        for step in ("iterate", "fix"):
+            if step == "iterate":
+                a.iterate(5)
+                b.iterate(5)
+            else:
+                a.fix(1e-12, 2000)
+                b.fix(1e-12, 2000)
+            ref = a.store_links()
+            hout[...] = 0
+            b.store_links(hout)
+            assert np.array_equal(ref, hout), step
