@@ -659,13 +659,10 @@ int tune_engine(lgf_handle h, Engine& e, int reps, int* out) {
 // ---------------------------------------------------------------------------
 struct lgf_batch_ctx {
   std::vector<lgf_handle> h;
-  std::vector<cudaStream_t> streams;  // one per member: parallel graph branches
-  std::vector<cudaEvent_t> joins;
+  std::vector<cudaStream_t> streams;  // capture streams of the lanes (at most one per member)
   cudaStream_t main = nullptr;
-  cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;        // source of exec (holds the members' loop conditions)
-  int exec_k = 0;                     // iterations per member per graph launch
   int lanes = 0;                      // parallel graph branches (0: one per member)
   std::vector<int> exec_members;      // members captured in exec
   std::vector<long long> exec_launches;  // kernels per member per graph launch
@@ -1380,16 +1377,12 @@ int lgf_batch_create(const lgf_handle* handles, int n, lgf_batch* out) {
   lgf_batch_ctx* b = new (std::nothrow) lgf_batch_ctx();
   if (!b) return fail(nullptr, LGF_ERR_OOM, "host allocation failed");
   b->h.assign(handles, handles + n);
-  bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess;
   b->streams.assign(n, nullptr);
-  b->joins.assign(n, nullptr);
-  for (int i = 0; i < n && ok; ++i)
-    ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i) ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     lgf_batch_destroy(b);
-    return fail(nullptr, LGF_ERR_CUDA, "lgf_batch_create: stream or event creation failed");
+    return fail(nullptr, LGF_ERR_CUDA, "lgf_batch_create: stream creation failed");
   }
   *out = b;
   return LGF_OK;
@@ -1401,9 +1394,6 @@ int lgf_batch_destroy(lgf_batch b) {
   drop_graph(b);
   for (cudaStream_t s : b->streams)
     if (s) cudaStreamDestroy(s);
-  for (cudaEvent_t e : b->joins)
-    if (e) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
   if (b->main) cudaStreamDestroy(b->main);
   delete b;
   return LGF_OK;
