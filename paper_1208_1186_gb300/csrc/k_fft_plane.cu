@@ -169,6 +169,50 @@ __global__ void __launch_bounds__(32) k_plane_xy_warp(cx<T>* __restrict__ D, int
   }
 }
 
+// x-y planes with 32 < L <= 64: the same scheme with one tile per CTA of two
+// warps (thread r owns y-line r, then x-line r; CTA barriers between the
+// phases).
+template <class T, int L, bool INV>
+__global__ void __launch_bounds__(64) k_plane_xy_pair(cx<T>* __restrict__ D, int V, int ntiles,
+                                                      const DevState* __restrict__ st) {
+  static_assert(L > 32 && L <= 64, "two warps per tile");
+  pdl_wait();
+  if (st != nullptr && st->done) return;
+  constexpr int P = L + 1, N = L * L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);
+  const int r = threadIdx.x, tile_id = blockIdx.x;  // = 4 plane + field
+  const bool active = r < L;
+  cx<T>* src = D + ((tile_id & 3) * V + (tile_id >> 2) * N);
+  if (active) {
+    cx<T> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = src[p * L + r];
+    if (INV)
+      regfft::inverse<T, L>(v);
+    else
+      regfft::forward<T, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[p * P + r] = v[p];
+  }
+  __syncthreads();
+  if (active) {
+    cx<T> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = tile[r * P + p];
+    if (INV)
+      regfft::inverse<T, L>(v);
+    else
+      regfft::forward<T, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[r * P + p] = v[p];
+  }
+  __syncthreads();
+  for (int k = 0; k < L; ++k)
+    if (active) src[k * L + r] = tile[k * P + r];
+  (void)ntiles;
+}
+
 // Inverse x-y transform fused with the gauge step on G (FP32 gauge
 // representation).  One CTA of four warps per floor(32 / L) planes (L <= 32): warp f inverse-
 // transforms field f of the CTA's planes exactly as k_plane_xy_warp does and
@@ -239,7 +283,70 @@ __global__ void __launch_bounds__(128) k_plane_xyinv_gstep(const cx<float>* __re
 
 template <int L>
 constexpr size_t xyinv_gstep_smem() {
-  return (size_t)4 * (32 / L) * L * (L + 1) * sizeof(cx<float>);
+  return (size_t)4 * (L <= 32 ? 32 / L : 1) * L * (L + 1) * sizeof(cx<float>);
+}
+
+// The fused kernel for 32 < L <= 64: one plane per CTA of 256 threads, two
+// warps per field for the transforms (CTA barriers between the phases), then
+// all 256 threads on the gauge step.
+template <int L, int NC, class RT, int KS>
+__global__ void __launch_bounds__(256, 2) k_plane_xyinv_gstep_pair(const cx<float>* __restrict__ D, cx<float>* G,
+                                                                int V, int nplanes, double hd,
+                                                                const DevState* __restrict__ st) {
+  static_assert(L > 32 && L <= 64, "two warps per field");
+  pdl_wait();
+  if (st != nullptr && st->done) return;
+  constexpr int P = L + 1, N = L * L, TS = L * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tiles = reinterpret_cast<cx<float>*>(smem_raw);  // [field][y][x]
+  const int f = threadIdx.x >> 6, r = threadIdx.x & 63;
+  const int plane = blockIdx.x;
+  const bool active = r < L;
+  cx<float>* tile = tiles + f * TS;
+  if (active) {
+    const cx<float>* src = D + ((int64_t)f * V + (int64_t)plane * N);
+    cx<float> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = src[p * L + r];
+    regfft::inverse<float, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[p * P + r] = v[p];
+  }
+  __syncthreads();
+  if (active) {
+    cx<float> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = tile[r * P + p];
+    regfft::inverse<float, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[r * P + p] = v[p];
+  }
+  __syncthreads();
+  const RT h = (RT)hd;
+  const int64_t base = (int64_t)plane * N;
+  for (int q0 = threadIdx.x; q0 < N; q0 += KS * blockDim.x) {
+    M3<float> Gk[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int q = q0 + k * blockDim.x;
+      if (q < N) Gk[k] = gstep_load_G<float, NC>(G, V, base + q);
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int q = q0 + k * blockDim.x;
+      if (q < N) {
+        const int o = (q / L) * P + q % L;
+        gstep_store<float, NC, RT>(gstep_g<RT>(tiles[o], tiles[TS + o], tiles[2 * TS + o], tiles[3 * TS + o], h),
+                                   Gk[k], G, V, base + q);
+      }
+    }
+  }
+  (void)nplanes;
+}
+
+template <int L>
+constexpr size_t xyinv_gstep_pair_smem() {
+  return (size_t)4 * L * (L + 1) * sizeof(cx<float>);
 }
 
 // x-run width of a z-t tile: 32 bytes of consecutive complex numbers
@@ -385,6 +492,12 @@ cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaS
     const auto Dp = static_cast<cx<T>*>(D);
     if (inverse) return launch_pdl(k_plane_xy_warp<T, L, true>, nb, 32, sm, s, Dp, (int)V, ntiles, st);
     return launch_pdl(k_plane_xy_warp<T, L, false>, nb, 32, sm, s, Dp, (int)V, ntiles, st);
+  } else if constexpr (L > 32 && L <= 64 && kXyWarpTiles) {
+    const int ntiles = 4 * Lz * Lt;
+    constexpr int sm = L * (L + 1) * (int)sizeof(cx<T>);
+    const auto Dp = static_cast<cx<T>*>(D);
+    if (inverse) return launch_pdl(k_plane_xy_pair<T, L, true>, (unsigned)ntiles, 64, sm, s, Dp, (int)V, ntiles, st);
+    return launch_pdl(k_plane_xy_pair<T, L, false>, (unsigned)ntiles, 64, sm, s, Dp, (int)V, ntiles, st);
   }
   const unsigned nb = (unsigned)(Lz * Lt);
   constexpr int NT = xy_threads<L, L>();
@@ -400,6 +513,36 @@ cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2
   dim3 grid((unsigned)((Lx / zt_bx<T>()) * Ly), 4);
   return launch_pdl(k_plane_zt<T, LZ, LT>, grid, zt_threads<T, LZ, LT>(), zt_smem_bytes<T, LZ, LT>(), s,
                     static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, st);
+}
+
+template <int L>
+cudaError_t xyinv_gstep_pair_launch(int nc, bool r64, const cx<float>* D, cx<float>* G, int V, int nplanes,
+                                    double ha, const DevState* st, cudaStream_t s) {
+  const unsigned nb = (unsigned)nplanes;
+  constexpr size_t sm = xyinv_gstep_pair_smem<L>();
+  if (nc == 9) {
+    if (r64) return launch_pdl(k_plane_xyinv_gstep_pair<L, 9, double, kXyGstepSites>, nb, 256, sm, s, D, G, V, nplanes, ha, st);
+    return launch_pdl(k_plane_xyinv_gstep_pair<L, 9, float, kXyGstepSites>, nb, 256, sm, s, D, G, V, nplanes, ha, st);
+  }
+  if (r64) return launch_pdl(k_plane_xyinv_gstep_pair<L, 6, double, kXyGstepSites>, nb, 256, sm, s, D, G, V, nplanes, ha, st);
+  return launch_pdl(k_plane_xyinv_gstep_pair<L, 6, float, kXyGstepSites>, nb, 256, sm, s, D, G, V, nplanes, ha, st);
+}
+
+template <int L>
+cudaError_t xyinv_gstep_pair_attr() {
+  constexpr int sm = (int)xyinv_gstep_pair_smem<L>();
+  cudaError_t e = cudaFuncSetAttribute(k_plane_xyinv_gstep_pair<L, 9, double, kXyGstepSites>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_plane_xyinv_gstep_pair<L, 9, float, kXyGstepSites>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_plane_xyinv_gstep_pair<L, 6, double, kXyGstepSites>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_plane_xyinv_gstep_pair<L, 6, float, kXyGstepSites>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
 }
 
 template <int L>
@@ -469,6 +612,7 @@ cudaError_t plane_pipeline_init() {
   if (e == cudaSuccess) e = zt_attr<float, A, B>();
 #define LGF_ZTA64(A, B) \
   if (e == cudaSuccess) e = zt_attr<double, A, B>();
+  if (e == cudaSuccess) e = xyinv_gstep_pair_attr<48>();
   LGF_XY_F32(LGF_XYA32)
   LGF_XY_F64(LGF_XYA64)
   LGF_ZT_F32(LGF_ZTA32)
@@ -499,7 +643,7 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
 bool plane_xyinv_gstep_supported(int prec, int L) {
   if (!kFuseXyinvGstep || prec != 4) return false;
   switch (L) {
-    case 4: case 6: case 8: case 12: case 16: case 20: case 24: case 32:
+    case 4: case 6: case 8: case 12: case 16: case 20: case 24: case 32: case 48:
       return true;
     default:
       return false;
@@ -520,6 +664,7 @@ cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int6
     case 20: return xyinv_gstep_launch<20>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     case 24: return xyinv_gstep_launch<24>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     case 32: return xyinv_gstep_launch<32>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
+    case 48: return xyinv_gstep_pair_launch<48>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -33,6 +33,7 @@ STEP_DIMS = [
     (20, 20, 4, 4),    # warp-tile x-y planes, one 20 x 20 tile per warp, 12 lanes idle
     (24, 24, 6, 6),    # warp-tile x-y planes, one 24 x 24 tile per warp, 8 lanes idle
     (6, 6, 6, 6),      # warp-tile x-y planes, five 6 x 6 tiles per warp, 2 lanes idle
+    (48, 48, 4, 4),    # two-warp x-y tiles (48 lines), fused inverse x-y + G update
     (6, 12, 4, 20),    # axis passes, radices 2, 3, 4, 5; V = 5760
     (20, 8, 24, 6),    # axis passes, V = 23040
     (4, 6, 10, 12),    # plane kernels (10); V = 2880, ragged last block
