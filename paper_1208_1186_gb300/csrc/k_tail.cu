@@ -36,6 +36,7 @@
 //
 // The tail's own error budget (each FP32 correction is exact to |eps| 2^-24,
 // about 1e-12 at the first step) is far above the double-float rounding.
+#include "lgf_df.cuh"
 #include "lgf_kernels.cuh"
 #include "lgf_reduce.cuh"
 
@@ -87,14 +88,10 @@ __global__ void __launch_bounds__(256) k_gradient_tail(const cx<double>* __restr
   grid_reduce<double>(fsum, tsum, partial, st, normF, normT, mode);
 }
 
-// eps = X + X^2 / 2, X = h Delta~ (traceless anti-Hermitian), 9 FP32 planes
-__global__ void __launch_bounds__(256) k_tail_step(const cx<float>* __restrict__ D, cx<float>* __restrict__ eps,
-                                                   int V, float h, const DevState* __restrict__ st) {
-  pdl_wait();
-  if (st != nullptr && st->done) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
-  const cx<float> c0 = ldg(D + s), c1 = ldg(D + V + s), c2 = ldg(D + 2 * V + s), c3 = ldg(D + 3 * V + s);
+// eps = X + X^2 / 2, X = h Delta~ (traceless anti-Hermitian), from the
+// packed accelerated gradient c0..c3 (Delta~_01, Delta~_02, Delta~_12,
+// Im Delta~_00 + i Im Delta~_11)
+__device__ __forceinline__ M3<float> tail_eps(cx<float> c0, cx<float> c1, cx<float> c2, cx<float> c3, float h) {
   M3<float> X;
   X.e[0][0] = mk<float>(0.f, h * c3.re);
   X.e[1][1] = mk<float>(0.f, h * c3.im);
@@ -108,10 +105,22 @@ __global__ void __launch_bounds__(256) k_tail_step(const cx<float>* __restrict__
   M3<float> X2;
   mm<float, 3>(X2, X, X);
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const int i = q / 3, j = q % 3;
-    eps[q * V + s] = X.e[i][j] + scale(X2.e[i][j], 0.5f);
-  }
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) X.e[i][j] = X.e[i][j] + scale(X2.e[i][j], 0.5f);
+  return X;
+}
+
+// eps as 9 FP32 planes (the FP64-link tail)
+__global__ void __launch_bounds__(256) k_tail_step(const cx<float>* __restrict__ D, cx<float>* __restrict__ eps,
+                                                   int V, float h, const DevState* __restrict__ st) {
+  pdl_wait();
+  if (st != nullptr && st->done) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const M3<float> e = tail_eps(ldg(D + s), ldg(D + V + s), ldg(D + 2 * V + s), ldg(D + 3 * V + s), h);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) eps[q * V + s] = e.e[q / 3][q % 3];
 }
 
 // U_mu(x) += eps(x) U + U eps(x+mu)^dag + eps(x) U eps(x+mu)^dag
@@ -151,49 +160,6 @@ __global__ void __launch_bounds__(256) k_tail_update(cx<double>* U, const cx<flo
   }
 }
 
-// ---------------------------------------------------------------------------
-// double-float arithmetic (FP32 pairs)
-// ---------------------------------------------------------------------------
-struct df {
-  float h, l;
-};
-
-// s + e = a + b exactly (Knuth)
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-
-// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker)
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-
-// x + y with both parts' errors carried (accurate under cancellation)
-__device__ __forceinline__ df df_add(df x, df y) {
-  df s = two_sum(x.h, y.h);
-  const df t = two_sum(x.l, y.l);
-  s.l += t.h;
-  s = fast_two_sum(s.h, s.l);
-  s.l += t.l;
-  return fast_two_sum(s.h, s.l);
-}
-
-// x + f for an FP32 f
-__device__ __forceinline__ df df_add_f(df x, float f) {
-  df s = two_sum(x.h, f);
-  s.l += x.l;
-  return fast_two_sum(s.h, s.l);
-}
-
-__device__ __forceinline__ df df_neg(df x) { return {-x.h, -x.l}; }
-
-struct cdf {
-  df re, im;
-};
-
 // Exact split of an FP64 value into hi + lo by bit manipulation (no FP64
 // arithmetic): hi = x truncated to 24 significant bits, lo = the remaining
 // (up to 29) bits rounded to 24.  |x| < 2^-100 (no SU(3) entry that matters)
@@ -231,31 +197,6 @@ __device__ __forceinline__ cdf load_cdf(const cx<float>* __restrict__ h, const c
   return {{a.re, b.re}, {a.im, b.im}};
 }
 
-// U_mu(x) = g(x) U_loaded,mu(x) g(x+mu)^dag, one thread per (site, mu), from
-// the exact splits g = Gh + Gl and U = Uh + Ul of the FP64 values:
-//   Gh Uh Gh'^dag in double-float (Gh Uh from exact FMA products of FP32
-//   numbers, then double-float times FP32), plus the first-order terms
-//   (Gl Uh + Gh Ul) Gh'^dag + (Gh Uh) Gl'^dag in FP32 (they are ~2^-24 of the
-//   result, so FP32 rounding leaves ~2^-48); the second-order terms (~2^-48)
-//   are dropped.
-__device__ __forceinline__ df df_add_sloppy(df x, df y) {  // error ~2^-47 (|x| + |y|)
-  df s = two_sum(x.h, y.h);
-  s.l += x.l + y.l;
-  return fast_two_sum(s.h, s.l);
-}
-
-__device__ __forceinline__ df two_prod(float a, float b) {
-  const float p = a * b;
-  return {p, fmaf(a, b, -p)};
-}
-
-__device__ __forceinline__ df df_mul_f(df x, float f) {
-  const float p = x.h * f;
-  float e = fmaf(x.h, f, -p);
-  e = fmaf(x.l, f, e);
-  return fast_two_sum(p, e);
-}
-
 __device__ __forceinline__ void split_matrix(const cx<double>* __restrict__ p, int V, int s, cx<float> (&h)[9],
                                              cx<float> (&l)[9]) {
 #pragma unroll
@@ -267,75 +208,191 @@ __device__ __forceinline__ void split_matrix(const cx<double>* __restrict__ p, i
   }
 }
 
-// one thread per (site, mu)
-__global__ void __launch_bounds__(128) k_tail_start_df(const cx<double>* __restrict__ Uin,
-                                                       const cx<double>* __restrict__ g, cx<float>* __restrict__ Uh,
-                                                       cx<float>* __restrict__ Ul, const Geom geo) {
-  const int V = (int)geo.V;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 4 * V) return;
-  const int s = i % V, mu = i / V;  // consecutive threads: consecutive sites of one direction
-  int c[4];
-  site_coords_i(geo.L, s, c);
-  const int st_mu = (int)geo.stride[mu];
-  const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - (geo.L[mu] - 1) * st_mu;
-  cx<float> Gh[9], Gl[9], UH[9], UL[9];
-  split_matrix(g, V, s, Gh, Gl);
-  split_matrix(Uin + mu * 9 * V, V, s, UH, UL);
-  cdf W[9];        // Gh Uh, double-float
-  cx<float> P[9];  // Gl Uh + Gh Ul, FP32
+// G reunitarised in double-float: Gram-Schmidt on its first two rows (the
+// projection the iteration uses, Sec. 2.1), row 3 the conjugated cross
+// product, so that Gh + Gl is special unitary to ~2^-47.  The FP32 G is
+// within ~1e-6 of unitary, so the row norms are 1 + O(1e-6) and the
+// reciprocal square root is the first-order-corrected rsqrtf of df_rsqrt.
+// Input: rows 0 and 1 of G (the first 6 planes of either storage form).
+// Output: Gh and Gl, each 9 complex FP32 planes.
+__global__ void __launch_bounds__(256) k_promote_df(const cx<float>* __restrict__ G, cx<float>* __restrict__ gh,
+                                                    cx<float>* __restrict__ gl, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  cx<float> r0[3], r1[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int j = 0; j < 3; ++j) {
+    r0[j] = ldg(G + j * V + s);
+    r1[j] = ldg(G + (3 + j) * V + s);
+  }
+  // row 0 / |row 0|
+  dacc n = dacc_zero();
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      df re = {0.f, 0.f}, im = {0.f, 0.f};
-      cx<float> p = mk<float>(0.f, 0.f);
+  for (int j = 0; j < 3; ++j) {
+    dacc_prod(n, r0[j].re, r0[j].re);
+    dacc_prod(n, r0[j].im, r0[j].im);
+  }
+  const df inv0 = df_rsqrt(dacc_result(n));
+  cdf u[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const cx<float> x = Gh[a * 3 + k], y = UH[k * 3 + b];
-        re = df_add_sloppy(re, two_prod(x.re, y.re));
-        re = df_add_sloppy(re, df_neg(two_prod(x.im, y.im)));
-        im = df_add_sloppy(im, two_prod(x.re, y.im));
-        im = df_add_sloppy(im, two_prod(x.im, y.re));
-        p = cmac(p, Gl[a * 3 + k], y);
-        p = cmac(p, x, UL[k * 3 + b]);
-      }
-      W[a * 3 + b] = {re, im};
-      P[a * 3 + b] = p;
-    }
-  cx<float> Fh[9], Fl[9];
-  split_matrix(g, V, sf, Fh, Fl);
+  for (int j = 0; j < 3; ++j) u[j] = {df_mul_f(inv0, r0[j].re), df_mul_f(inv0, r0[j].im)};
+  // <u, row 1> = sum conj(u_j) r1_j
+  dacc pr = dacc_zero(), pi = dacc_zero();
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int j = 0; j < 3; ++j) {
+    dacc_prod_df(pr, u[j].re, r1[j].re);
+    dacc_prod_df(pr, u[j].im, r1[j].im);
+    dacc_prod_df(pi, u[j].re, r1[j].im);
+    dacc_prod_df(pi, df_neg(u[j].im), r1[j].re);
+  }
+  const df ipr = dacc_result(pr), ipi = dacc_result(pi);
+  // w = row 1 - <u, row 1> u, then w / |w|
+  cdf w[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      df re = {0.f, 0.f}, im = {0.f, 0.f};
-      cx<float> corr = mk<float>(0.f, 0.f);
+  for (int j = 0; j < 3; ++j) {
+    dacc a = {r1[j].re, 0.f}, b = {r1[j].im, 0.f};
+    dacc_prod_dd(a, df_neg(ipr), u[j].re);
+    dacc_prod_dd(a, ipi, u[j].im);
+    dacc_prod_dd(b, df_neg(ipr), u[j].im);
+    dacc_prod_dd(b, df_neg(ipi), u[j].re);
+    w[j] = {dacc_result(a), dacc_result(b)};
+  }
+  n = dacc_zero();
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        // W conj(Fh): re += W.re Fh.re + W.im Fh.im, im += W.im Fh.re - W.re Fh.im
-        const cdf w = W[a * 3 + k];
-        const cx<float> f = Fh[b * 3 + k];
-        re = df_add_sloppy(re, df_mul_f(w.re, f.re));
-        re = df_add_sloppy(re, df_mul_f(w.im, f.im));
-        im = df_add_sloppy(im, df_mul_f(w.im, f.re));
-        im = df_add_sloppy(im, df_neg(df_mul_f(w.re, f.im)));
-        corr = cmac_cj(corr, P[a * 3 + k], f);
-        corr = cmac_cj(corr, mk<float>(w.re.h, w.im.h), Fl[b * 3 + k]);
-      }
-      re = df_add_f(re, corr.re);
-      im = df_add_f(im, corr.im);
-      const int o = (mu * 9 + a * 3 + b) * V + s;
-      Uh[o] = mk<float>(re.h, im.h);
-      Ul[o] = mk<float>(re.l, im.l);
-    }
+  for (int j = 0; j < 3; ++j) {
+    dacc_prod_dd(n, w[j].re, w[j].re);
+    dacc_prod_dd(n, w[j].im, w[j].im);
+  }
+  const df inv1 = df_rsqrt(dacc_result(n));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) w[j] = {df_mul(w[j].re, inv1), df_mul(w[j].im, inv1)};
+  // row 2 = conj(u x w): v_j = conj(u_k w_l - u_l w_k), (j, k, l) cyclic
+  cdf v[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int k = (j + 1) % 3, l = (j + 2) % 3;
+    dacc a = dacc_zero(), b = dacc_zero();
+    dacc_prod_dd(a, u[k].re, w[l].re);
+    dacc_prod_dd(a, df_neg(u[k].im), w[l].im);
+    dacc_prod_dd(a, df_neg(u[l].re), w[k].re);
+    dacc_prod_dd(a, u[l].im, w[k].im);
+    // -Im(u_k w_l - u_l w_k)
+    dacc_prod_dd(b, df_neg(u[k].re), w[l].im);
+    dacc_prod_dd(b, df_neg(u[k].im), w[l].re);
+    dacc_prod_dd(b, u[l].re, w[k].im);
+    dacc_prod_dd(b, u[l].im, w[k].re);
+    v[j] = {dacc_result(a), dacc_result(b)};
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    gh[j * V + s] = mk<float>(u[j].re.h, u[j].im.h);
+    gl[j * V + s] = mk<float>(u[j].re.l, u[j].im.l);
+    gh[(3 + j) * V + s] = mk<float>(w[j].re.h, w[j].im.h);
+    gl[(3 + j) * V + s] = mk<float>(w[j].re.l, w[j].im.l);
+    gh[(6 + j) * V + s] = mk<float>(v[j].re.h, v[j].im.h);
+    gl[(6 + j) * V + s] = mk<float>(v[j].re.l, v[j].im.l);
+  }
 }
 
-// Delta and F/theta from double-float links; D stored as FP32
-__global__ void __launch_bounds__(256) k_gradient_tail_df(const cx<float>* __restrict__ Uh,
-                                                          const cx<float>* __restrict__ Ul, cx<float>* __restrict__ D,
-                                                          double2* __restrict__ partial, const Geom geo, DevState* st,
-                                                          int mode, double normF, double normT) {
+// U_mu(x) = g(x) U_loaded,mu(x) g(x+mu)^dag, one thread per (site, mu), with
+// g = Gh + Gl from k_promote_df and U = Uh + Ul the exact split of the FP64
+// input.  Row a of W = g U: Gh Uh by compensated dot products of exact FP32
+// products, the first-order terms Gl Uh + Gh Ul (~2^-24 of the result) added
+// to the low parts.  Then row a of W g'^dag the same way: W Fh'^dag with W in
+// double-float, plus Wh Fl'^dag in the low parts.  The dropped second-order
+// terms are ~2^-48.  Rows are processed one at a time (no unrolling) so that
+// a thread holds U and one row of g and W, not all three.
+__global__ void __launch_bounds__(128, 4) k_tail_start_df(const cx<double>* __restrict__ Uin,
+                                                          const cx<float>* __restrict__ gh,
+                                                          const cx<float>* __restrict__ gl, cx<float>* __restrict__ Uh,
+                                                          cx<float>* __restrict__ Ul, const Geom geo) {
+  const int V = (int)geo.V;
+  // a block is 32 consecutive sites x the 4 directions, one warp per
+  // direction: the warps share g(x) through L1
+  const int mu = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (s >= V) return;
+  int c[4];
+  site_coords_i(geo.L, s, c);
+  // selects, not a runtime index: keeps c and the geometry in registers
+  const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+  const int Lm = mu == 0 ? geo.L[0] : mu == 1 ? geo.L[1] : mu == 2 ? geo.L[2] : geo.L[3];
+  const int st_mu = mu == 0 ? 1 : mu == 1 ? geo.L[0] : mu == 2 ? geo.L[0] * geo.L[1] : geo.L[0] * geo.L[1] * geo.L[2];
+  const int sf = cm < Lm - 1 ? s + st_mu : s - (Lm - 1) * st_mu;
+  cx<float> UH[9], UL[9];
+  split_matrix(Uin + mu * 9 * V, V, s, UH, UL);
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) {
+    cx<float> xh[3], xl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      xh[k] = ldg(gh + (a * 3 + k) * V + s);
+      xl[k] = ldg(gl + (a * 3 + k) * V + s);
+    }
+    cdf W[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      dacc re = dacc_zero(), im = dacc_zero();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const cx<float> x = xh[k], y = UH[k * 3 + b], xe = xl[k], ye = UL[k * 3 + b];
+        dacc_prod(re, x.re, y.re);
+        dacc_prod(re, -x.im, y.im);
+        dacc_prod(im, x.re, y.im);
+        dacc_prod(im, x.im, y.re);
+        dacc_lo(re, xe.re, y.re);
+        dacc_lo(re, -xe.im, y.im);
+        dacc_lo(re, x.re, ye.re);
+        dacc_lo(re, -x.im, ye.im);
+        dacc_lo(im, xe.re, y.im);
+        dacc_lo(im, xe.im, y.re);
+        dacc_lo(im, x.re, ye.im);
+        dacc_lo(im, x.im, ye.re);
+      }
+      W[b] = {dacc_result(re), dacc_result(im)};
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      dacc re = dacc_zero(), im = dacc_zero();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // W conj(F): re += W.re F.re + W.im F.im, im += W.im F.re - W.re F.im
+        const cx<float> f = ldg(gh + (b * 3 + k) * V + sf), fe = ldg(gl + (b * 3 + k) * V + sf);
+        const cdf w = W[k];
+        dacc_prod_df(re, w.re, f.re);
+        dacc_prod_df(re, w.im, f.im);
+        dacc_prod_df(im, w.im, f.re);
+        dacc_prod_df(im, df_neg(w.re), f.im);
+        dacc_lo(re, w.re.h, fe.re);
+        dacc_lo(re, w.im.h, fe.im);
+        dacc_lo(im, w.im.h, fe.re);
+        dacc_lo(im, -w.re.h, fe.im);
+      }
+      const df r = dacc_result(re), m = dacc_result(im);
+      const int o = (mu * 9 + a * 3 + b) * V + s;
+      Uh[o] = mk<float>(r.h, m.h);
+      Ul[o] = mk<float>(r.l, m.l);
+    }
+  }
+}
+
+// a += v (double-float) by one exact two-sum; v's low part and the sum
+// error go to the low part (the Dot2 accumulation of lgf_df.cuh for sums)
+__device__ __forceinline__ void dacc_add(dacc& a, float vh, float vl) {
+  const df t = two_sum(a.h, vh);
+  a.h = t.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(vl, t.l));
+}
+
+// Delta and F/theta from double-float links; D stored as FP32.  Per
+// direction a thread first issues all 36 loads of its own and backward
+// links (hi and lo planes), then accumulates A = sum_mu U_mu(x-mu) - U_mu(x)
+// with compensated sums (one renormalisation per entry at the end).
+__global__ void __launch_bounds__(256, 2) k_gradient_tail_df(const cx<float>* __restrict__ Uh,
+                                                             const cx<float>* __restrict__ Ul,
+                                                             cx<float>* __restrict__ D, double2* __restrict__ partial,
+                                                             const Geom geo, DevState* st, int mode, double normF,
+                                                             double normT) {
   pdl_wait();
   if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;
@@ -345,31 +402,45 @@ __global__ void __launch_bounds__(256) k_gradient_tail_df(const cx<float>* __res
   if (s < V) {
     int c[4];
     site_coords_i(geo.L, s, c);
-    cdf A[9];
+    dacc Ar[9], Ai[9], fs = dacc_zero();
 #pragma unroll
-    for (int q = 0; q < 9; ++q) A[q] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int q = 0; q < 9; ++q) Ar[q] = Ai[q] = dacc_zero();
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const int st_mu = (int)geo.stride[mu];
       const int sb = c[mu] > 0 ? s - st_mu : s + (geo.L[mu] - 1) * st_mu;
+      cx<float> oh[9], ol[9], bh[9], bl[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const cdf own = load_cdf(Uh, Ul, (mu * 9 + q) * V + s);
-        const cdf back = load_cdf(Uh, Ul, (mu * 9 + q) * V + sb);
-        // sloppy double-float sums: errors ~2^-47 of the O(1) operands,
-        // ~1e-14 absolute, far below what the tail resolves
-        A[q].re = df_add_sloppy(A[q].re, df_add_sloppy(back.re, df_neg(own.re)));
-        A[q].im = df_add_sloppy(A[q].im, df_add_sloppy(back.im, df_neg(own.im)));
-        if (q == 0 || q == 4 || q == 8) fsum = df_add_sloppy(fsum, own.re);
+        const int o = (mu * 9 + q) * V;
+        oh[q] = ldg(Uh + o + s);
+        ol[q] = ldg(Ul + o + s);
+        bh[q] = ldg(Uh + o + sb);
+        bl[q] = ldg(Ul + o + sb);
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        dacc_add(Ar[q], bh[q].re, bl[q].re);
+        dacc_add(Ar[q], -oh[q].re, -ol[q].re);
+        dacc_add(Ai[q], bh[q].im, bl[q].im);
+        dacc_add(Ai[q], -oh[q].im, -ol[q].im);
+        if (q == 0 || q == 4 || q == 8) dacc_add(fs, oh[q].re, ol[q].re);
       }
     }
+    df A_re[9], A_im[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      A_re[q] = dacc_result(Ar[q]);
+      A_im[q] = dacc_result(Ai[q]);
+    }
+    fsum = dacc_result(fs);
     // Delta = A - A^dag - trace: off-diagonal pairs and imaginary diagonal
-    const df r01 = df_add(A[1].re, df_neg(A[3].re)), i01 = df_add(A[1].im, A[3].im);
-    const df r02 = df_add(A[2].re, df_neg(A[6].re)), i02 = df_add(A[2].im, A[6].im);
-    const df r12 = df_add(A[5].re, df_neg(A[7].re)), i12 = df_add(A[5].im, A[7].im);
+    const df r01 = df_add(A_re[1], df_neg(A_re[3])), i01 = df_add(A_im[1], A_im[3]);
+    const df r02 = df_add(A_re[2], df_neg(A_re[6])), i02 = df_add(A_im[2], A_im[6]);
+    const df r12 = df_add(A_re[5], df_neg(A_re[7])), i12 = df_add(A_im[5], A_im[7]);
     // traceless imaginary diagonal: Im Tr A need not be small, so the
     // cancellation 2 a_k - a_l - a_m happens in double-float, before rounding
-    const df a0 = A[0].im, a1 = A[4].im, a2 = A[8].im;  // times 2, below
+    const df a0 = A_im[0], a1 = A_im[4], a2 = A_im[8];
     const df n0 = df_add(df_add({2.f * a0.h, 2.f * a0.l}, df_neg(a1)), df_neg(a2));
     const df n1 = df_add(df_add({2.f * a1.h, 2.f * a1.l}, df_neg(a0)), df_neg(a2));
     const float i0 = 2.f * (n0.h + n0.l) / 3.f, i1 = 2.f * (n1.h + n1.l) / 3.f, i2 = -(i0 + i1);
@@ -393,41 +464,54 @@ __global__ void __launch_bounds__(256) k_gradient_tail_df(const cx<float>* __res
   grid_reduce_warp_totals(wf, (double)tsum, partial, st, normF, normT, mode);
 }
 
-// U_mu(x) += eps(x) U + U eps(x+mu)^dag + eps(x) U eps(x+mu)^dag, the
-// correction formed in FP32 from hi, added in double-float
-__global__ void __launch_bounds__(256) k_tail_update_df(cx<float>* __restrict__ Uh, cx<float>* __restrict__ Ul,
-                                                        const cx<float>* __restrict__ eps,
-                                                        const Geom geo, const DevState* __restrict__ st) {
+// U_mu(x) += eps(x) U + U eps(x+mu)^dag + eps(x) U eps(x+mu)^dag with
+// eps = X + X^2/2 formed here from the packed accelerated gradient (no eps
+// array): the correction in FP32 from hi, added in double-float.  A block is
+// 32 consecutive sites x the 4 directions, one warp per direction; each
+// thread issues all its loads (two packed gradients, hi and lo links) first.
+__global__ void __launch_bounds__(128, 4) k_tail_update_df(cx<float>* __restrict__ Uh, cx<float>* __restrict__ Ul,
+                                                           const cx<float>* __restrict__ D, float h, const Geom geo,
+                                                           const DevState* __restrict__ st) {
   pdl_wait();
   if (st != nullptr && st->done) return;
   const int V = (int)geo.V;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + (threadIdx.x & 31);
   if (s >= V) return;
   int c[4];
   site_coords_i(geo.L, s, c);
-  const M3<float> ex = load_m3i<float, 9>(eps, V, s);
+  const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+  const int Lm = mu == 0 ? geo.L[0] : mu == 1 ? geo.L[1] : mu == 2 ? geo.L[2] : geo.L[3];
+  const int st_mu = mu == 0 ? 1 : mu == 1 ? geo.L[0] : mu == 2 ? geo.L[0] * geo.L[1] : geo.L[0] * geo.L[1] * geo.L[2];
+  const int sf = cm < Lm - 1 ? s + st_mu : s - (Lm - 1) * st_mu;
+  const cx<float> x0 = ldg(D + s), x1 = ldg(D + V + s), x2 = ldg(D + 2 * V + s), x3 = ldg(D + 3 * V + s);
+  const cx<float> f0 = ldg(D + sf), f1 = ldg(D + V + sf), f2 = ldg(D + 2 * V + sf), f3 = ldg(D + 3 * V + sf);
+  M3<float> uh;
+  cx<float> ul[9];
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) {
-    const int st_mu = (int)geo.stride[mu];
-    const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - (geo.L[mu] - 1) * st_mu;
-    const M3<float> ef = load_m3i<float, 9>(eps, V, sf);
-    M3<float> uh;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) uh.e[q / 3][q % 3] = Uh[(mu * 9 + q) * V + s];
-    M3<float> a, d;
-    mm<float, 3>(a, ex, uh);      // eps U
+  for (int q = 0; q < 9; ++q) {
+    const int o = (mu * 9 + q) * V + s;
+    uh.e[q / 3][q % 3] = Uh[o];
+    ul[q] = Ul[o];
+  }
+  M3<float> a, d;
+  {
+    const M3<float> ex = tail_eps(x0, x1, x2, x3, h);
+    mm<float, 3>(a, ex, uh);  // eps U
+  }
+  {
+    const M3<float> ef = tail_eps(f0, f1, f2, f3, h);
     mm_dag<float, 3>(d, uh, ef);  // U eps'^dag
     mm_dag_acc(d, a, ef);         // + eps U eps'^dag
+  }
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const int o = (mu * 9 + q) * V + s;
-      const cx<float> delta = a.e[q / 3][q % 3] + d.e[q / 3][q % 3];
-      const cx<float> lo = Ul[o];
-      const df re = df_add_f({uh.e[q / 3][q % 3].re, lo.re}, delta.re);
-      const df im = df_add_f({uh.e[q / 3][q % 3].im, lo.im}, delta.im);
-      Uh[o] = mk<float>(re.h, im.h);
-      Ul[o] = mk<float>(re.l, im.l);
-    }
+  for (int q = 0; q < 9; ++q) {
+    const int o = (mu * 9 + q) * V + s;
+    const cx<float> delta = a.e[q / 3][q % 3] + d.e[q / 3][q % 3];
+    const df re = df_add_f({uh.e[q / 3][q % 3].re, ul[q].re}, delta.re);
+    const df im = df_add_f({uh.e[q / 3][q % 3].im, ul[q].im}, delta.im);
+    Uh[o] = mk<float>(re.h, im.h);
+    Ul[o] = mk<float>(re.l, im.l);
   }
 }
 
@@ -444,12 +528,17 @@ __global__ void __launch_bounds__(256) k_df_to_fp64(const cx<float>* __restrict_
 
 }  // namespace
 
-cudaError_t launch_tail_start_df(const void* Uin64, const void* g64, void* Udf, const Geom& geo, cudaStream_t s) {
-  const int64_t n = 4 * geo.V;
+cudaError_t launch_promote_df(const void* G32, void* g_df, int64_t V, cudaStream_t s) {
+  auto h = static_cast<cx<float>*>(g_df);
+  k_promote_df<<<(unsigned)((V + 255) / 256), 256, 0, s>>>(static_cast<const cx<float>*>(G32), h, h + 9 * V, (int)V);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf, const Geom& geo, cudaStream_t s) {
   auto h = static_cast<cx<float>*>(Udf);
-  k_tail_start_df<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(static_cast<const cx<double>*>(Uin64),
-                                                               static_cast<const cx<double>*>(g64), h, h + 36 * geo.V,
-                                                               geo);
+  auto g = static_cast<const cx<float>*>(g_df);
+  k_tail_start_df<<<(unsigned)((geo.V + 31) / 32), 128, 0, s>>>(static_cast<const cx<double>*>(Uin64), g,
+                                                               g + 9 * geo.V, h, h + 36 * geo.V, geo);
   return cudaPeekAtLastError();
 }
 
@@ -462,10 +551,11 @@ cudaError_t launch_gradient_tail_df(const void* Udf, void* D32, double2* partial
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_tail_update_df(void* Udf, const void* eps, const Geom& geo, const DevState* st, cudaStream_t s) {
+cudaError_t launch_tail_update_df(void* Udf, const void* D32, double half_alpha, const Geom& geo,
+                                  const DevState* st, cudaStream_t s) {
   auto h = static_cast<cx<float>*>(Udf);
-  launch_pdl(k_tail_update_df, (unsigned)((geo.V + 255) / 256), 256, 0, s, h, h + 36 * geo.V,
-             static_cast<const cx<float>*>(eps), geo, st);
+  launch_pdl(k_tail_update_df, (unsigned)((geo.V + 31) / 32), 128, 0, s, h, h + 36 * geo.V,
+             static_cast<const cx<float>*>(D32), (float)half_alpha, geo, st);
   return cudaPeekAtLastError();
 }
 

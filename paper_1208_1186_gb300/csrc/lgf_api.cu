@@ -348,13 +348,12 @@ int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
 }
 
 // FP64 tail start of a mixed handle after its FP32 phase: the gauge G
-// reunitarised in FP64, then the links rebuilt from the loaded input as
-// G U_loaded G^dagger.  The defect-correction tail (theta < 1e-8 at the
+// reunitarised (in double-float for the double-float tail, else in FP64),
+// then the links rebuilt from the loaded input as G U_loaded G^dagger.  The defect-correction tail (theta < 1e-8 at the
 // hand-over, tail modes 0 and 2) and, in mode 0, its double-float links are
 // chosen here.
 int queue_tail_start(lgf_handle h) {
   const int64_t V = h->V;
-  LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
   h->defect = h->tail_mode != 1 && h->st_host->theta < 1e-8;
   h->df = h->defect && h->tail_mode == 0;
   if (h->df) {
@@ -362,8 +361,11 @@ int queue_tail_start(lgf_handle h) {
       h->Udf = dev_alloc(h, (size_t)2 * 36 * V * sizeof(float) * 2);
       if (!h->Udf) return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail links failed");
     }
+    // e64.g (9 FP64 complex planes) holds Gh and Gl (2 x 9 FP32 complex planes)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_df(h->G, h->e64.g, V, h->stream));
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_start_df(h->Uorig, h->e64.g, h->Udf, h->geo, h->stream));
   } else {
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
     LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
   }
@@ -403,8 +405,7 @@ int queue_iteration(lgf_handle h, Engine& e) {
     LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient_tail_df(h->Udf, f.D, h->partial, h->geo, h->st, 1, s));
     int rc = queue_accelerate(h, f, h->st);
     if (rc) return rc;
-    LGF_LAUNCH(h, LGF_K_BUILD_G, launch_tail_step(f.D, f.g, h->V, 0.5 * h->alpha, h->st, s));
-    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_update_df(h->Udf, f.g, h->geo, h->st, s));
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_update_df(h->Udf, f.D, 0.5 * h->alpha, h->geo, h->st, s));
     return LGF_OK;
   }
   if (h->defect && &e == &h->e64) {

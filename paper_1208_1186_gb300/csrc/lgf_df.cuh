@@ -1,0 +1,141 @@
+// Double-float arithmetic on the FP32 pipe for the FP64 tail (value = h + l,
+// |l| <= ulp(h)/2, 48 significant bits).  Built from the error-free
+// transformations of Knuth (two-sum), Dekker (fast-two-sum) and the FMA
+// two-product.  Every rounding step that must happen exactly as written uses
+// the _rn intrinsics, which the compiler never contracts into a fused
+// multiply-add: a contraction would change fl(a + b) in a two-sum and break
+// its error-free property.
+#pragma once
+
+#include "lgf_common.cuh"
+
+namespace lgf {
+
+struct df {
+  float h, l;
+};
+
+struct cdf {
+  df re, im;
+};
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker)
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// p + e = a b exactly (FMA two-product)
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// x + y with both parts' errors carried (accurate under cancellation)
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.h, y.h);
+  const df t = two_sum(x.l, y.l);
+  s.l = __fadd_rn(s.l, t.h);
+  s = fast_two_sum(s.h, s.l);
+  s.l = __fadd_rn(s.l, t.l);
+  return fast_two_sum(s.h, s.l);
+}
+
+// x + y, error ~2^-47 (|x| + |y|)
+__device__ __forceinline__ df df_add_sloppy(df x, df y) {
+  df s = two_sum(x.h, y.h);
+  s.l = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
+  return fast_two_sum(s.h, s.l);
+}
+
+// x + f for an FP32 f
+__device__ __forceinline__ df df_add_f(df x, float f) {
+  df s = two_sum(x.h, f);
+  s.l = __fadd_rn(s.l, x.l);
+  return fast_two_sum(s.h, s.l);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return {-x.h, -x.l}; }
+
+// x f for an FP32 f
+__device__ __forceinline__ df df_mul_f(df x, float f) {
+  const df p = two_prod(x.h, f);
+  return fast_two_sum(p.h, __fmaf_rn(x.l, f, p.l));
+}
+
+// x y, both double-float (the product of the two low parts, ~2^-48 |x y|,
+// is dropped)
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const df p = two_prod(x.h, y.h);
+  return fast_two_sum(p.h, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, p.l)));
+}
+
+// ---------------------------------------------------------------------------
+// Compensated dot products (the Dot2 scheme of Ogita, Rump and Oishi, 2005):
+// the running sum's high part advances by exact two-sums, every product and
+// sum error goes into one FP32 low part, and the pair is renormalised once at
+// the end.  The result is as accurate as a dot product evaluated in twice the
+// working precision, at about 10 operations per term instead of 13 for a
+// renormalising double-float addition per term.
+// ---------------------------------------------------------------------------
+struct dacc {
+  float h, l;
+};
+
+__device__ __forceinline__ dacc dacc_zero() { return {0.f, 0.f}; }
+
+// a += x y, x and y FP32
+__device__ __forceinline__ void dacc_prod(dacc& a, float x, float y) {
+  const df p = two_prod(x, y);
+  const df s = two_sum(a.h, p.h);
+  a.h = s.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(p.l, s.l));
+}
+
+// a += x y, x double-float, y FP32
+__device__ __forceinline__ void dacc_prod_df(dacc& a, df x, float y) {
+  const df p = two_prod(x.h, y);
+  const df s = two_sum(a.h, p.h);
+  a.h = s.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(__fmaf_rn(x.l, y, p.l), s.l));
+}
+
+// a += x y, both double-float
+__device__ __forceinline__ void dacc_prod_dd(dacc& a, df x, df y) {
+  const df p = two_prod(x.h, y.h);
+  const df s = two_sum(a.h, p.h);
+  a.h = s.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(__fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, p.l)), s.l));
+}
+
+// a += a first-order (low-part) term x y: it lands in the low part only
+__device__ __forceinline__ void dacc_lo(dacc& a, float x, float y) { a.l = __fmaf_rn(x, y, a.l); }
+
+__device__ __forceinline__ df dacc_result(dacc a) { return fast_two_sum(a.h, a.l); }
+
+// 1 / sqrt(n) for a double-float n near 1 (a row norm of a matrix within
+// ~1e-3 of unitary): y = rsqrtf(n.h), then with n y^2 = 1 + d, |d| ~ 2^-22,
+// 1/sqrt(n) = y (1 - d/2 + 3 d^2 / 8 - ...), whose next term (~2^-68) is far
+// below double-float rounding.  d is formed exactly: n.h y^2 - 1 by an exact
+// subtraction (Sterbenz) plus the low parts.
+__device__ __forceinline__ df df_rsqrt(df n) {
+  const float y = rsqrtf(n.h);
+  const df t = two_prod(y, y);
+  const df m = two_prod(n.h, t.h);
+  const float dh = __fsub_rn(m.h, 1.f);
+  const float dl = __fmaf_rn(n.h, t.l, __fmaf_rn(n.l, t.h, m.l));
+  // y (-dh / 2) exactly, the rest to first order
+  const df p = two_prod(y, -0.5f * dh);
+  const float rest = __fmaf_rn(y, __fmaf_rn(0.375f * dh, dh, -0.5f * dl), p.l);
+  const df q = fast_two_sum(y, p.h);
+  return fast_two_sum(q.h, __fadd_rn(q.l, rest));
+}
+
+}  // namespace lgf

@@ -131,10 +131,15 @@ cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* ao
 
 // FP64 tail by defect correction with double-float links (k_tail.cu): Udf
 // holds 36 V complex hi parts followed by 36 V complex lo parts
-cudaError_t launch_tail_start_df(const void* Uin64, const void* g64, void* Udf, const Geom& geo, cudaStream_t s);
+// G (FP32, rows 0-1 used) -> Gh, Gl (2 x 9 FP32 complex planes), reunitarised in double-float
+cudaError_t launch_promote_df(const void* G32, void* g_df, int64_t V, cudaStream_t s);
+// Udf = Gh+Gl U_loaded (Gh+Gl)(x+mu)^dag in double-float (hi planes, then lo planes)
+cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf, const Geom& geo, cudaStream_t s);
 cudaError_t launch_gradient_tail_df(const void* Udf, void* D32, double2* partial, const Geom& geo, DevState* st,
                                     int mode, cudaStream_t s);
-cudaError_t launch_tail_update_df(void* Udf, const void* eps, const Geom& geo, const DevState* st, cudaStream_t s);
+// Udf += (1 + eps) Udf (1 + eps(x+mu))^dag - Udf, eps = X + X^2/2 with X = half_alpha Delta~ from D32
+cudaError_t launch_tail_update_df(void* Udf, const void* D32, double half_alpha, const Geom& geo,
+                                  const DevState* st, cudaStream_t s);
 cudaError_t launch_df_to_fp64(const void* Udf, void* U64, int64_t V, cudaStream_t s);
 // FP64 tail by defect correction (k_tail.cu): FP64 links, FP32 FFT and step
 cudaError_t launch_gradient_tail(const void* U64, void* D32, double2* partial, const Geom& geo, DevState* st,

@@ -311,6 +311,35 @@ def test_both_fp64_tails_reach_the_oracle_functional(lgf, dims):
         # a correction (|eps| 2^-24 < 1e-11), their link storage by 2^-47
         assert np.max(np.abs(res[0][3] - res[2][3])) < 1e-10
 
+@pytest.mark.parametrize("dtype", ["f32", "f32_r12"])
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (12, 12, 32, 8)])
+def test_double_float_tail_start_matches_the_fp64_one(lgf, dims, dtype):
+    """The tail start alone: a fix capped at the FP32 phase's own length runs
+    that phase, rebuilds the links from the loaded input as G U G'^dag and
+    stops.  In tail mode 0 G is reunitarised and the product formed in
+    double-float (48-bit significands), in mode 2 in FP64: the links agree to
+    a few 2^-47 per entry.  Mode 2 is unitary to FP64 rounding; the
+    double-float links carry a representation error of up to 2^-48 per real,
+    and det U sums six triple products of them, so their defect bound is
+    6 x 3 x 2 x 2^-48 ~ 1.3e-13."""
+    U = I.synthetic_config(dims, seed=3, link_scale=0.5)
+    with lgf.GaugeFixer(dims, dtype) as gf:
+        gf.load_links(U)
+        gf.fix(1e-15, 2000)
+        n32 = gf.fix_split()[0]
+    out = {}
+    for mode in (0, 2):
+        with lgf.GaugeFixer(dims, dtype) as gf:
+            gf.set_param(7, mode)  # LGF_TAIL_MODE
+            gf.load_links(U)
+            it, conv = gf.fix(1e-15, n32)
+            assert it == n32 and not conv
+            out[mode] = gf.store_links()
+    assert np.max(np.abs(out[0] - out[2])) < 5e-14
+    assert O.unitarity_defect(out[0]) < 1.3e-13
+    assert O.unitarity_defect(out[2]) < 5e-14
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_device_loop_and_host_loop_stop_at_the_same_update(lgf, mode):
     """lgf_fix runs each phase as a device-side graph loop, or (under
