@@ -25,12 +25,15 @@
 // transformations (Knuth's two-sum, Dekker's fast-two-sum, the FMA
 // two-product):
 //
-//   k_tail_start_df     U = g U_loaded g(x+mu)^dag from the FP64 input and the
-//                       FP64-reunitarised gauge, both split exactly into
-//                       hi + lo by bit manipulation, products in double-float;
+//   k_promote_df        the FP32 gauge G reunitarised in double-float
+//                       (Gram-Schmidt), stored as hi and lo planes;
+//   k_tail_start_df     U = g U_loaded g(x+mu)^dag from the FP64 input (split
+//                       exactly into hi + lo by bit manipulation) and that
+//                       g, products in double-float;
 //   k_gradient_tail_df  Delta by double-float sums, F summed in double-float
 //                       per warp, D stored as FP32;
-//   k_tail_update_df    U += the FP32 correction, a double-float addition;
+//   k_tail_update_df    eps from the accelerated gradient, U += the FP32
+//                       correction, a double-float addition;
 //   k_df_to_fp64        the final links back to FP64 (exact conversions, one
 //                       FP64 addition per real).
 //
