@@ -89,8 +89,9 @@ enum lgf_param {
                             theta < 1e-8: FP32 acceleration and step, g = 1 +
                             eps with eps the exponential to second order, the
                             correction added to links held in double-float
-                            form (FP32 hi + lo, 48 bits; converted back to
-                            FP64 at the end); 2 the same tail on FP64 links;
+                            form (FP32 hi + lo, 48 bits), which they keep
+                            until the next load (lgf_store_links writes them
+                            as FP64, hi + lo); 2 the same tail on FP64 links;
                             1 always uses the plain FP64 iteration.  Values
                             other than 0, 1, 2 give LGF_ERR_ARG.              */
   LGF_LINK_UPDATE = 6    /* FP32 storage, from the next load: 0 (default) keeps
@@ -148,8 +149,8 @@ int lgf_iterate(lgf_handle h, int n);
  * LGF_ERR_NOT_CONVERGED or an error.  Mixed-precision handles run the FP32
  * phase down to LGF_TAIL_THETA (or until theta below 1e-6 stops halving
  * within 8 updates), then rebuild the links in FP64 from the loaded input and
- * the accumulated gauge transformation and finish in FP64; the links are
- * FP64 from then on until the next load.  Each phase runs as one CUDA graph
+ * the accumulated gauge transformation and finish in FP64; the links stay
+ * in that FP64 form (double-float in tail mode 0) until the next load.  Each phase runs as one CUDA graph
  * launch with the loop on the device (the first call builds the graphs; the
  * host waits once per phase); under lgf_profile the host queues the
  * iterations instead.  Both stop at the same update. */

@@ -13,6 +13,7 @@
 //
 // Links of direction mu occupy NC complex planes of V elements:
 // U[(mu*NC + c)*V + s]; NC = 9 stores every entry, NC = 6 rows 1-2 only.
+#include "lgf_df.cuh"
 #include "lgf_kernels.cuh"
 #include "lgf_reduce.cuh"
 
@@ -211,6 +212,31 @@ __global__ void __launch_bounds__(kStageMats) k_store_aos(const cx<T>* __restric
   stage_out(sm, aos, first, n);
 }
 
+// double-float links (36 hi planes, then 36 lo planes) -> AoS doubles, each
+// entry hi + lo exactly
+__global__ void __launch_bounds__(kStageMats) k_store_aos_df(const cx<float>* __restrict__ Uh,
+                                                             const cx<float>* __restrict__ Ul,
+                                                             double* __restrict__ aos, int64_t V) {
+  __shared__ double sm[kStageMats * kStagePitch];
+  const int64_t first = (int64_t)blockIdx.x * kStageMats;
+  const int n = (int)(4 * V - first < kStageMats ? 4 * V - first : kStageMats);
+  if ((int)threadIdx.x < n) {
+    const int64_t i = first + threadIdx.x;
+    const int64_t s = i >> 2;
+    const int mu = (int)(i & 3);
+    double* d = sm + threadIdx.x * kStagePitch;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const int64_t o = ((int64_t)mu * 9 + c) * V + s;
+      const cx<float> h = ldg(Uh + o), l = ldg(Ul + o);
+      d[2 * c] = df_to_double(h.re, l.re);
+      d[2 * c + 1] = df_to_double(h.im, l.im);
+    }
+  }
+  __syncthreads();
+  stage_out(sm, aos, first, n);
+}
+
 template <class T, int NC>
 __global__ void k_soa_to_aos(const cx<T>* __restrict__ U, double* __restrict__ aos, int64_t V, int nmu) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,6 +408,12 @@ cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, i
   LGF_DISPATCH(prec, nc,
                (k_promote_gauge<T, NC><<<blocks_for(V, 256), 256, 0, s>>>(static_cast<const cx<T>*>(G),
                                                                           static_cast<cx<double>*>(out64), V)));
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_store_aos_df(const void* Udf, double* aos, int64_t V, cudaStream_t s) {
+  auto h = static_cast<const cx<float>*>(Udf);
+  k_store_aos_df<<<blocks_for(4 * V, kStageMats), kStageMats, 0, s>>>(h, h + 36 * V, aos, V);
   return cudaPeekAtLastError();
 }
 

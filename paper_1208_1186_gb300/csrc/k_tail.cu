@@ -34,8 +34,10 @@
 //                       per warp, D stored as FP32;
 //   k_tail_update_df    eps from the accelerated gradient, U += the FP32
 //                       correction, a double-float addition;
-//   k_df_to_fp64        the final links back to FP64 (exact conversions, one
-//                       FP64 addition per real).
+//   k_df_to_fp64        the links as FP64 planes, for the calls that need
+//                       them (exact conversions, one FP64 addition per
+//                       real); the links otherwise stay double-float, and
+//                       the host store writes FP64 from hi + lo directly.
 //
 // The tail's own error budget (each FP32 correction is exact to |eps| 2^-24,
 // about 1e-12 at the first step) is far above the double-float rounding.
@@ -180,24 +182,6 @@ __device__ __forceinline__ df split_fp64(double x) {
   const float scale = se >= 1 ? __uint_as_float((unsigned)se << 23) : 0.f;
   const float lo = __uint2float_rn((unsigned)(m & 0x1fffffffull)) * scale;
   return {hi, sign ? -lo : lo};
-}
-
-// Exact FP64 value of an FP32 number by bit manipulation (normal numbers and
-// zero; FP32 subnormals, below 1.2e-38, map to zero; NaN/Inf to NaN).
-__device__ __forceinline__ double fp32_to_fp64_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
-  const int e = (int)((u >> 23) & 0xffu);
-  if (e == 0) return __longlong_as_double((long long)s);
-  if (e == 0xff) return __longlong_as_double(0x7ff8000000000000ll);
-  const unsigned long long bits = s | ((unsigned long long)(e - 127 + 1023) << 52) |
-                                  ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)bits);
-}
-
-__device__ __forceinline__ cdf load_cdf(const cx<float>* __restrict__ h, const cx<float>* __restrict__ l, int i) {
-  const cx<float> a = ldg(h + i), b = ldg(l + i);
-  return {{a.re, b.re}, {a.im, b.im}};
 }
 
 __device__ __forceinline__ void split_matrix(const cx<double>* __restrict__ p, int V, int s, cx<float> (&h)[9],
@@ -525,8 +509,7 @@ __global__ void __launch_bounds__(256) k_df_to_fp64(const cx<float>* __restrict_
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const cx<float> h = ldg(Uh + i), l = ldg(Ul + i);
-  U[i] = mk<double>(fp32_to_fp64_bits(h.re) + fp32_to_fp64_bits(l.re),
-                    fp32_to_fp64_bits(h.im) + fp32_to_fp64_bits(l.im));
+  U[i] = mk<double>(df_to_double(h.re, l.re), df_to_double(h.im, l.im));
 }
 
 }  // namespace

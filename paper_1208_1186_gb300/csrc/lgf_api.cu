@@ -373,10 +373,12 @@ int queue_tail_start(lgf_handle h) {
   return LGF_OK;
 }
 
-// After a double-float tail: its links into the FP64 engine, which holds the
-// handle's links from then on (a later lgf_fix continues in FP64).
-int finish_df_tail(lgf_handle h) {
-  if (!h->df) return LGF_OK;
+// After a double-float tail the handle's links stay in double-float form
+// (h->df): later fixes and iterations continue on them, lgf_functional takes
+// the double-float gradient and lgf_store_links writes FP64 from hi + lo.
+// Calls that need the links as FP64 planes convert them here first.
+int materialize_df(lgf_handle h) {
+  if (!h->df || h->cur != &h->e64) return LGF_OK;
   LGF_LAUNCH(h, LGF_K_OTHER, launch_df_to_fp64(h->Udf, h->e64.U, h->V, h->stream));
   h->df = false;
   return LGF_OK;
@@ -384,7 +386,10 @@ int finish_df_tail(lgf_handle h) {
 
 // Gradient (+ F/theta reduction) of the engine's current links.
 int queue_gradient(lgf_handle h, Engine& e, int mode) {
-  if (e.grep)
+  if (&e == &h->e64 && h->df)
+    LGF_LAUNCH(h, LGF_K_GRADIENT,
+               launch_gradient_tail_df(h->Udf, h->e32.D, h->partial, h->geo, h->st, mode, h->stream));
+  else if (e.grep)
     LGF_LAUNCH(h, LGF_K_GRADIENT,
                launch_gradient_grep(e.nc, e.U, h->G, e.D, h->partial, h->geo, h->st, mode, h->stream));
   else
@@ -1227,7 +1232,9 @@ int lgf_store_links(lgf_handle h, double* host_aos) {
   }
   double* dst = direct ? direct : h->staging;
   Engine& e = *h->cur;
-  if (e.grep)
+  if (&e == &h->e64 && h->df)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos_df(h->Udf, dst, h->V, h->stream));
+  else if (e.grep)
     LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, dst, h->geo, h->stream));
   else
     LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos(e.prec, e.nc, e.U, dst, h->V, h->stream));
@@ -1281,8 +1288,6 @@ int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out) {
   const int left = max_iter - n1;
   rc = run_fix(h, *h->cur, theta_tol, left, false, &n2, &conv);
   if (rc) return rc;
-  rc = finish_df_tail(h);
-  if (rc) return rc;
   h->total_updates += n2;
   if (h->cur == &h->e64)
     h->last_n64 = n2;
@@ -1308,7 +1313,9 @@ int lgf_functional(lgf_handle h, double* F, double* theta) {
 int lgf_probe(lgf_handle h, double* delta_packed, double* delta_tilde_packed, double* g) {
   if (!h) return LGF_ERR_ARG;
   if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
-  int rc = ensure_staging(h);
+  int rc = materialize_df(h);
+  if (rc) return rc;
+  rc = ensure_staging(h);
   if (rc) return rc;
   Engine& e = *h->cur;
   const int64_t V = h->V;
@@ -1467,14 +1474,6 @@ int lgf_batch_fix(lgf_batch b, double theta_tol, int max_iter, int* iters_out, i
   std::vector<char> stall2(tail.size(), 0);
   rc = run_members(b, tail, tol2, cap2, stall2);
   if (rc) return rc;
-  for (int i : tail) {  // double-float tails back to FP64 links
-    lgf_handle h = b->h[i];
-    cudaStream_t saved = h->stream;
-    h->stream = b->main;
-    rc = finish_df_tail(h);
-    h->stream = saved;
-    if (rc) return bfail(b, rc, h->err);
-  }
   LGF_BCUDA(b, cudaStreamSynchronize(b->main));
   for (int i : tail) {
     n2[i] = b->h[i]->st_host->iters;

@@ -138,4 +138,23 @@ __device__ __forceinline__ df df_rsqrt(df n) {
   return fast_two_sum(q.h, __fadd_rn(q.l, rest));
 }
 
+// Exact FP64 value of an FP32 number by bit manipulation (normal numbers and
+// zero; FP32 subnormals, below 1.2e-38, map to zero; NaN/Inf to NaN).
+__device__ __forceinline__ double fp32_to_fp64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  const int e = (int)((u >> 23) & 0xffu);
+  if (e == 0) return __longlong_as_double((long long)s);
+  if (e == 0xff) return __longlong_as_double(0x7ff8000000000000ll);
+  const unsigned long long bits = s | ((unsigned long long)(e - 127 + 1023) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// hi + lo as one FP64 value by one FP64 addition: exact whenever the pair's
+// bits span at most 53 binary places, else its FP64 rounding
+__device__ __forceinline__ double df_to_double(float h, float l) {
+  return fp32_to_fp64_bits(h) + fp32_to_fp64_bits(l);
+}
+
 }  // namespace lgf

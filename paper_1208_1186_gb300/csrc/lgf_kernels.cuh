@@ -88,6 +88,8 @@ cudaError_t launch_soa_to_aos(int prec, int nc, const void* U, double* aos, int6
 // G <- reunitarised g G (storage precision); FP64 reunitarised copy of G
 cudaError_t launch_accumulate(int prec, int nc, void* G, const void* g, int64_t V, const DevState* st,
                               cudaStream_t s);
+// double-float links (hi planes, then lo planes) -> AoS doubles (host or device)
+cudaError_t launch_store_aos_df(const void* Udf, double* aos, int64_t V, cudaStream_t s);
 cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, int64_t V, cudaStream_t s);
 // G <- 1 at every site
 cudaError_t launch_set_identity(int prec, int nc, void* G, int64_t V, cudaStream_t s);
