@@ -238,35 +238,64 @@ def profile_traffic(kernel: str, workload: str, gauge_rep: bool):
     return None
 
 
+class Replicas:
+    """One process per GPU under torchrun (RANK, LOCAL_RANK, WORLD_SIZE from
+    the environment), each fixing its own configuration: no collective on the
+    data path.  Timing across ranks: a barrier before and after each timed
+    region and the maximum of the ranks' times; the reported value is the
+    units all ranks processed over that maximum."""
+
+    def __init__(self, backend: str, device):
+        import torch.distributed as dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.device = device
+        self._dist = dist
+        if self.world > 1 and not dist.is_initialized():
+            if backend == "nccl":
+                dist.init_process_group(backend, device_id=device)
+            else:
+                dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            self._dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self._dist.all_reduce(t, op=self._dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def seed(self, base: int) -> int:
+        return base + self.rank
+
+    def throughput(self, units_per_rank: float, seconds_max: float) -> float:
+        return self.world * units_per_rank / seconds_max
+
+    def close(self):
+        if self.world > 1 and self._dist.is_initialized():
+            self._dist.destroy_process_group()
+
+
 def run_ours(args, W):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import lgf_inputs
     import paper_1208_1186_gb300 as lgf
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    rp = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rp.world, rp.rank
+    barrier, max_over_ranks = rp.barrier, rp.max
 
     dims = W["dims"]
     V = int(np.prod(dims))
-    seed = W["seed"] + rank  # independent configurations per rank (replicas)
+    seed = rp.seed(W["seed"])  # independent configurations per rank (replicas)
     t = time.time()
     from lgf_inputs import torch_gen
     Ud = torch_gen.synthetic_config(dims, seed=seed, link_scale=W["link_scale"], gauge_scale=W["gauge_scale"],
@@ -373,8 +402,7 @@ def run_ours(args, W):
     gf.close()
 
     if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
+        rp.close()
         return None
 
     prec = 4 if W["dtype"].startswith("f32") else 8
@@ -394,7 +422,7 @@ def run_ours(args, W):
     ach = kernels[dom]["algorithmic_gbs"]
     step_bytes = sum(bytes_per_site(k, prec, r, gauge_rep) * kernels[k]["launches"] / args.steps
                      for k in kernels) * V
-    value = world * V * args.steps / (ms_max / 1e3)
+    value = rp.throughput(V * args.steps, ms_max / 1e3)
     h2d = V * 576
     d2h = V * 576
     line = {
@@ -431,7 +459,7 @@ def run_ours(args, W):
                           "fp32_iterations": split[0], "fp64_iterations": split[1], "converged": conv,
                           "F": F, "theta": theta,
                           "kernel_ms_profiled_run": fix_prof, "kernel_launches_profiled_run": fix_launches},
-        "e2e": {"value": round(V * iters_e2e * world / e2e_s, 1), "unit": METRIC, "seconds": round(e2e_s, 4),
+        "e2e": {"value": round(rp.throughput(V * iters_e2e, e2e_s), 1), "unit": METRIC, "seconds": round(e2e_s, 4),
                 "what": "lgf_load_links(pinned host) + lgf_fix(theta<tol) + lgf_store_links(pinned host)",
                 "parts": e2e_parts, "warmup_pass_parts": e2e_warm_parts,
                 "h2d_bytes_per_step": round(h2d / max(iters_e2e, 1), 1),
@@ -446,8 +474,7 @@ def run_ours(args, W):
         line["cpu_baseline"] = {"value": round(V * n / secs, 1), "unit": METRIC, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} iteration(s) of the numpy FP64 oracle on the same {dims} input "
                                           f"({secs:.1f} s, 1 thread)"}
-    if world > 1:
-        dist.destroy_process_group()
+    rp.close()
     return line
 
 
