@@ -213,24 +213,53 @@ __global__ void __launch_bounds__(kStageMats) k_store_aos(const cx<T>* __restric
 }
 
 // double-float links (36 hi planes, then 36 lo planes) -> AoS doubles, each
-// entry hi + lo exactly
+// entry hi + lo; with eta (not null: hi planes, then lo planes) the links
+// (1 + eta(x)) U (1 + eta(x+mu))^dag of the tail's gauge representation,
+// formed in double-float
 __global__ void __launch_bounds__(kStageMats) k_store_aos_df(const cx<float>* __restrict__ Uh,
                                                              const cx<float>* __restrict__ Ul,
-                                                             double* __restrict__ aos, int64_t V) {
+                                                             const cx<float>* __restrict__ eta, const Geom geo,
+                                                             double* __restrict__ aos) {
   __shared__ double sm[kStageMats * kStagePitch];
+  const int V = (int)geo.V;
   const int64_t first = (int64_t)blockIdx.x * kStageMats;
-  const int n = (int)(4 * V - first < kStageMats ? 4 * V - first : kStageMats);
+  const int n = (int)(4 * (int64_t)V - first < kStageMats ? 4 * (int64_t)V - first : kStageMats);
   if ((int)threadIdx.x < n) {
     const int64_t i = first + threadIdx.x;
-    const int64_t s = i >> 2;
+    const int s = (int)(i >> 2);
     const int mu = (int)(i & 3);
+    M3<float> uh;
+    cx<float> ul[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const int o = (mu * 9 + c) * V + s;
+      uh.e[c / 3][c % 3] = ldg(Uh + o);
+      ul[c] = ldg(Ul + o);
+    }
+    df re[9], im[9];
+    if (eta != nullptr) {
+      int x[4];
+      site_coords_i(geo.L, s, x);
+      const int cm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
+      const int Lm = mu == 0 ? geo.L[0] : mu == 1 ? geo.L[1] : mu == 2 ? geo.L[2] : geo.L[3];
+      const int st = mu == 0 ? 1 : mu == 1 ? geo.L[0] : mu == 2 ? geo.L[0] * geo.L[1] : geo.L[0] * geo.L[1] * geo.L[2];
+      const int sf = cm < Lm - 1 ? s + st : s - (Lm - 1) * st;
+      const cx<float>* el = eta + 9 * V;
+      const M3<float> xh = load_m3i<float, 9>(eta, V, s), xl = load_m3i<float, 9>(el, V, s);
+      const M3<float> fh = load_m3i<float, 9>(eta, V, sf), fl = load_m3i<float, 9>(el, V, sf);
+      tail_link_exact(uh, ul, xh, xl, fh, fl, re, im);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        re[c] = {uh.e[c / 3][c % 3].re, ul[c].re};
+        im[c] = {uh.e[c / 3][c % 3].im, ul[c].im};
+      }
+    }
     double* d = sm + threadIdx.x * kStagePitch;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      const int64_t o = ((int64_t)mu * 9 + c) * V + s;
-      const cx<float> h = ldg(Uh + o), l = ldg(Ul + o);
-      d[2 * c] = df_to_double(h.re, l.re);
-      d[2 * c + 1] = df_to_double(h.im, l.im);
+      d[2 * c] = df_to_double(re[c].h, re[c].l);
+      d[2 * c + 1] = df_to_double(im[c].h, im[c].l);
     }
   }
   __syncthreads();
@@ -411,9 +440,10 @@ cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, i
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_store_aos_df(const void* Udf, double* aos, int64_t V, cudaStream_t s) {
+cudaError_t launch_store_aos_df(const void* Udf, const void* eta, const Geom& geo, double* aos, cudaStream_t s) {
   auto h = static_cast<const cx<float>*>(Udf);
-  k_store_aos_df<<<blocks_for(4 * V, kStageMats), kStageMats, 0, s>>>(h, h + 36 * V, aos, V);
+  k_store_aos_df<<<blocks_for(4 * geo.V, kStageMats), kStageMats, 0, s>>>(h, h + 36 * geo.V,
+                                                                          static_cast<const cx<float>*>(eta), geo, aos);
   return cudaPeekAtLastError();
 }
 

@@ -30,10 +30,12 @@
 //   k_tail_start_df     U = g U_loaded g(x+mu)^dag from the FP64 input (split
 //                       exactly into hi + lo by bit manipulation) and that
 //                       g, products in double-float;
-//   k_gradient_tail_df  Delta by double-float sums, F summed in double-float
-//                       per warp, D stored as FP32;
-//   k_tail_update_df    eps from the accelerated gradient, U += the FP32
-//                       correction, a double-float addition;
+//   k_gradient_tail_eta Delta of the current links (1 + eta) U (1 + eta')^dag:
+//                       double-float sums of U plus the FP32 corrections,
+//                       F summed in double-float per warp, D stored as FP32;
+//   k_tail_eta_step     eps from the accelerated gradient, 1 + eta <-
+//                       (1 + eps)(1 + eta) at each site (the links of the
+//                       tail start are never rewritten);
 //   k_df_to_fp64        the links as FP64 planes, for the calls that need
 //                       them (exact conversions, one FP64 addition per
 //                       real); the links otherwise stay double-float, and
@@ -371,15 +373,33 @@ __device__ __forceinline__ void dacc_add(dacc& a, float vh, float vl) {
   a.l = __fadd_rn(a.l, __fadd_rn(vl, t.l));
 }
 
-// Delta and F/theta from double-float links; D stored as FP32.  Per
-// direction a thread first issues all 36 loads of its own and backward
-// links (hi and lo planes), then accumulates A = sum_mu U_mu(x-mu) - U_mu(x)
-// with compensated sums (one renormalisation per entry at the end).
-__global__ void __launch_bounds__(256, 2) k_gradient_tail_df(const cx<float>* __restrict__ Uh,
-                                                             const cx<float>* __restrict__ Ul,
-                                                             cx<float>* __restrict__ D, double2* __restrict__ partial,
-                                                             const Geom geo, DevState* st, int mode, double normF,
-                                                             double normT) {
+// ---------------------------------------------------------------------------
+// The tail in gauge representation.  The double-float links U of the tail
+// start stay fixed; the tail accumulates a gauge transformation 1 + eta(x)
+// close to the identity (eta FP32, |eta| ~ 1e-5), so that its current links
+// are
+//   U'_mu(x) = (1 + eta(x)) U_mu(x) (1 + eta(x+mu))^dag
+//            = U + eta U + U eta'^dag + eta U eta'^dag,
+// the correction (all terms) formed in FP32 from hi and added in double-float.
+// The update of the method, U' <- g U' g(x+mu)^dag with g = 1 + eps, becomes
+// 1 + eta <- (1 + eps)(1 + eta) at each site alone; no link is written.
+// The FP32 rounding of each correction (|eps| 2^-24 per step) is that of
+// the link-update form of the defect correction.
+// ---------------------------------------------------------------------------
+
+// a += v for an FP32 v, exactly (one two-sum)
+__device__ __forceinline__ void dacc_add_f(dacc& a, float v) { dacc_add(a, v, 0.f); }
+
+// Delta and F/theta of U'.  Backward links first: their double-float sum,
+// P = sum eta(x-mu) U_mu(x-mu) and T = sum (U + P terms), closed by one
+// product T eta(x)^dag; then the forward links: their sum, W = sum U eta'^dag
+// and T = sum (U + W terms), closed by eta(x) T.  Ten FP32 products per site.
+__global__ void __launch_bounds__(128, 3) k_gradient_tail_eta(const cx<float>* __restrict__ Uh,
+                                                              const cx<float>* __restrict__ Ul,
+                                                              const cx<float>* __restrict__ eta,
+                                                              cx<float>* __restrict__ D, double2* __restrict__ partial,
+                                                              const Geom geo, DevState* st, int mode, double normF,
+                                                              double normT) {
   pdl_wait();
   if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;
@@ -392,41 +412,104 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_df(const cx<float>* __
     dacc Ar[9], Ai[9], fs = dacc_zero();
 #pragma unroll
     for (int q = 0; q < 9; ++q) Ar[q] = Ai[q] = dacc_zero();
+    M3<float> Cc, T;  // the links' corrections; the pending factor of one product
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Cc.e[i][j] = T.e[i][j] = mk<float>(0.f, 0.f);
+    // backward links (1 + eta(x-mu)) U (1 + eta(x))^dag
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const int st_mu = (int)geo.stride[mu];
       const int sb = c[mu] > 0 ? s - st_mu : s + (geo.L[mu] - 1) * st_mu;
-      cx<float> oh[9], ol[9], bh[9], bl[9];
+      M3<float> ub, eb;
+      cx<float> ul[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const int o = (mu * 9 + q) * V;
-        oh[q] = ldg(Uh + o + s);
-        ol[q] = ldg(Ul + o + s);
-        bh[q] = ldg(Uh + o + sb);
-        bl[q] = ldg(Ul + o + sb);
+        const int o = (mu * 9 + q) * V + sb;
+        ub.e[q / 3][q % 3] = ldg(Uh + o);
+        ul[q] = ldg(Ul + o);
+        eb.e[q / 3][q % 3] = ldg(eta + q * V + sb);
       }
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        dacc_add(Ar[q], bh[q].re, bl[q].re);
-        dacc_add(Ar[q], -oh[q].re, -ol[q].re);
-        dacc_add(Ai[q], bh[q].im, bl[q].im);
-        dacc_add(Ai[q], -oh[q].im, -ol[q].im);
-        if (q == 0 || q == 4 || q == 8) dacc_add(fs, oh[q].re, ol[q].re);
+        dacc_add(Ar[q], ub.e[q / 3][q % 3].re, ul[q].re);
+        dacc_add(Ai[q], ub.e[q / 3][q % 3].im, ul[q].im);
       }
+      M3<float> y;
+      mm<float, 3>(y, eb, ub);  // eta(x-mu) U
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          Cc.e[i][j] = Cc.e[i][j] + y.e[i][j];
+          T.e[i][j] = T.e[i][j] + (ub.e[i][j] + y.e[i][j]);
+        }
+    }
+    {
+      const M3<float> ex = load_m3i<float, 9>(eta, V, s);
+      mm_dag_acc(Cc, T, ex);  // + sum (1 + eta(x-mu)) U eta(x)^dag
+    }
+    // forward links (1 + eta(x)) U (1 + eta(x+mu))^dag
+    float fc = 0.f;  // Re tr of their corrections
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) T.e[i][j] = mk<float>(0.f, 0.f);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int st_mu = (int)geo.stride[mu];
+      const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - (geo.L[mu] - 1) * st_mu;
+      M3<float> uf, ef;
+      cx<float> ul[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int o = (mu * 9 + q) * V + s;
+        uf.e[q / 3][q % 3] = ldg(Uh + o);
+        ul[q] = ldg(Ul + o);
+        ef.e[q / 3][q % 3] = ldg(eta + q * V + sf);
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        dacc_add(Ar[q], -uf.e[q / 3][q % 3].re, -ul[q].re);
+        dacc_add(Ai[q], -uf.e[q / 3][q % 3].im, -ul[q].im);
+        if (q == 0 || q == 4 || q == 8) dacc_add(fs, uf.e[q / 3][q % 3].re, ul[q].re);
+      }
+      M3<float> w;
+      mm_dag<float, 3>(w, uf, ef);  // U eta(x+mu)^dag
+      fc += w.e[0][0].re + w.e[1][1].re + w.e[2][2].re;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          Cc.e[i][j] = Cc.e[i][j] - w.e[i][j];
+          T.e[i][j] = T.e[i][j] + (uf.e[i][j] + w.e[i][j]);
+        }
+    }
+    {
+      const M3<float> ex = load_m3i<float, 9>(eta, V, s);
+      M3<float> m;
+      mm<float, 3>(m, ex, T);  // eta(x) sum U (1 + eta(x+mu))^dag
+      fc += m.e[0][0].re + m.e[1][1].re + m.e[2][2].re;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Cc.e[i][j] = Cc.e[i][j] - m.e[i][j];
     }
     df A_re[9], A_im[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
+      dacc_add_f(Ar[q], Cc.e[q / 3][q % 3].re);
+      dacc_add_f(Ai[q], Cc.e[q / 3][q % 3].im);
       A_re[q] = dacc_result(Ar[q]);
       A_im[q] = dacc_result(Ai[q]);
     }
+    dacc_add_f(fs, fc);
     fsum = dacc_result(fs);
     // Delta = A - A^dag - trace: off-diagonal pairs and imaginary diagonal
     const df r01 = df_add(A_re[1], df_neg(A_re[3])), i01 = df_add(A_im[1], A_im[3]);
     const df r02 = df_add(A_re[2], df_neg(A_re[6])), i02 = df_add(A_im[2], A_im[6]);
     const df r12 = df_add(A_re[5], df_neg(A_re[7])), i12 = df_add(A_im[5], A_im[7]);
-    // traceless imaginary diagonal: Im Tr A need not be small, so the
-    // cancellation 2 a_k - a_l - a_m happens in double-float, before rounding
     const df a0 = A_im[0], a1 = A_im[4], a2 = A_im[8];
     const df n0 = df_add(df_add({2.f * a0.h, 2.f * a0.l}, df_neg(a1)), df_neg(a2));
     const df n1 = df_add(df_add({2.f * a1.h, 2.f * a1.l}, df_neg(a0)), df_neg(a2));
@@ -440,7 +523,6 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_df(const cx<float>* __
     D[3 * V + s] = mk<float>(i0, i1);
     tsum = 2.f * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
   }
-  // warp sums: F in double-float, theta in FP32; FP64 above the warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const df other = {__shfl_down_sync(0xffffffffu, fsum.h, o), __shfl_down_sync(0xffffffffu, fsum.l, o)};
@@ -451,16 +533,64 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_df(const cx<float>* __
   grid_reduce_warp_totals(wf, (double)tsum, partial, st, normF, normT, mode);
 }
 
-// U_mu(x) += eps(x) U + U eps(x+mu)^dag + eps(x) U eps(x+mu)^dag with
-// eps = X + X^2/2 formed here from the packed accelerated gradient (no eps
-// array): the correction in FP32 from hi, added in double-float.  A block is
-// 32 consecutive sites x the 4 directions, one warp per direction; each
-// thread issues all its loads (two packed gradients, hi and lo links) first.
-__global__ void __launch_bounds__(128, 4) k_tail_update_df(cx<float>* __restrict__ Uh, cx<float>* __restrict__ Ul,
-                                                           const cx<float>* __restrict__ D, float h, const Geom geo,
-                                                           const DevState* __restrict__ st) {
+// 1 + eta <- (1 + eps)(1 + eta), eps = X + X^2/2, eta in double-float (hi
+// planes, then lo planes): eta <- eta + X + (X^2/2 + eps eta_hi).  X, exactly
+// anti-Hermitian, enters by exact two-sums; only the small Hermitian terms
+// (|X|^2 ~ 1e-10) are rounded in FP32.  So 1 + eta stays unitary to O(|X|^3)
+// plus ~1e-17, where rounding X + X^2/2 as one FP32 sum would break unitarity
+// by 2^-24 |X| at every step.
+__global__ void __launch_bounds__(256) k_tail_eta_step(const cx<float>* __restrict__ D, cx<float>* eh,
+                                                       cx<float>* el, int V, float h,
+                                                       const DevState* __restrict__ st) {
   pdl_wait();
   if (st != nullptr && st->done) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const cx<float> c0 = ldg(D + s), c1 = ldg(D + V + s), c2 = ldg(D + 2 * V + s), c3 = ldg(D + 3 * V + s);
+  M3<float> X;
+  X.e[0][0] = mk<float>(0.f, h * c3.re);
+  X.e[1][1] = mk<float>(0.f, h * c3.im);
+  X.e[2][2] = mk<float>(0.f, -h * (c3.re + c3.im));
+  X.e[0][1] = scale(c0, h);
+  X.e[0][2] = scale(c1, h);
+  X.e[1][2] = scale(c2, h);
+  X.e[1][0] = mk<float>(-h * c0.re, h * c0.im);
+  X.e[2][0] = mk<float>(-h * c1.re, h * c1.im);
+  X.e[2][1] = mk<float>(-h * c2.re, h * c2.im);
+  M3<float> n;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) n.e[q / 3][q % 3] = eh[q * V + s];
+  // small terms: X^2/2 + (X + X^2/2) eta_hi
+  M3<float> Y;
+  mm<float, 3>(Y, X, X);
+  M3<float> e = X;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Y.e[i][j] = scale(Y.e[i][j], 0.5f);
+      e.e[i][j] = e.e[i][j] + Y.e[i][j];
+    }
+  mm_acc(Y, e, n);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const int i = q / 3, j = q % 3;
+    const cx<float> lo = el[q * V + s];
+    df re = two_sum(n.e[i][j].re, X.e[i][j].re);
+    df im = two_sum(n.e[i][j].im, X.e[i][j].im);
+    re = fast_two_sum(re.h, __fadd_rn(re.l, __fadd_rn(lo.re, Y.e[i][j].re)));
+    im = fast_two_sum(im.h, __fadd_rn(im.l, __fadd_rn(lo.im, Y.e[i][j].im)));
+    eh[q * V + s] = mk<float>(re.h, im.h);
+    el[q * V + s] = mk<float>(re.l, im.l);
+  }
+}
+
+// U <- U' (the caller then clears eta): one thread per (site, direction), a
+// block 32 sites x 4 directions
+__global__ void __launch_bounds__(128) k_tail_apply_eta(cx<float>* __restrict__ Uh, cx<float>* __restrict__ Ul,
+                                                        const cx<float>* __restrict__ eh,
+                                                        const cx<float>* __restrict__ el, const Geom geo) {
+  pdl_wait();
   const int V = (int)geo.V;
   const int mu = threadIdx.x >> 5;
   const int s = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -471,8 +601,8 @@ __global__ void __launch_bounds__(128, 4) k_tail_update_df(cx<float>* __restrict
   const int Lm = mu == 0 ? geo.L[0] : mu == 1 ? geo.L[1] : mu == 2 ? geo.L[2] : geo.L[3];
   const int st_mu = mu == 0 ? 1 : mu == 1 ? geo.L[0] : mu == 2 ? geo.L[0] * geo.L[1] : geo.L[0] * geo.L[1] * geo.L[2];
   const int sf = cm < Lm - 1 ? s + st_mu : s - (Lm - 1) * st_mu;
-  const cx<float> x0 = ldg(D + s), x1 = ldg(D + V + s), x2 = ldg(D + 2 * V + s), x3 = ldg(D + 3 * V + s);
-  const cx<float> f0 = ldg(D + sf), f1 = ldg(D + V + sf), f2 = ldg(D + 2 * V + sf), f3 = ldg(D + 3 * V + sf);
+  const M3<float> xh = load_m3i<float, 9>(eh, V, s), xl = load_m3i<float, 9>(el, V, s);
+  const M3<float> fh = load_m3i<float, 9>(eh, V, sf), fl = load_m3i<float, 9>(el, V, sf);
   M3<float> uh;
   cx<float> ul[9];
 #pragma unroll
@@ -481,24 +611,13 @@ __global__ void __launch_bounds__(128, 4) k_tail_update_df(cx<float>* __restrict
     uh.e[q / 3][q % 3] = Uh[o];
     ul[q] = Ul[o];
   }
-  M3<float> a, d;
-  {
-    const M3<float> ex = tail_eps(x0, x1, x2, x3, h);
-    mm<float, 3>(a, ex, uh);  // eps U
-  }
-  {
-    const M3<float> ef = tail_eps(f0, f1, f2, f3, h);
-    mm_dag<float, 3>(d, uh, ef);  // U eps'^dag
-    mm_dag_acc(d, a, ef);         // + eps U eps'^dag
-  }
+  df re[9], im[9];
+  tail_link_exact(uh, ul, xh, xl, fh, fl, re, im);
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     const int o = (mu * 9 + q) * V + s;
-    const cx<float> delta = a.e[q / 3][q % 3] + d.e[q / 3][q % 3];
-    const df re = df_add_f({uh.e[q / 3][q % 3].re, ul[q].re}, delta.re);
-    const df im = df_add_f({uh.e[q / 3][q % 3].im, ul[q].im}, delta.im);
-    Uh[o] = mk<float>(re.h, im.h);
-    Ul[o] = mk<float>(re.l, im.l);
+    Uh[o] = mk<float>(re[q].h, im[q].h);
+    Ul[o] = mk<float>(re[q].l, im[q].l);
   }
 }
 
@@ -528,21 +647,31 @@ cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf,
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_gradient_tail_df(const void* Udf, void* D32, double2* partial, const Geom& geo, DevState* st,
-                                    int mode, cudaStream_t s) {
+cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, void* D32, double2* partial, const Geom& geo,
+                                     DevState* st, int mode, cudaStream_t s) {
   auto h = static_cast<const cx<float>*>(Udf);
-  const unsigned nb = (unsigned)((geo.V + 255) / 256);
-  launch_pdl(k_gradient_tail_df, nb, 256, 0, s, h, h + 36 * geo.V, static_cast<cx<float>*>(D32), partial, geo, st,
-             mode, 1.0 / (12.0 * (double)geo.V), 1.0 / (3.0 * (double)geo.V));
+  const unsigned nb = (unsigned)((geo.V + 127) / 128);
+  launch_pdl(k_gradient_tail_eta, nb, 128, 0, s, h, h + 36 * geo.V, static_cast<const cx<float>*>(eta),
+             static_cast<cx<float>*>(D32), partial, geo, st, mode, 1.0 / (12.0 * (double)geo.V),
+             1.0 / (3.0 * (double)geo.V));
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_tail_update_df(void* Udf, const void* D32, double half_alpha, const Geom& geo,
-                                  const DevState* st, cudaStream_t s) {
-  auto h = static_cast<cx<float>*>(Udf);
-  launch_pdl(k_tail_update_df, (unsigned)((geo.V + 31) / 32), 128, 0, s, h, h + 36 * geo.V,
-             static_cast<const cx<float>*>(D32), (float)half_alpha, geo, st);
+cudaError_t launch_tail_eta_step(const void* D32, void* eta, int64_t V, double half_alpha, const DevState* st,
+                                 cudaStream_t s) {
+  auto e = static_cast<cx<float>*>(eta);
+  launch_pdl(k_tail_eta_step, (unsigned)((V + 255) / 256), 256, 0, s, static_cast<const cx<float>*>(D32), e,
+             e + 9 * V, (int)V, (float)half_alpha, st);
   return cudaPeekAtLastError();
+}
+
+cudaError_t launch_tail_apply_eta(void* Udf, void* eta, const Geom& geo, cudaStream_t s) {
+  auto h = static_cast<cx<float>*>(Udf);
+  auto e = static_cast<const cx<float>*>(eta);
+  launch_pdl(k_tail_apply_eta, (unsigned)((geo.V + 31) / 32), 128, 0, s, h, h + 36 * geo.V, e, e + 9 * geo.V, geo);
+  cudaError_t err = cudaPeekAtLastError();
+  if (err != cudaSuccess) return err;
+  return cudaMemsetAsync(eta, 0, (size_t)18 * geo.V * sizeof(cx<float>), s);
 }
 
 cudaError_t launch_df_to_fp64(const void* Udf, void* U64, int64_t V, cudaStream_t s) {

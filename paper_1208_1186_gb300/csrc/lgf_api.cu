@@ -83,6 +83,7 @@ struct lgf_ctx {
   bool defect = false;        // the FP64 engine runs the defect-correction tail
   bool df = false;            // ... on the double-float links in Udf (converted back at the end)
   void* Udf = nullptr;        // tail links in double-float: 36 V complex hi, then 36 V complex lo
+  void* eta = nullptr;        // the tail's gauge transformation 1 + eta: 9 V complex hi, then 9 V lo
 
   Geom geo{};
   Engine e64, e32;
@@ -359,11 +360,13 @@ int queue_tail_start(lgf_handle h) {
   if (h->df) {
     if (!h->Udf) {
       h->Udf = dev_alloc(h, (size_t)2 * 36 * V * sizeof(float) * 2);
-      if (!h->Udf) return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail links failed");
+      h->eta = dev_alloc(h, (size_t)18 * V * sizeof(float) * 2);
+      if (!h->Udf || !h->eta) return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail failed");
     }
     // e64.g (9 FP64 complex planes) holds Gh and Gl (2 x 9 FP32 complex planes)
     LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_df(h->G, h->e64.g, V, h->stream));
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_start_df(h->Uorig, h->e64.g, h->Udf, h->geo, h->stream));
+    LGF_CUDA(h, cudaMemsetAsync(h->eta, 0, (size_t)18 * V * sizeof(float) * 2, h->stream));
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
     LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
@@ -373,12 +376,14 @@ int queue_tail_start(lgf_handle h) {
   return LGF_OK;
 }
 
-// After a double-float tail the handle's links stay in double-float form
-// (h->df): later fixes and iterations continue on them, lgf_functional takes
-// the double-float gradient and lgf_store_links writes FP64 from hi + lo.
-// Calls that need the links as FP64 planes convert them here first.
+// After a double-float tail the handle's links stay in that form, U' = (1 +
+// eta) Udf (1 + eta(x+mu))^dag (h->df): later fixes and iterations continue
+// on them, lgf_functional takes their gradient and lgf_store_links writes
+// FP64 from them directly.  Calls that need the links as FP64 planes apply
+// eta to Udf and convert here first.
 int materialize_df(lgf_handle h) {
   if (!h->df || h->cur != &h->e64) return LGF_OK;
+  LGF_LAUNCH(h, LGF_K_OTHER, launch_tail_apply_eta(h->Udf, h->eta, h->geo, h->stream));
   LGF_LAUNCH(h, LGF_K_OTHER, launch_df_to_fp64(h->Udf, h->e64.U, h->V, h->stream));
   h->df = false;
   return LGF_OK;
@@ -388,7 +393,7 @@ int materialize_df(lgf_handle h) {
 int queue_gradient(lgf_handle h, Engine& e, int mode) {
   if (&e == &h->e64 && h->df)
     LGF_LAUNCH(h, LGF_K_GRADIENT,
-               launch_gradient_tail_df(h->Udf, h->e32.D, h->partial, h->geo, h->st, mode, h->stream));
+               launch_gradient_tail_eta(h->Udf, h->eta, h->e32.D, h->partial, h->geo, h->st, mode, h->stream));
   else if (e.grep)
     LGF_LAUNCH(h, LGF_K_GRADIENT,
                launch_gradient_grep(e.nc, e.U, h->G, e.D, h->partial, h->geo, h->st, mode, h->stream));
@@ -405,12 +410,14 @@ int queue_gradient(lgf_handle h, Engine& e, int mode) {
 int queue_iteration(lgf_handle h, Engine& e) {
   cudaStream_t s = h->stream;
   if (h->defect && h->df && &e == &h->e64) {
-    // defect-correction tail on double-float links; FP32 acceleration and step
+    // defect-correction tail on the double-float links of the tail start in
+    // gauge representation; FP32 acceleration and step on eta
     Engine& f = h->e32;
-    LGF_LAUNCH(h, LGF_K_GRADIENT, launch_gradient_tail_df(h->Udf, f.D, h->partial, h->geo, h->st, 1, s));
+    LGF_LAUNCH(h, LGF_K_GRADIENT,
+               launch_gradient_tail_eta(h->Udf, h->eta, f.D, h->partial, h->geo, h->st, 1, s));
     int rc = queue_accelerate(h, f, h->st);
     if (rc) return rc;
-    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_update_df(h->Udf, f.D, 0.5 * h->alpha, h->geo, h->st, s));
+    LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_eta_step(f.D, h->eta, h->V, 0.5 * h->alpha, h->st, s));
     return LGF_OK;
   }
   if (h->defect && &e == &h->e64) {
@@ -1233,7 +1240,7 @@ int lgf_store_links(lgf_handle h, double* host_aos) {
   double* dst = direct ? direct : h->staging;
   Engine& e = *h->cur;
   if (&e == &h->e64 && h->df)
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos_df(h->Udf, dst, h->V, h->stream));
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos_df(h->Udf, h->eta, h->geo, dst, h->stream));
   else if (e.grep)
     LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, dst, h->geo, h->stream));
   else

@@ -157,4 +157,58 @@ __device__ __forceinline__ double df_to_double(float h, float l) {
   return fp32_to_fp64_bits(h) + fp32_to_fp64_bits(l);
 }
 
+// One link of U' = (1 + eta) U (1 + eta')^dag in double-float, accurate to
+// ~2^-48: U and eta = eta(x), eta' = eta(x+mu) in double-float, the first-order
+// terms eta U + U eta'^dag by compensated dot products of exact products
+// (their hi x lo parts in the low parts), the second-order eta U eta'^dag
+// (~1e-10) in FP32.  For the host store and the conversion to FP64 planes.
+__device__ __forceinline__ void tail_link_exact(const M3<float>& uh, const cx<float> (&ul)[9], const M3<float>& xh,
+                                                const M3<float>& xl, const M3<float>& fh, const M3<float>& fl,
+                                                df (&re)[9], df (&im)[9]) {
+  M3<float> a, t2;
+  mm<float, 3>(a, xh, uh);
+  mm_dag<float, 3>(t2, a, fh);  // eta U eta'^dag
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dacc r = {uh.e[i][j].re, ul[i * 3 + j].re}, m = {uh.e[i][j].im, ul[i * 3 + j].im};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // (eta U)_ij += eta_ik U_kj
+        const cx<float> x = xh.e[i][k], y = uh.e[k][j], xe = xl.e[i][k], ye = ul[k * 3 + j];
+        dacc_prod(r, x.re, y.re);
+        dacc_prod(r, -x.im, y.im);
+        dacc_prod(m, x.re, y.im);
+        dacc_prod(m, x.im, y.re);
+        dacc_lo(r, xe.re, y.re);
+        dacc_lo(r, -xe.im, y.im);
+        dacc_lo(r, x.re, ye.re);
+        dacc_lo(r, -x.im, ye.im);
+        dacc_lo(m, xe.re, y.im);
+        dacc_lo(m, xe.im, y.re);
+        dacc_lo(m, x.re, ye.im);
+        dacc_lo(m, x.im, ye.re);
+        // (U eta'^dag)_ij += U_ik conj(eta'_jk)
+        const cx<float> u = uh.e[i][k], f = fh.e[j][k], ue = ul[i * 3 + k], fe = fl.e[j][k];
+        dacc_prod(r, u.re, f.re);
+        dacc_prod(r, u.im, f.im);
+        dacc_prod(m, u.im, f.re);
+        dacc_prod(m, -u.re, f.im);
+        dacc_lo(r, ue.re, f.re);
+        dacc_lo(r, ue.im, f.im);
+        dacc_lo(r, u.re, fe.re);
+        dacc_lo(r, u.im, fe.im);
+        dacc_lo(m, ue.im, f.re);
+        dacc_lo(m, -ue.re, f.im);
+        dacc_lo(m, u.im, fe.re);
+        dacc_lo(m, -u.re, fe.im);
+      }
+      r.l = __fadd_rn(r.l, t2.e[i][j].re);
+      m.l = __fadd_rn(m.l, t2.e[i][j].im);
+      re[i * 3 + j] = dacc_result(r);
+      im[i * 3 + j] = dacc_result(m);
+    }
+}
+
 }  // namespace lgf

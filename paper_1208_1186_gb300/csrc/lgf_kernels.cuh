@@ -88,8 +88,9 @@ cudaError_t launch_soa_to_aos(int prec, int nc, const void* U, double* aos, int6
 // G <- reunitarised g G (storage precision); FP64 reunitarised copy of G
 cudaError_t launch_accumulate(int prec, int nc, void* G, const void* g, int64_t V, const DevState* st,
                               cudaStream_t s);
-// double-float links (hi planes, then lo planes) -> AoS doubles (host or device)
-cudaError_t launch_store_aos_df(const void* Udf, double* aos, int64_t V, cudaStream_t s);
+// double-float links (hi planes, then lo planes) -> AoS doubles (host or device); with eta (not
+// null) the tail's links (1 + eta) Udf (1 + eta(x+mu))^dag
+cudaError_t launch_store_aos_df(const void* Udf, const void* eta, const Geom& geo, double* aos, cudaStream_t s);
 cudaError_t launch_promote_gauge(int prec, int nc, const void* G, void* out64, int64_t V, cudaStream_t s);
 // G <- 1 at every site
 cudaError_t launch_set_identity(int prec, int nc, void* G, int64_t V, cudaStream_t s);
@@ -137,11 +138,15 @@ cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* ao
 cudaError_t launch_promote_df(const void* G32, void* g_df, int64_t V, cudaStream_t s);
 // Udf = Gh+Gl U_loaded (Gh+Gl)(x+mu)^dag in double-float (hi planes, then lo planes)
 cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf, const Geom& geo, cudaStream_t s);
-cudaError_t launch_gradient_tail_df(const void* Udf, void* D32, double2* partial, const Geom& geo, DevState* st,
-                                    int mode, cudaStream_t s);
-// Udf += (1 + eps) Udf (1 + eps(x+mu))^dag - Udf, eps = X + X^2/2 with X = half_alpha Delta~ from D32
-cudaError_t launch_tail_update_df(void* Udf, const void* D32, double half_alpha, const Geom& geo,
-                                  const DevState* st, cudaStream_t s);
+// the tail in gauge representation: links (1 + eta) Udf (1 + eta(x+mu))^dag, eta in double-float
+// (9 complex hi planes, then 9 lo planes; the gradient reads the hi planes)
+cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, void* D32, double2* partial, const Geom& geo,
+                                     DevState* st, int mode, cudaStream_t s);
+// eta <- (1 + eps)(1 + eta) - 1, eps = X + X^2/2 with X = half_alpha Delta~ from D32
+cudaError_t launch_tail_eta_step(const void* D32, void* eta, int64_t V, double half_alpha, const DevState* st,
+                                 cudaStream_t s);
+// Udf <- (1 + eta) Udf (1 + eta(x+mu))^dag, then eta <- 0
+cudaError_t launch_tail_apply_eta(void* Udf, void* eta, const Geom& geo, cudaStream_t s);
 cudaError_t launch_df_to_fp64(const void* Udf, void* U64, int64_t V, cudaStream_t s);
 // FP64 tail by defect correction (k_tail.cu): FP64 links, FP32 FFT and step
 cudaError_t launch_gradient_tail(const void* U64, void* D32, double2* partial, const Geom& geo, DevState* st,

@@ -340,6 +340,32 @@ def test_double_float_tail_start_matches_the_fp64_one(lgf, dims, dtype):
     assert O.unitarity_defect(out[2]) < 5e-14
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f32_r12"])
+def test_tail_links_read_the_same_before_and_after_conversion(lgf, dtype):
+    """After the double-float tail the handle holds its links as the tail
+    start's double-float links and the tail's gauge transformation 1 + eta.
+    lgf_store_links and lgf_functional form them on the fly; lgf_probe first
+    applies eta and converts them to FP64 planes.  Both readings agree to
+    FP64 rounding, and a later fix continues from either."""
+    dims = (8, 8, 8, 8)
+    U = I.synthetic_config(dims, seed=4, link_scale=0.5)
+    with lgf.GaugeFixer(dims, dtype) as gf:
+        gf.load_links(U)
+        it, conv = gf.fix(1e-15, 2000)
+        assert conv and gf.fix_split()[1] > 0
+        F1, th1 = gf.functional()
+        out1 = gf.store_links()
+        gf.probe()
+        F2, th2 = gf.functional()
+        out2 = gf.store_links()
+        it2, conv2 = gf.fix(1e-15, 2000)
+    assert np.max(np.abs(out1 - out2)) < 1e-14
+    assert F2 == pytest.approx(F1, rel=1e-14)
+    assert th1 < 1e-15 and th2 < 1e-15 and abs(th1 - th2) < 1e-18
+    assert conv2 and it2 == 0
+    assert O.functional(out1)[1] < 1e-15
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_device_loop_and_host_loop_stop_at_the_same_update(lgf, mode):
     """lgf_fix runs each phase as a device-side graph loop, or (under
