@@ -390,13 +390,79 @@ __device__ __forceinline__ void dacc_add(dacc& a, float vh, float vl) {
 // a += v for an FP32 v, exactly (one two-sum)
 __device__ __forceinline__ void dacc_add_f(dacc& a, float v) { dacc_add(a, v, 0.f); }
 
-// Delta and F/theta of U'.  Backward links first: their double-float sum,
-// P = sum eta(x-mu) U_mu(x-mu) and T = sum (U + P terms), closed by one
-// product T eta(x)^dag; then the forward links: their sum, W = sum U eta'^dag
-// and T = sum (U + W terms), closed by eta(x) T.  Ten FP32 products per site.
-__global__ void __launch_bounds__(128, 3) k_gradient_tail_eta(const cx<float>* __restrict__ Uh,
-                                                              const cx<float>* __restrict__ Ul,
+// The fixed part of the tail's gradient.  Delta is linear in A = sum_mu
+// U'_mu(x-mu) - U'_mu(x), and U' = U + (small corrections), so Delta(U') =
+// Delta(U) + Delta(corrections) with Delta(U) fixed for the whole tail.
+// This kernel forms Delta(U) (~1e-6 after the FP32 phase) by double-float
+// sums and stores it packed in FP32 (error ~2^-24 1e-6, below the FP32
+// rounding of the corrections), and each site's F term sum_mu Re tr U_mu(x)
+// in double-float.  Once per tail start.
+__global__ void __launch_bounds__(256, 2) k_tail_base(const cx<float>* __restrict__ Uh, const cx<float>* __restrict__ Ul,
+                                                      cx<float>* __restrict__ D0, float2* __restrict__ F0,
+                                                      const Geom geo) {
+  pdl_wait();
+  const int V = (int)geo.V;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  int c[4];
+  site_coords_i(geo.L, s, c);
+  dacc Ar[9], Ai[9], fs = dacc_zero();
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Ar[q] = Ai[q] = dacc_zero();
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int st_mu = (int)geo.stride[mu];
+    const int sb = c[mu] > 0 ? s - st_mu : s + (geo.L[mu] - 1) * st_mu;
+    cx<float> oh[9], ol[9], bh[9], bl[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const int o = (mu * 9 + q) * V;
+      oh[q] = ldg(Uh + o + s);
+      ol[q] = ldg(Ul + o + s);
+      bh[q] = ldg(Uh + o + sb);
+      bl[q] = ldg(Ul + o + sb);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      dacc_add(Ar[q], bh[q].re, bl[q].re);
+      dacc_add(Ar[q], -oh[q].re, -ol[q].re);
+      dacc_add(Ai[q], bh[q].im, bl[q].im);
+      dacc_add(Ai[q], -oh[q].im, -ol[q].im);
+      if (q == 0 || q == 4 || q == 8) dacc_add(fs, oh[q].re, ol[q].re);
+    }
+  }
+  df A_re[9], A_im[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    A_re[q] = dacc_result(Ar[q]);
+    A_im[q] = dacc_result(Ai[q]);
+  }
+  // Delta = A - A^dag - trace: off-diagonal pairs and imaginary diagonal
+  const df r01 = df_add(A_re[1], df_neg(A_re[3])), i01 = df_add(A_im[1], A_im[3]);
+  const df r02 = df_add(A_re[2], df_neg(A_re[6])), i02 = df_add(A_im[2], A_im[6]);
+  const df r12 = df_add(A_re[5], df_neg(A_re[7])), i12 = df_add(A_im[5], A_im[7]);
+  // traceless imaginary diagonal: Im Tr A need not be small, so the
+  // cancellation 2 a_k - a_l - a_m happens in double-float, before rounding
+  const df a0 = A_im[0], a1 = A_im[4], a2 = A_im[8];
+  const df n0 = df_add(df_add({2.f * a0.h, 2.f * a0.l}, df_neg(a1)), df_neg(a2));
+  const df n1 = df_add(df_add({2.f * a1.h, 2.f * a1.l}, df_neg(a0)), df_neg(a2));
+  D0[s] = mk<float>(r01.h + r01.l, i01.h + i01.l);
+  D0[V + s] = mk<float>(r02.h + r02.l, i02.h + i02.l);
+  D0[2 * V + s] = mk<float>(r12.h + r12.l, i12.h + i12.l);
+  D0[3 * V + s] = mk<float>(2.f * (n0.h + n0.l) / 3.f, 2.f * (n1.h + n1.l) / 3.f);
+  const df f = dacc_result(fs);
+  F0[s] = make_float2(f.h, f.l);
+}
+
+// Delta and F/theta of U' = U + corrections: the fixed part from k_tail_base,
+// the corrections from the FP32 hi links and eta (hi).  Backward links
+// first: P = sum eta(x-mu) U_mu(x-mu) and T = sum (U + P terms), closed by
+// one product T eta(x)^dag; then the forward links: W = sum U eta'^dag and
+// T = sum (U + W terms), closed by eta(x) T.  Ten FP32 products per site.
+__global__ void __launch_bounds__(256, 2) k_gradient_tail_eta(const cx<float>* __restrict__ Uh,
                                                               const cx<float>* __restrict__ eta,
+                                                              const cx<float>* __restrict__ D0,
+                                                              const float2* __restrict__ F0,
                                                               cx<float>* __restrict__ D, double2* __restrict__ partial,
                                                               const Geom geo, DevState* st, int mode, double normF,
                                                               double normT) {
@@ -409,9 +475,6 @@ __global__ void __launch_bounds__(128, 3) k_gradient_tail_eta(const cx<float>* _
   if (s < V) {
     int c[4];
     site_coords_i(geo.L, s, c);
-    dacc Ar[9], Ai[9], fs = dacc_zero();
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Ar[q] = Ai[q] = dacc_zero();
     M3<float> Cc, T;  // the links' corrections; the pending factor of one product
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -423,18 +486,10 @@ __global__ void __launch_bounds__(128, 3) k_gradient_tail_eta(const cx<float>* _
       const int st_mu = (int)geo.stride[mu];
       const int sb = c[mu] > 0 ? s - st_mu : s + (geo.L[mu] - 1) * st_mu;
       M3<float> ub, eb;
-      cx<float> ul[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const int o = (mu * 9 + q) * V + sb;
-        ub.e[q / 3][q % 3] = ldg(Uh + o);
-        ul[q] = ldg(Ul + o);
+        ub.e[q / 3][q % 3] = ldg(Uh + (mu * 9 + q) * V + sb);
         eb.e[q / 3][q % 3] = ldg(eta + q * V + sb);
-      }
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        dacc_add(Ar[q], ub.e[q / 3][q % 3].re, ul[q].re);
-        dacc_add(Ai[q], ub.e[q / 3][q % 3].im, ul[q].im);
       }
       M3<float> y;
       mm<float, 3>(y, eb, ub);  // eta(x-mu) U
@@ -461,19 +516,10 @@ __global__ void __launch_bounds__(128, 3) k_gradient_tail_eta(const cx<float>* _
       const int st_mu = (int)geo.stride[mu];
       const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - (geo.L[mu] - 1) * st_mu;
       M3<float> uf, ef;
-      cx<float> ul[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const int o = (mu * 9 + q) * V + s;
-        uf.e[q / 3][q % 3] = ldg(Uh + o);
-        ul[q] = ldg(Ul + o);
+        uf.e[q / 3][q % 3] = ldg(Uh + (mu * 9 + q) * V + s);
         ef.e[q / 3][q % 3] = ldg(eta + q * V + sf);
-      }
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        dacc_add(Ar[q], -uf.e[q / 3][q % 3].re, -ul[q].re);
-        dacc_add(Ai[q], -uf.e[q / 3][q % 3].im, -ul[q].im);
-        if (q == 0 || q == 4 || q == 8) dacc_add(fs, uf.e[q / 3][q % 3].re, ul[q].re);
       }
       M3<float> w;
       mm_dag<float, 3>(w, uf, ef);  // U eta(x+mu)^dag
@@ -496,32 +542,23 @@ __global__ void __launch_bounds__(128, 3) k_gradient_tail_eta(const cx<float>* _
 #pragma unroll
         for (int j = 0; j < 3; ++j) Cc.e[i][j] = Cc.e[i][j] - m.e[i][j];
     }
-    df A_re[9], A_im[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      dacc_add_f(Ar[q], Cc.e[q / 3][q % 3].re);
-      dacc_add_f(Ai[q], Cc.e[q / 3][q % 3].im);
-      A_re[q] = dacc_result(Ar[q]);
-      A_im[q] = dacc_result(Ai[q]);
-    }
-    dacc_add_f(fs, fc);
-    fsum = dacc_result(fs);
-    // Delta = A - A^dag - trace: off-diagonal pairs and imaginary diagonal
-    const df r01 = df_add(A_re[1], df_neg(A_re[3])), i01 = df_add(A_im[1], A_im[3]);
-    const df r02 = df_add(A_re[2], df_neg(A_re[6])), i02 = df_add(A_im[2], A_im[6]);
-    const df r12 = df_add(A_re[5], df_neg(A_re[7])), i12 = df_add(A_im[5], A_im[7]);
-    const df a0 = A_im[0], a1 = A_im[4], a2 = A_im[8];
-    const df n0 = df_add(df_add({2.f * a0.h, 2.f * a0.l}, df_neg(a1)), df_neg(a2));
-    const df n1 = df_add(df_add({2.f * a1.h, 2.f * a1.l}, df_neg(a0)), df_neg(a2));
-    const float i0 = 2.f * (n0.h + n0.l) / 3.f, i1 = 2.f * (n1.h + n1.l) / 3.f, i2 = -(i0 + i1);
-    const cx<float> d01 = mk<float>(r01.h + r01.l, i01.h + i01.l);
-    const cx<float> d02 = mk<float>(r02.h + r02.l, i02.h + i02.l);
-    const cx<float> d12 = mk<float>(r12.h + r12.l, i12.h + i12.l);
+    // Delta = Delta(U) + Delta(corrections)
+    const cx<float> b01 = ldg(D0 + s), b02 = ldg(D0 + V + s), b12 = ldg(D0 + 2 * V + s), bd = ldg(D0 + 3 * V + s);
+    const cx<float> d01 = b01 + (Cc.e[0][1] - conj(Cc.e[1][0]));
+    const cx<float> d02 = b02 + (Cc.e[0][2] - conj(Cc.e[2][0]));
+    const cx<float> d12 = b12 + (Cc.e[1][2] - conj(Cc.e[2][1]));
+    const float c0 = 2.f * Cc.e[0][0].im, c1 = 2.f * Cc.e[1][1].im, c2 = 2.f * Cc.e[2][2].im;
+    const float ctr = (c0 + c1 + c2) / 3.f;
+    const float i0 = bd.re + (c0 - ctr), i1 = bd.im + (c1 - ctr), i2 = -(i0 + i1);
     D[s] = d01;
     D[V + s] = d02;
     D[2 * V + s] = d12;
     D[3 * V + s] = mk<float>(i0, i1);
     tsum = 2.f * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
+    const float2 f0 = __ldg(F0 + s);
+    dacc fs = {f0.x, f0.y};
+    dacc_add_f(fs, fc);
+    fsum = dacc_result(fs);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -647,11 +684,19 @@ cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf,
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, void* D32, double2* partial, const Geom& geo,
-                                     DevState* st, int mode, cudaStream_t s) {
+cudaError_t launch_tail_base(const void* Udf, void* base, const Geom& geo, cudaStream_t s) {
   auto h = static_cast<const cx<float>*>(Udf);
-  const unsigned nb = (unsigned)((geo.V + 127) / 128);
-  launch_pdl(k_gradient_tail_eta, nb, 128, 0, s, h, h + 36 * geo.V, static_cast<const cx<float>*>(eta),
+  auto D0 = static_cast<cx<float>*>(base);
+  launch_pdl(k_tail_base, (unsigned)((geo.V + 255) / 256), 256, 0, s, h, h + 36 * geo.V, D0,
+             reinterpret_cast<float2*>(D0 + 4 * geo.V), geo);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, const void* base, void* D32,
+                                     double2* partial, const Geom& geo, DevState* st, int mode, cudaStream_t s) {
+  auto D0 = static_cast<const cx<float>*>(base);
+  launch_pdl(k_gradient_tail_eta, (unsigned)((geo.V + 255) / 256), 256, 0, s, static_cast<const cx<float>*>(Udf),
+             static_cast<const cx<float>*>(eta), D0, reinterpret_cast<const float2*>(D0 + 4 * geo.V),
              static_cast<cx<float>*>(D32), partial, geo, st, mode, 1.0 / (12.0 * (double)geo.V),
              1.0 / (3.0 * (double)geo.V));
   return cudaPeekAtLastError();

@@ -84,6 +84,7 @@ struct lgf_ctx {
   bool df = false;            // ... on the double-float links in Udf (converted back at the end)
   void* Udf = nullptr;        // tail links in double-float: 36 V complex hi, then 36 V complex lo
   void* eta = nullptr;        // the tail's gauge transformation 1 + eta: 9 V complex hi, then 9 V lo
+  void* tbase = nullptr;      // the tail gradient's fixed part: Delta(Udf) (4 V complex), F terms (V float pairs)
 
   Geom geo{};
   Engine e64, e32;
@@ -361,12 +362,15 @@ int queue_tail_start(lgf_handle h) {
     if (!h->Udf) {
       h->Udf = dev_alloc(h, (size_t)2 * 36 * V * sizeof(float) * 2);
       h->eta = dev_alloc(h, (size_t)18 * V * sizeof(float) * 2);
-      if (!h->Udf || !h->eta) return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail failed");
+      h->tbase = dev_alloc(h, (size_t)5 * V * sizeof(float) * 2);
+      if (!h->Udf || !h->eta || !h->tbase)
+        return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail failed");
     }
     // e64.g (9 FP64 complex planes) holds Gh and Gl (2 x 9 FP32 complex planes)
     LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_df(h->G, h->e64.g, V, h->stream));
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_start_df(h->Uorig, h->e64.g, h->Udf, h->geo, h->stream));
     LGF_CUDA(h, cudaMemsetAsync(h->eta, 0, (size_t)18 * V * sizeof(float) * 2, h->stream));
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_tail_base(h->Udf, h->tbase, h->geo, h->stream));
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
     LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
@@ -393,7 +397,8 @@ int materialize_df(lgf_handle h) {
 int queue_gradient(lgf_handle h, Engine& e, int mode) {
   if (&e == &h->e64 && h->df)
     LGF_LAUNCH(h, LGF_K_GRADIENT,
-               launch_gradient_tail_eta(h->Udf, h->eta, h->e32.D, h->partial, h->geo, h->st, mode, h->stream));
+               launch_gradient_tail_eta(h->Udf, h->eta, h->tbase, h->e32.D, h->partial, h->geo, h->st, mode,
+                                        h->stream));
   else if (e.grep)
     LGF_LAUNCH(h, LGF_K_GRADIENT,
                launch_gradient_grep(e.nc, e.U, h->G, e.D, h->partial, h->geo, h->st, mode, h->stream));
@@ -414,7 +419,7 @@ int queue_iteration(lgf_handle h, Engine& e) {
     // gauge representation; FP32 acceleration and step on eta
     Engine& f = h->e32;
     LGF_LAUNCH(h, LGF_K_GRADIENT,
-               launch_gradient_tail_eta(h->Udf, h->eta, f.D, h->partial, h->geo, h->st, 1, s));
+               launch_gradient_tail_eta(h->Udf, h->eta, h->tbase, f.D, h->partial, h->geo, h->st, 1, s));
     int rc = queue_accelerate(h, f, h->st);
     if (rc) return rc;
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_eta_step(f.D, h->eta, h->V, 0.5 * h->alpha, h->st, s));

@@ -140,8 +140,11 @@ cudaError_t launch_promote_df(const void* G32, void* g_df, int64_t V, cudaStream
 cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf, const Geom& geo, cudaStream_t s);
 // the tail in gauge representation: links (1 + eta) Udf (1 + eta(x+mu))^dag, eta in double-float
 // (9 complex hi planes, then 9 lo planes; the gradient reads the hi planes)
-cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, void* D32, double2* partial, const Geom& geo,
-                                     DevState* st, int mode, cudaStream_t s);
+// the fixed part of the tail's gradient: Delta(Udf) packed (4 V complex FP32), then each site's
+// F term sum_mu Re tr Udf_mu(x) in double-float (V float pairs); 40 bytes per site in base
+cudaError_t launch_tail_base(const void* Udf, void* base, const Geom& geo, cudaStream_t s);
+cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, const void* base, void* D32,
+                                     double2* partial, const Geom& geo, DevState* st, int mode, cudaStream_t s);
 // eta <- (1 + eps)(1 + eta) - 1, eps = X + X^2/2 with X = half_alpha Delta~ from D32
 cudaError_t launch_tail_eta_step(const void* D32, void* eta, int64_t V, double half_alpha, const DevState* st,
                                  cudaStream_t s);
