@@ -576,8 +576,8 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_eta(const cx<float>* _
 // (|X|^2 ~ 1e-10) are rounded in FP32.  So 1 + eta stays unitary to O(|X|^3)
 // plus ~1e-17, where rounding X + X^2/2 as one FP32 sum would break unitarity
 // by 2^-24 |X| at every step.
-__global__ void __launch_bounds__(256) k_tail_eta_step(const cx<float>* __restrict__ D, cx<float>* eh,
-                                                       cx<float>* el, int V, float h,
+__global__ void __launch_bounds__(128, 5) k_tail_eta_step(const cx<float>* __restrict__ D, cx<float>* __restrict__ eh,
+                                                       cx<float>* __restrict__ el, int V, float h,
                                                        const DevState* __restrict__ st) {
   pdl_wait();
   if (st != nullptr && st->done) return;
@@ -595,8 +595,12 @@ __global__ void __launch_bounds__(256) k_tail_eta_step(const cx<float>* __restri
   X.e[2][0] = mk<float>(-h * c1.re, h * c1.im);
   X.e[2][1] = mk<float>(-h * c2.re, h * c2.im);
   M3<float> n;
+  cx<float> lo[9];  // all of eta's loads issued before any arithmetic
 #pragma unroll
-  for (int q = 0; q < 9; ++q) n.e[q / 3][q % 3] = eh[q * V + s];
+  for (int q = 0; q < 9; ++q) {
+    n.e[q / 3][q % 3] = eh[q * V + s];
+    lo[q] = el[q * V + s];
+  }
   // small terms: X^2/2 + (X + X^2/2) eta_hi
   M3<float> Y;
   mm<float, 3>(Y, X, X);
@@ -612,11 +616,10 @@ __global__ void __launch_bounds__(256) k_tail_eta_step(const cx<float>* __restri
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     const int i = q / 3, j = q % 3;
-    const cx<float> lo = el[q * V + s];
     df re = two_sum(n.e[i][j].re, X.e[i][j].re);
     df im = two_sum(n.e[i][j].im, X.e[i][j].im);
-    re = fast_two_sum(re.h, __fadd_rn(re.l, __fadd_rn(lo.re, Y.e[i][j].re)));
-    im = fast_two_sum(im.h, __fadd_rn(im.l, __fadd_rn(lo.im, Y.e[i][j].im)));
+    re = fast_two_sum(re.h, __fadd_rn(re.l, __fadd_rn(lo[q].re, Y.e[i][j].re)));
+    im = fast_two_sum(im.h, __fadd_rn(im.l, __fadd_rn(lo[q].im, Y.e[i][j].im)));
     eh[q * V + s] = mk<float>(re.h, im.h);
     el[q * V + s] = mk<float>(re.l, im.l);
   }
@@ -705,7 +708,7 @@ cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, const voi
 cudaError_t launch_tail_eta_step(const void* D32, void* eta, int64_t V, double half_alpha, const DevState* st,
                                  cudaStream_t s) {
   auto e = static_cast<cx<float>*>(eta);
-  launch_pdl(k_tail_eta_step, (unsigned)((V + 255) / 256), 256, 0, s, static_cast<const cx<float>*>(D32), e,
+  launch_pdl(k_tail_eta_step, (unsigned)((V + 127) / 128), 128, 0, s, static_cast<const cx<float>*>(D32), e,
              e + 9 * V, (int)V, (float)half_alpha, st);
   return cudaPeekAtLastError();
 }
