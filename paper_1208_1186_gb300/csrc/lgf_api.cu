@@ -351,20 +351,22 @@ int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
 
 // FP64 tail start of a mixed handle after its FP32 phase: the gauge G
 // reunitarised (in double-float for the double-float tail, else in FP64),
-// then the links rebuilt from the loaded input as G U_loaded G^dagger.  The defect-correction tail (theta < 1e-8 at the
-// hand-over, tail modes 0 and 2) and, in mode 0, its double-float links are
-// chosen here.
+// then the links rebuilt from the loaded input as G U_loaded G^dagger.  The
+// defect-correction tail (theta < 1e-8 at the hand-over, tail modes 0 and 2)
+// and, in mode 0, its double-float form are chosen here; that form also
+// clears the tail's gauge transformation and forms its gradient's fixed part.
 int queue_tail_start(lgf_handle h) {
   const int64_t V = h->V;
   h->defect = h->tail_mode != 1 && h->st_host->theta < 1e-8;
   h->df = h->defect && h->tail_mode == 0;
   if (h->df) {
-    if (!h->Udf) {
-      h->Udf = dev_alloc(h, (size_t)2 * 36 * V * sizeof(float) * 2);
-      h->eta = dev_alloc(h, (size_t)18 * V * sizeof(float) * 2);
-      h->tbase = dev_alloc(h, (size_t)5 * V * sizeof(float) * 2);
-      if (!h->Udf || !h->eta || !h->tbase)
-        return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail failed");
+    // each buffer on its own, so that a failed allocation is retried by the next tail start
+    if (!h->Udf) h->Udf = dev_alloc(h, (size_t)2 * 36 * V * sizeof(float) * 2);
+    if (!h->eta) h->eta = dev_alloc(h, (size_t)18 * V * sizeof(float) * 2);
+    if (!h->tbase) h->tbase = dev_alloc(h, (size_t)5 * V * sizeof(float) * 2);
+    if (!h->Udf || !h->eta || !h->tbase) {
+      h->df = false;
+      return fail(h, LGF_ERR_OOM, "device allocation of the double-float tail failed");
     }
     // e64.g (9 FP64 complex planes) holds Gh and Gl (2 x 9 FP32 complex planes)
     LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_df(h->G, h->e64.g, V, h->stream));
