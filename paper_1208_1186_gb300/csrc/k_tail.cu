@@ -16,33 +16,38 @@
 //                    correction in FP32 (from FP32-rounded U; its error is
 //                    |eps| * 2^-24 ~ 1e-13 |eps|), accumulated in FP64.
 //
-// FP64 work per site drops from ~2.5k operations (FP64 products, FFT,
-// Gram-Schmidt) to ~0.3k (sums).  Even those sums bound the kernels on this
-// GPU, whose FP64 pipe runs at 1/62 of FP32.  So by default the tail keeps its
-// links in double-float form instead: two FP32 planes per entry, value =
-// hi + lo with |lo| <= ulp(hi)/2 (48 significant bits, relative rounding
-// about 2^-47), and does every operation on the FP32 pipe with error-free
+// That is tail mode 2.  FP64 work per site drops from ~2.5k operations (FP64
+// products, FFT, Gram-Schmidt) to ~0.3k (sums), yet even those sums bound the
+// kernels on this GPU, whose FP64 pipe runs at 1/62 of FP32.  The default tail
+// (mode 0) does every operation on the FP32 pipe instead, in double-float form
+// where the precision is needed: two FP32 numbers per real, value = hi + lo
+// with |lo| <= ulp(hi)/2 (48 significant bits), handled by error-free
 // transformations (Knuth's two-sum, Dekker's fast-two-sum, the FMA
-// two-product):
+// two-product; lgf_df.cuh).  It also runs in gauge representation: the links
+// of the tail start stay fixed and the tail accumulates its own gauge
+// transformation 1 + eta(x), close to the identity:
 //
 //   k_promote_df        the FP32 gauge G reunitarised in double-float
 //                       (Gram-Schmidt), stored as hi and lo planes;
 //   k_tail_start_df     U = g U_loaded g(x+mu)^dag from the FP64 input (split
 //                       exactly into hi + lo by bit manipulation) and that
 //                       g, products in double-float;
+//   k_tail_base         Delta(U) and each site's F term, once (Delta is linear
+//                       in the link sums, so the tail's gradient is this
+//                       fixed part plus that of the corrections);
 //   k_gradient_tail_eta Delta of the current links (1 + eta) U (1 + eta')^dag:
-//                       double-float sums of U plus the FP32 corrections,
-//                       F summed in double-float per warp, D stored as FP32;
+//                       the fixed part plus the FP32 corrections, F summed
+//                       in double-float per warp, D stored as FP32;
 //   k_tail_eta_step     eps from the accelerated gradient, 1 + eta <-
-//                       (1 + eps)(1 + eta) at each site (the links of the
-//                       tail start are never rewritten);
-//   k_df_to_fp64        the links as FP64 planes, for the calls that need
-//                       them (exact conversions, one FP64 addition per
-//                       real); the links otherwise stay double-float, and
-//                       the host store writes FP64 from hi + lo directly.
+//                       (1 + eps)(1 + eta) at each site in double-float, X
+//                       added exactly (no link is rewritten);
+//   k_tail_apply_eta,   the links as FP64 planes, for the calls that need
+//   k_df_to_fp64        them; otherwise the host store forms them in FP64
+//                       directly (k_store_aos_df).
 //
-// The tail's own error budget (each FP32 correction is exact to |eps| 2^-24,
-// about 1e-12 at the first step) is far above the double-float rounding.
+// The corrections' FP32 rounding (2^-24 |eta| < 1e-12) perturbs only the
+// gradient that the tail drives to zero; the links and 1 + eta are formed
+// to ~2^-47.
 #include "lgf_df.cuh"
 #include "lgf_kernels.cuh"
 #include "lgf_reduce.cuh"
