@@ -6,9 +6,11 @@ Workload (default): one 32^4 configuration (links of scale 0.5 behind a random
 gauge of scale 1.0, seed 0), FP32 links (18 reals, structure of arrays) with
 FP64 F/theta sums, alpha = 0.08.  A step is one full iteration of the method
 (gradient, F/theta reduction, forward 4D FFT, p2_max/p2 scaling, inverse FFT,
-gauge step g, link update, gauge accumulation); ``value`` = lattice sites x
-timed steps / device time.  Then the same configuration is fixed to
-theta < 1e-15 (FP32 phase + FP64 tail): ``time_to_theta``.  ``e2e`` repeats the
+gauge step g, and the update, applied to the accumulated gauge transformation
+G <- g G with the links formed on the fly by the next gradient); ``value`` =
+lattice sites x timed steps / device time.  Then the same configuration is
+fixed to theta < 1e-15 (FP32 phase + an FP64-accurate double-float tail):
+``time_to_theta``.  ``e2e`` repeats the
 fix through the public API from pinned host links, with the host<->device
 copies inside the timed region.
 
