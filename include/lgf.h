@@ -156,7 +156,10 @@ int lgf_iterate(lgf_handle h, int n);
  * iterations instead.  Both stop at the same update. */
 int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out);
 
-/* F and theta of the current links (either pointer may be NULL). */
+/* F and theta of the current links (either pointer may be NULL).  After the
+ * double-float tail (LGF_TAIL_MODE 0) they come from that tail's gradient:
+ * F to double-float accuracy, Delta to ~1e-12 absolute (its link corrections
+ * are rounded in FP32), so theta is exact to ~1e-12 sqrt(theta). */
 int lgf_functional(lgf_handle h, double* F, double* theta);
 
 /* Intermediates of one iteration on the current links, without updating
