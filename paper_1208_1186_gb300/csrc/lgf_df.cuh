@@ -123,17 +123,19 @@ __device__ __forceinline__ df dacc_result(dacc a) { return fast_two_sum(a.h, a.l
 // 1 / sqrt(n) for a double-float n near 1 (a row norm of a matrix within
 // ~1e-3 of unitary): y = rsqrtf(n.h), then with n y^2 = 1 + d, |d| ~ 2^-22,
 // 1/sqrt(n) = y (1 - d/2 + 3 d^2 / 8 - ...), whose next term (~2^-68) is far
-// below double-float rounding.  d is formed exactly: n.h y^2 - 1 by an exact
-// subtraction (Sterbenz) plus the low parts.
+// below double-float rounding.  d = dh + dl is formed exactly: n.h y^2 - 1 by
+// an exact subtraction (Sterbenz), plus the low parts (dl ~ 2^-23, so the
+// quadratic term needs the whole d: its cross term 3/4 dh dl is ~2^-45).
 __device__ __forceinline__ df df_rsqrt(df n) {
   const float y = rsqrtf(n.h);
   const df t = two_prod(y, y);
   const df m = two_prod(n.h, t.h);
   const float dh = __fsub_rn(m.h, 1.f);
   const float dl = __fmaf_rn(n.h, t.l, __fmaf_rn(n.l, t.h, m.l));
+  const float d = __fadd_rn(dh, dl);
   // y (-dh / 2) exactly, the rest to first order
   const df p = two_prod(y, -0.5f * dh);
-  const float rest = __fmaf_rn(y, __fmaf_rn(0.375f * dh, dh, -0.5f * dl), p.l);
+  const float rest = __fmaf_rn(y, __fmaf_rn(0.375f * d, d, -0.5f * dl), p.l);
   const df q = fast_two_sum(y, p.h);
   return fast_two_sum(q.h, __fadd_rn(q.l, rest));
 }

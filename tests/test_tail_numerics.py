@@ -116,3 +116,63 @@ def test_two_sum_is_exact():
     s, e = _two_sum(a, b)
     np.testing.assert_array_equal(s.astype(np.float64) + e.astype(np.float64),
                                   a.astype(np.float64) + b.astype(np.float64))
+
+
+def _two_prod(a, b):
+    """p + e = a b exactly: the FMA's exact residual, emulated in float64
+    (a product of two FP32 numbers is exact in float64)."""
+    p = (a * b).astype(F)
+    e = (a.astype(np.float64) * b.astype(np.float64) - p.astype(np.float64)).astype(F)
+    return p, e
+
+
+def test_corrected_rsqrt_reaches_double_float_accuracy():
+    """df_rsqrt: y = an approximate 1/sqrt(n.h) (here off by up to 4 ulp, as
+    a hardware approximation may be), then with n y^2 = 1 + d formed exactly,
+    1/sqrt(n) = y (1 - d/2 + 3 d^2/8): relative error ~2^-47, for n within
+    1e-3 of 1 as the row norms of a nearly unitary matrix are.  The quadratic
+    term takes the whole d = dh + dl: with dh^2 alone (an earlier form) the
+    dropped 3/4 dh dl left ~2^-44."""
+    rng = np.random.default_rng(11)
+    nh = (1.0 + rng.uniform(-1e-3, 1e-3, 5000)).astype(F)
+    nl = (rng.uniform(-1, 1, 5000) * np.spacing(nh) * 0.5).astype(F)
+    exact = 1.0 / np.sqrt(nh.astype(np.longdouble) + nl.astype(np.longdouble))
+    y = (1.0 / np.sqrt(nh.astype(np.float64))).astype(F)
+    y = (y + rng.integers(-4, 5, 5000) * np.spacing(y)).astype(F)  # the approximation
+    th, tl = _two_prod(y, y)
+    mh, ml = _two_prod(nh, th)
+    dh = (mh - F(1.0)).astype(F)  # exact (Sterbenz)
+    dl = ((nh * tl).astype(F) + (nl * th).astype(F) + ml).astype(F)
+    d = (dh + dl).astype(F)
+    ph, pl = _two_prod(y, (F(-0.5) * dh).astype(F))
+    rest = (y * ((F(0.375) * d).astype(F) * d - F(0.5) * dl).astype(F) + pl).astype(F)
+    qh, ql = _fast_two_sum(y, ph)
+    rh, rl = _fast_two_sum(qh, (ql + rest).astype(F))
+    got = rh.astype(np.longdouble) + rl.astype(np.longdouble)
+    rel = np.abs(got / exact - 1.0)
+    assert float(np.max(rel)) < 2.0 ** -46
+    # the uncorrected approximation is ~2^-21 off: the correction is what matters
+    assert float(np.max(np.abs(y.astype(np.longdouble) / exact - 1.0))) > 2.0 ** -24
+
+
+def test_dot2_accumulation_reaches_double_float_accuracy():
+    """dacc_prod (Dot2): the running high part advances by exact two-sums and
+    all product and sum errors go to one FP32 low part.  A 3-term complex dot
+    product of FP32 numbers (6 real products) comes out accurate to ~2^-47 of
+    the sum of |terms|."""
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for _ in range(2000):
+        x = rng.uniform(-1, 1, 6).astype(F)
+        y = rng.uniform(-1, 1, 6).astype(F)
+        h, lo = F(0.0), F(0.0)
+        for a, b in zip(x, y):
+            p, e = _two_prod(np.array([a]), np.array([b]))
+            s, t = _two_sum(np.array([h]), p)
+            h = s[0]
+            lo = F(lo + F(e[0] + t[0]))
+        got = np.longdouble(h) + np.longdouble(lo)
+        exact = np.sum(x.astype(np.longdouble) * y.astype(np.longdouble))
+        scale = np.sum(np.abs(x.astype(np.longdouble) * y.astype(np.longdouble)))
+        worst = max(worst, float(abs(got - exact) / scale))
+    assert worst < 2.0 ** -46
