@@ -176,3 +176,140 @@ def test_dot2_accumulation_reaches_double_float_accuracy():
         scale = np.sum(np.abs(x.astype(np.longdouble) * y.astype(np.longdouble)))
         worst = max(worst, float(abs(got - exact) / scale))
     assert worst < 2.0 ** -46
+
+
+# ---------------------------------------------------------------------------
+# k_promote_df: Gram-Schmidt of the FP32 gauge G in double-float
+# ---------------------------------------------------------------------------
+class _Acc:
+    """dacc: h advances by exact two-sums, every error into one FP32 l."""
+
+    def __init__(self, h=0.0, lo=0.0):
+        self.h, self.l = F(h), F(lo)
+
+    def prod(self, x, y):  # x, y FP32
+        p, e = _two_prod(np.array([x], F), np.array([y], F))
+        s, t = _two_sum(np.array([self.h], F), p)
+        self.h, self.l = s[0], F(self.l + F(e[0] + t[0]))
+
+    def prod_df(self, xh, xl, y):  # x double-float, y FP32
+        p, e = _two_prod(np.array([xh], F), np.array([y], F))
+        s, t = _two_sum(np.array([self.h], F), p)
+        self.h, self.l = s[0], F(self.l + F(F(F(xl * y) + e[0]) + t[0]))
+
+    def prod_dd(self, xh, xl, yh, yl):  # both double-float
+        p, e = _two_prod(np.array([xh], F), np.array([yh], F))
+        s, t = _two_sum(np.array([self.h], F), p)
+        self.h, self.l = s[0], F(self.l + F(F(F(xh * yl) + F(F(xl * yh) + e[0])) + t[0]))
+
+    def result(self):
+        s, e = _fast_two_sum(np.array([self.h], F), np.array([self.l], F))
+        return s[0], e[0]
+
+
+def _rsqrt_df(nh, nl):
+    y = F(1.0 / np.sqrt(np.float64(nh)))
+    th, tl = _two_prod(np.array([y], F), np.array([y], F))
+    mh, ml = _two_prod(np.array([nh], F), th)
+    dh = F(mh[0] - F(1.0))
+    dl = F(F(nh * tl[0]) + F(F(nl * th[0]) + ml[0]))
+    d = F(dh + dl)
+    ph, pl = _two_prod(np.array([y], F), np.array([F(F(-0.5) * dh)], F))
+    rest = F(F(y * F(F(F(0.375) * d) * d - F(F(0.5) * dl))) + pl[0])
+    qh, ql = _fast_two_sum(np.array([y], F), ph)
+    return _fast_two_sum(qh, np.array([F(ql[0] + rest)], F))
+
+
+def _mul_f(xh, xl, f):  # df_mul_f
+    p, e = _two_prod(np.array([xh], F), np.array([f], F))
+    return _fast_two_sum(p, np.array([F(F(xl * f) + e[0])], F))
+
+
+def _mul_dd(xh, xl, yh, yl):  # df_mul
+    p, e = _two_prod(np.array([xh], F), np.array([yh], F))
+    return _fast_two_sum(p, np.array([F(F(xh * yl) + F(F(xl * yh) + e[0]))], F))
+
+
+def _promote(G):
+    """Rows 0 and 1 of an FP32 3x3 complex G -> (Gh, Gl) in the kernel's order."""
+    r0, r1 = G[0], G[1]
+    n = _Acc()
+    for j in range(3):
+        n.prod(r0[j].real, r0[j].real)
+        n.prod(r0[j].imag, r0[j].imag)
+    ih, il = _rsqrt_df(*n.result())
+    u = []
+    for j in range(3):
+        a = _mul_f(ih[0], il[0], r0[j].real)
+        b = _mul_f(ih[0], il[0], r0[j].imag)
+        u.append((a[0][0], a[1][0], b[0][0], b[1][0]))  # re h, re l, im h, im l
+    pr, pi = _Acc(), _Acc()
+    for j in range(3):
+        urh, url, uih, uil = u[j]
+        pr.prod_df(urh, url, r1[j].real)
+        pr.prod_df(uih, uil, r1[j].imag)
+        pi.prod_df(urh, url, r1[j].imag)
+        pi.prod_df(-uih, -uil, r1[j].real)
+    ipr, ipi = pr.result(), pi.result()
+    w = []
+    for j in range(3):
+        urh, url, uih, uil = u[j]
+        a, b = _Acc(r1[j].real), _Acc(r1[j].imag)
+        a.prod_dd(-ipr[0], -ipr[1], urh, url)
+        a.prod_dd(ipi[0], ipi[1], uih, uil)
+        b.prod_dd(-ipr[0], -ipr[1], uih, uil)
+        b.prod_dd(-ipi[0], -ipi[1], urh, url)
+        w.append(a.result() + b.result())
+    n = _Acc()
+    for j in range(3):
+        n.prod_dd(w[j][0], w[j][1], w[j][0], w[j][1])
+        n.prod_dd(w[j][2], w[j][3], w[j][2], w[j][3])
+    jh, jl = _rsqrt_df(*n.result())
+    w2 = []
+    for j in range(3):
+        a = _mul_dd(w[j][0], w[j][1], jh[0], jl[0])
+        b = _mul_dd(w[j][2], w[j][3], jh[0], jl[0])
+        w2.append((a[0][0], a[1][0], b[0][0], b[1][0]))
+    v = []
+    for j in range(3):
+        k, l = (j + 1) % 3, (j + 2) % 3
+        ukr, ukrl, uki, ukil = u[k]
+        ulr, ulrl, uli, ulil = u[l]
+        wkr, wkrl, wki, wkil = w2[k]
+        wlr, wlrl, wli, wlil = w2[l]
+        a, b = _Acc(), _Acc()
+        a.prod_dd(ukr, ukrl, wlr, wlrl)
+        a.prod_dd(-uki, -ukil, wli, wlil)
+        a.prod_dd(-ulr, -ulrl, wkr, wkrl)
+        a.prod_dd(uli, ulil, wki, wkil)
+        b.prod_dd(-ukr, -ukrl, wli, wlil)
+        b.prod_dd(-uki, -ukil, wlr, wlrl)
+        b.prod_dd(ulr, ulrl, wki, wkil)
+        b.prod_dd(uli, ulil, wkr, wkrl)
+        v.append(a.result() + b.result())
+    M = np.zeros((3, 3), np.complex128)
+    for j in range(3):
+        for row, src in ((0, u[j]), (1, w2[j]), (2, v[j])):
+            M[row, j] = (np.float64(src[0]) + np.float64(src[1])) + 1j * (np.float64(src[2]) + np.float64(src[3]))
+    return M
+
+
+def test_double_float_promote_is_special_unitary_to_double_float_accuracy():
+    """k_promote_df's Gram-Schmidt, emulated: for FP32 gauge matrices within
+    ~1e-6 of SU(3), Gh + Gl is unitary with det 1 to ~2^-46, and rows 0 and 1
+    span the same directions as the input's (it reunitarises, it does not
+    move the matrix)."""
+    rng = np.random.default_rng(9)
+    worst = 0.0
+    for _ in range(200):
+        A = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        Q, R = np.linalg.qr(A)
+        Q = Q * (np.diag(R) / np.abs(np.diag(R)))
+        Q[2] = np.conj(np.cross(Q[0], Q[1]))  # SU(3)
+        G = (Q + 1e-6 * (rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3)))).astype(np.complex64)
+        M = _promote(G)
+        worst = max(worst, np.max(np.abs(M @ M.conj().T - np.eye(3))), abs(np.linalg.det(M) - 1))
+        # row 0 is G's row 0 normalised
+        r0 = G[0].astype(np.complex128)
+        assert np.max(np.abs(M[0] - r0 / np.linalg.norm(r0))) < 1e-14
+    assert worst < 2.0 ** -45
