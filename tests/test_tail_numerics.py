@@ -313,3 +313,86 @@ def test_double_float_promote_is_special_unitary_to_double_float_accuracy():
         r0 = G[0].astype(np.complex128)
         assert np.max(np.abs(M[0] - r0 / np.linalg.norm(r0))) < 1e-14
     assert worst < 2.0 ** -45
+
+
+# ---------------------------------------------------------------------------
+# k_tail_start_df: U = g U_loaded g'^dag in double-float
+# ---------------------------------------------------------------------------
+def _split64(x):
+    """split_fp64: hi = x truncated to 24 significant bits, lo = the rest
+    rounded to FP32."""
+    b = np.array([x], np.float64).view(np.uint64)[0]
+    hi = np.array([b & np.uint64(0xFFFFFFFFE0000000)], np.uint64).view(np.float64)[0]
+    return F(hi), F(x - hi)
+
+
+def _tail_link(gh, gl, U, fh, fl):
+    """One link, rows of W = g U with the first-order terms in the low parts,
+    then W f^dag likewise (the kernel's order)."""
+    UH = np.zeros((3, 3), np.complex64)
+    UL = np.zeros((3, 3), np.complex64)
+    for i in range(3):
+        for j in range(3):
+            rh, rl = _split64(U[i, j].real)
+            ih, il = _split64(U[i, j].imag)
+            UH[i, j], UL[i, j] = complex(rh, ih), complex(rl, il)
+    out = np.zeros((3, 3), np.complex128)
+    for a in range(3):
+        W = []
+        for b in range(3):
+            re, im = _Acc(), _Acc()
+            for k in range(3):
+                x, y, xe, ye = gh[a, k], UH[k, b], gl[a, k], UL[k, b]
+                re.prod(x.real, y.real)
+                re.prod(-x.imag, y.imag)
+                im.prod(x.real, y.imag)
+                im.prod(x.imag, y.real)
+                re.l = F(re.l + F(F(F(xe.real * y.real) - F(xe.imag * y.imag)) + F(F(x.real * ye.real) - F(x.imag * ye.imag))))
+                im.l = F(im.l + F(F(F(xe.real * y.imag) + F(xe.imag * y.real)) + F(F(x.real * ye.imag) + F(x.imag * ye.real))))
+            W.append(re.result() + im.result())
+        for b in range(3):
+            re, im = _Acc(), _Acc()
+            for k in range(3):
+                wrh, wrl, wih, wil = W[k]
+                f, fe = fh[b, k], fl[b, k]
+                re.prod_df(wrh, wrl, f.real)
+                re.prod_df(wih, wil, f.imag)
+                im.prod_df(wih, wil, f.real)
+                im.prod_df(-wrh, -wrl, f.imag)
+                re.l = F(re.l + F(F(wrh * fe.real) + F(wih * fe.imag)))
+                im.l = F(im.l + F(F(wih * fe.real) - F(wrh * fe.imag)))
+            rh, rl = re.result()
+            ih, il = im.result()
+            out[a, b] = (np.float64(rh) + np.float64(rl)) + 1j * (np.float64(ih) + np.float64(il))
+    return out
+
+
+def _split_df(M):
+    h = M.astype(np.complex64)
+    return h, (M - h.astype(np.complex128)).astype(np.complex64)
+
+
+def test_double_float_tail_start_forms_the_link_to_double_float_accuracy():
+    """k_tail_start_df, emulated: with g, g' double-float matrices and U an
+    FP64 SU(3) link, g U g'^dag comes out within ~2^-46 of the product in
+    FP64 (the dropped second-order terms and the roundings are ~2^-48 each)."""
+    rng = np.random.default_rng(13)
+
+    def su3():
+        A = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        Q, R = np.linalg.qr(A)
+        Q = Q * (np.diag(R) / np.abs(np.diag(R)))
+        Q[2] = np.conj(np.cross(Q[0], Q[1]))
+        return Q
+
+    worst_err = 0.0
+    for _ in range(100):
+        g, U, f = su3(), su3(), su3()
+        gh, gl = _split_df(g)
+        fh, fl = _split_df(f)
+        gd = gh.astype(np.complex128) + gl.astype(np.complex128)
+        fd = fh.astype(np.complex128) + fl.astype(np.complex128)
+        ref = gd @ U @ fd.conj().T
+        got = _tail_link(gh, gl, U, fh, fl)
+        worst_err = max(worst_err, np.max(np.abs(got - ref)))
+    assert worst_err < 2.0 ** -45
