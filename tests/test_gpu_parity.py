@@ -286,6 +286,9 @@ def test_full_size_32_4_fp32_tail(lgf):
     # Landau condition from the oracle's own gradient of the result
     assert O.functional(out)[1] < 1e-15
     assert F > O.functional(U)[0]
+    # the oracle's own fix of this input (stored by tests/golden/make_fullsize_fix.py)
+    from tests.test_gpu_fullsize import check_against_oracle_fix
+    check_against_oracle_fix("32^4", dims, F, iters)
 
 
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (12, 12, 32, 8)])
