@@ -108,9 +108,11 @@ typedef void* (*lgf_alloc_fn)(size_t bytes, int device, void* stream, void* user
 typedef void (*lgf_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
 int lgf_set_allocator(lgf_alloc_fn alloc, lgf_free_fn free_fn, void* user);
 
-/* Create a context for an Lx x Ly x Lz x Lt periodic lattice (Sec. 2.2 keeps
- * lattice constants in constant memory; here they live in the handle and are
- * passed by value to every kernel).  Each extent must be in [2, 64] and a
+/* Create a context for an Lx x Ly x Lz x Lt periodic lattice.  Paper Sec.
+ * 2.2: one thread per lattice site, the site index rebuilt inside the kernel,
+ * lattice constants in constant memory (here they live in the handle and are
+ * passed by value to every kernel); Sec. 3.1: single or double precision,
+ * 18-real or 12-real storage, the dtype choices here.  Each extent must be in [2, 64] and a
  * product of 2, 3 and 5 (the radices of the on-chip FFT); dtype is an
  * lgf_dtype.  Allocates all device buffers.  On failure *out is NULL and
  * lgf_last_error(NULL) describes the cause. */
@@ -129,22 +131,37 @@ int lgf_set_param(lgf_handle h, int key, double value);
 
 /* Copy V*4*18 doubles of host links in (layout above), converting to the
  * handle's storage; links must be SU(3) to rounding.  Mixed-precision
- * handles also keep the FP64 input for the FP64 tail. */
+ * handles also keep the FP64 input for the FP64 tail.
+ * Paper Sec. 2.2: the lattice lives in global memory as a structure of
+ * arrays, one plane per matrix element and direction, so that the FFT can
+ * work on each element without reordering; the 12-real storage keeps rows 1
+ * and 2 and rebuilds row 3 from unitarity.  This call performs that
+ * re-layout (and, for LGF_F32*, the rounding to FP32) on the device. */
 int lgf_load_links(lgf_handle h, const double* host_aos);
 
 /* As lgf_load_links, from device memory (e.g. a torch tensor's data_ptr)
- * on the handle's device. */
+ * on the handle's device (paper Sec. 2.2, the same structure-of-arrays
+ * re-layout).  dev_aos must hold V*4*18 doubles; it is read, not kept. */
 int lgf_load_links_device(lgf_handle h, const double* dev_aos);
 
 /* Copy the current links out, as V*4*18 host doubles (layout above).  12-real
- * storage rebuilds row 3. */
+ * storage rebuilds row 3 as conj(row1 x row2) (paper Sec. 2.2).  host_aos
+ * is caller-owned; the call returns once it is written. */
 int lgf_store_links(lgf_handle h, double* host_aos);
 
 /* Apply exactly n iterations (no convergence test).  Mixed-precision handles
- * iterate in their FP32 storage. */
+ * iterate in their FP32 storage.  One iteration is one step of the paper's
+ * steepest descent with Fourier acceleration (Sec. 1, after Davies et al.),
+ * with the gradient transformed as 2D plus 2D FFTs (Sec. 2.2): the formulas
+ * at the top of this file, gradient through update.  n < 0 gives
+ * LGF_ERR_ARG; n = 0 does nothing. */
 int lgf_iterate(lgf_handle h, int n);
 
-/* Iterate until theta < theta_tol or max_iter updates have been applied.
+/* Fix to Landau gauge (paper Sec. 1: the singlet correlator is not gauge
+ * invariant, so the links are first brought to Landau gauge by steepest
+ * descent with Fourier acceleration; Sec. 3.1 measures that iteration in
+ * single and double precision).
+ * Iterate until theta < theta_tol or max_iter updates have been applied.
  * *iters_out (may be NULL) receives the number of updates.  Returns LGF_OK,
  * LGF_ERR_NOT_CONVERGED or an error.  Mixed-precision handles run the FP32
  * phase down to LGF_TAIL_THETA (or until theta below 1e-6 stops halving
@@ -156,7 +173,11 @@ int lgf_iterate(lgf_handle h, int n);
  * iterations instead.  Both stop at the same update. */
 int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out);
 
-/* F and theta of the current links (either pointer may be NULL).  After the
+/* F and theta of the current links (either pointer may be NULL): the gauge
+ * functional the steepest descent of paper Sec. 1 maximises and its
+ * convergence measure, normalised as at the top of this file, summed in a
+ * fixed order with FP64 above the warp (the result does not depend on
+ * scheduling).  After the
  * double-float tail (LGF_TAIL_MODE 0) they come from that tail's gradient:
  * F to double-float accuracy, Delta to ~1e-12 absolute (its link corrections
  * are rounded in FP32), so theta is exact to ~1e-12 sqrt(theta). */
@@ -334,10 +355,14 @@ const char* lgf_net_last_error(lgf_net n);
  * held until the process exits), so V may be at most 4,194,304 sites
  * (e.g. 32^4 or 48^3 x 12; 64^4 is rejected with LGF_ERR_ARG).  Every call
  * shares that array: calls that overlap on the GPU race on it and give wrong
- * results, so order them on one stream or synchronise between them.  The
- * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.  Errors: LGF_ERR_ARG for bad extents,
+ * results, so order them on one stream or synchronise between them.  Every
+ * call made while `stream` is not capturing looks up the array's device
+ * address (cudaGetSymbolAddress) in the current device's current context,
+ * so a call after cudaDeviceReset or in another context finds the right
+ * array; a call made during stream capture reuses the address found by the
+ * last uncaptured call on that device, so make one uncaptured call, in the
+ * context the capture will use, before capture begins (a captured call with
+ * no earlier one gives LGF_ERR_ARG).  Errors: LGF_ERR_ARG for bad extents,
  * dtype, size or NULL pointers, LGF_ERR_CUDA for a failed lookup or launch;
  * the text is in lgf_last_error(NULL). */
 int lgf_functional_noalloc(const void* links, int Lx, int Ly, int Lz, int Lt, int dtype, double* out,
