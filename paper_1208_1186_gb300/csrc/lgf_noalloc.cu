@@ -19,9 +19,14 @@
 // order them on one stream or synchronise between them.
 //
 // Host code never dereferences the array's name: on the host it is only a
-// stand-in symbol.  The device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, on the first call made on
-// that device; make that first call before any stream capture begins.
+// stand-in symbol.  The device address comes from cudaGetSymbolAddress with
+// the caller's device current.  A call whose stream is not capturing looks it
+// up again every time (a few microseconds of host work), so the address
+// always belongs to the current context, also after cudaDeviceReset or when
+// the caller runs in a context of its own; the result is remembered per
+// device for calls made during stream capture, which reuse the address of the
+// last uncaptured call on that device.  So make one uncaptured call, in the
+// context the capture will use, before capture begins.
 #include <mutex>
 #include <string>
 
@@ -126,14 +131,21 @@ __global__ void __launch_bounds__(1024) k_functional_final(const double2* __rest
   }
 }
 
-// Device address of the partials array on the current device (looked up once).
-cudaError_t partials_address(double2** out) {
+// Device address of the partials array in the current context.  Outside
+// stream capture it is looked up on every call and remembered per device;
+// during capture the remembered address is used (*out stays null if there is
+// none yet).
+cudaError_t partials_address(cudaStream_t s, double2** out) {
+  *out = nullptr;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_symbol_mutex);
-  if (g_symbol_addr[dev] == nullptr) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
@@ -175,13 +187,17 @@ extern "C" int lgf_functional_noalloc(const void* links, int Lx, int Ly, int Lz,
   if (dtype < LGF_F64 || dtype > LGF_F64_R12) return noalloc_fail(LGF_ERR_ARG, "lgf_functional_noalloc: unknown dtype");
   if (links == nullptr || out == nullptr)
     return noalloc_fail(LGF_ERR_ARG, "lgf_functional_noalloc: links and out must be device pointers");
-  double2* partial = nullptr;
-  cudaError_t e = partials_address(&partial);
-  if (e != cudaSuccess)
-    return noalloc_fail(LGF_ERR_CUDA, std::string("lgf_functional_noalloc: cudaGetSymbolAddress: ") +
-                                          cudaGetErrorString(e));
-  const int nb = (int)((V + kNoallocThreads - 1) / kNoallocThreads);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double2* partial = nullptr;
+  cudaError_t e = partials_address(s, &partial);
+  if (e != cudaSuccess)
+    return noalloc_fail(LGF_ERR_CUDA, std::string("lgf_functional_noalloc: scratch address lookup: ") +
+                                          cudaGetErrorString(e));
+  if (partial == nullptr)
+    return noalloc_fail(LGF_ERR_ARG,
+                        "lgf_functional_noalloc: called during stream capture before any uncaptured call on this "
+                        "device (the scratch array's address is looked up outside capture)");
+  const int nb = (int)((V + kNoallocThreads - 1) / kNoallocThreads);
   const bool f64 = (dtype == LGF_F64 || dtype == LGF_F64_R12);
   const bool r12 = (dtype == LGF_F32_R12 || dtype == LGF_F64_R12);
   if (f64 && !r12)

@@ -6,8 +6,9 @@ libraries to call cudaMalloc, or a monitor that must not change the memory
 footprint of the job it watches).  The links and the output live in memory
 the caller already owns; the library's only scratch is a fixed array compiled
 into it.  The GPU test checks two calls in a row, on different lattices,
-against lgf_functional, the entry point that allocates its own buffers.  The
-file is named to be collected last.
+against lgf_functional, the entry point that allocates its own buffers, and
+against the FP64 oracle's F and theta of the same links.  The file is named
+to be collected last.
 """
 import ctypes
 
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 
 import lgf_inputs as I
+from oracle import lgf_oracle as O
 from paper_1208_1186_gb300 import _lib
 from paper_1208_1186_gb300.build import build
 
@@ -62,6 +64,12 @@ def test_noalloc_functional_matches_lgf_functional(dtype):
         rel_F, rel_th = (1e-13, 1e-12) if dtype.startswith("f64") else (1e-6, 1e-5)
         assert F == pytest.approx(F_ref, rel=rel_F)
         assert th == pytest.approx(th_ref, rel=rel_th)
+        # the oracle's FP64 F and theta of the unrounded links: FP32 storage
+        # rounds each entry by 2^-24 relative, which moves F and theta by
+        # about that much relative (theta of these links is O(1))
+        F_o, th_o = O.functional(U)
+        assert F == pytest.approx(F_o, rel=rel_F)
+        assert th == pytest.approx(th_o, rel=rel_th)
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
