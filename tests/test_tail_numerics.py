@@ -1,5 +1,7 @@
 """The arithmetic of the double-float tail step, emulated in numpy float32
-(each operation rounded to nearest, no fused multiply-add), on the CPU.
+on the CPU: each operation rounded to nearest, and a fused multiply-add
+(``_fma``) rounded once wherever the kernels use ``__fmaf_rn``, in the
+kernels' order of operations.
 
 The tail accumulates its gauge transformation 1 + eta <- (1 + eps)(1 + eta),
 eps = X + X^2/2 with X = alpha/2 Delta~ traceless anti-Hermitian, |X| ~ 1e-5.
@@ -24,6 +26,53 @@ def _two_sum(a, b):
 def _fast_two_sum(a, b):
     s = (a + b).astype(F)
     return s, (b - (s - a).astype(F)).astype(F)
+
+
+def _fma(x, y, z):
+    """FP32 fma(x, y, z) = x y + z rounded once to nearest (even).  The
+    product of two FP32 numbers is exact in float64; the float64 sum s and
+    its exact two-sum residual e settle the one case where rounding s to
+    FP32 differs from rounding the exact value: s on an FP32 midpoint."""
+    x, y, z = float(F(x)), float(F(y)), float(F(z))
+    p = x * y
+    s = p + z
+    bb = s - p
+    e = (p - (s - bb)) + (z - bb)
+    r = F(s)
+    if e != 0.0 and float(r) != s:
+        dn = r if float(r) < s else np.nextafter(r, F(-np.inf))
+        up = np.nextafter(r, F(np.inf)) if float(r) < s else r
+        if s == (float(dn) + float(up)) / 2:
+            r = up if e > 0 else dn
+    return F(r)
+
+
+def test_fma_emulation_rounds_once():
+    """_fma against exact rational arithmetic, including products whose sum
+    lands on an FP32 rounding midpoint after the float64 addition."""
+    from fractions import Fraction
+    rng = np.random.default_rng(2)
+
+    def round32(q):
+        # nearest FP32 to the rational q (ties to even), by bracketing
+        f = F(float(q))
+        lo = f if Fraction(float(f)) <= q else np.nextafter(f, F(-np.inf))
+        hi = np.nextafter(lo, F(np.inf))
+        dl, dh = q - Fraction(float(lo)), Fraction(float(hi)) - q
+        if dl < dh:
+            return lo
+        if dh < dl:
+            return hi
+        return lo if (np.array([lo], F).view(np.uint32)[0] & 1) == 0 else hi
+
+    cases = [(F(1 + 2.0 ** -12), F(1 + 2.0 ** -12), F(-(2.0 ** -24) * 0.5))]
+    for _ in range(3000):
+        x, y = F(rng.uniform(-2, 2)), F(rng.uniform(-2, 2))
+        z = F(-float(x) * float(y) + rng.uniform(-1, 1) * 2.0 ** -rng.integers(0, 40))
+        cases.append((x, y, z))
+    for x, y, z in cases:
+        exact = Fraction(float(x)) * Fraction(float(y)) + Fraction(float(z))
+        assert _fma(x, y, z) == round32(exact)
 
 
 def _mm32(a, b):
@@ -142,10 +191,11 @@ def test_corrected_rsqrt_reaches_double_float_accuracy():
     th, tl = _two_prod(y, y)
     mh, ml = _two_prod(nh, th)
     dh = (mh - F(1.0)).astype(F)  # exact (Sterbenz)
-    dl = ((nh * tl).astype(F) + (nl * th).astype(F) + ml).astype(F)
+    vfma = np.vectorize(_fma, otypes=[F])
+    dl = vfma(nh, tl, vfma(nl, th, ml))
     d = (dh + dl).astype(F)
     ph, pl = _two_prod(y, (F(-0.5) * dh).astype(F))
-    rest = (y * ((F(0.375) * d).astype(F) * d - F(0.5) * dl).astype(F) + pl).astype(F)
+    rest = vfma(y, vfma((F(0.375) * d).astype(F), d, (F(-0.5) * dl).astype(F)), pl)
     qh, ql = _fast_two_sum(y, ph)
     rh, rl = _fast_two_sum(qh, (ql + rest).astype(F))
     got = rh.astype(np.longdouble) + rl.astype(np.longdouble)
@@ -195,12 +245,15 @@ class _Acc:
     def prod_df(self, xh, xl, y):  # x double-float, y FP32
         p, e = _two_prod(np.array([xh], F), np.array([y], F))
         s, t = _two_sum(np.array([self.h], F), p)
-        self.h, self.l = s[0], F(self.l + F(F(F(xl * y) + e[0]) + t[0]))
+        self.h, self.l = s[0], F(self.l + F(_fma(xl, y, e[0]) + t[0]))
 
     def prod_dd(self, xh, xl, yh, yl):  # both double-float
         p, e = _two_prod(np.array([xh], F), np.array([yh], F))
         s, t = _two_sum(np.array([self.h], F), p)
-        self.h, self.l = s[0], F(self.l + F(F(F(xh * yl) + F(F(xl * yh) + e[0])) + t[0]))
+        self.h, self.l = s[0], F(self.l + F(_fma(xh, yl, _fma(xl, yh, e[0])) + t[0]))
+
+    def lo(self, x, y):  # dacc_lo: a first-order term into the low part, one FMA
+        self.l = _fma(x, y, self.l)
 
     def result(self):
         s, e = _fast_two_sum(np.array([self.h], F), np.array([self.l], F))
@@ -212,22 +265,22 @@ def _rsqrt_df(nh, nl):
     th, tl = _two_prod(np.array([y], F), np.array([y], F))
     mh, ml = _two_prod(np.array([nh], F), th)
     dh = F(mh[0] - F(1.0))
-    dl = F(F(nh * tl[0]) + F(F(nl * th[0]) + ml[0]))
+    dl = _fma(nh, tl[0], _fma(nl, th[0], ml[0]))
     d = F(dh + dl)
     ph, pl = _two_prod(np.array([y], F), np.array([F(F(-0.5) * dh)], F))
-    rest = F(F(y * F(F(F(0.375) * d) * d - F(F(0.5) * dl))) + pl[0])
+    rest = _fma(y, _fma(F(F(0.375) * d), d, F(F(-0.5) * dl)), pl[0])
     qh, ql = _fast_two_sum(np.array([y], F), ph)
     return _fast_two_sum(qh, np.array([F(ql[0] + rest)], F))
 
 
 def _mul_f(xh, xl, f):  # df_mul_f
     p, e = _two_prod(np.array([xh], F), np.array([f], F))
-    return _fast_two_sum(p, np.array([F(F(xl * f) + e[0])], F))
+    return _fast_two_sum(p, np.array([_fma(xl, f, e[0])], F))
 
 
 def _mul_dd(xh, xl, yh, yl):  # df_mul
     p, e = _two_prod(np.array([xh], F), np.array([yh], F))
-    return _fast_two_sum(p, np.array([F(F(xh * yl) + F(F(xl * yh) + e[0]))], F))
+    return _fast_two_sum(p, np.array([_fma(xh, yl, _fma(xl, yh, e[0]))], F))
 
 
 def _promote(G):
@@ -347,8 +400,14 @@ def _tail_link(gh, gl, U, fh, fl):
                 re.prod(-x.imag, y.imag)
                 im.prod(x.real, y.imag)
                 im.prod(x.imag, y.real)
-                re.l = F(re.l + F(F(F(xe.real * y.real) - F(xe.imag * y.imag)) + F(F(x.real * ye.real) - F(x.imag * ye.imag))))
-                im.l = F(im.l + F(F(F(xe.real * y.imag) + F(xe.imag * y.real)) + F(F(x.real * ye.imag) + F(x.imag * ye.real))))
+                re.lo(xe.real, y.real)
+                re.lo(-xe.imag, y.imag)
+                re.lo(x.real, ye.real)
+                re.lo(-x.imag, ye.imag)
+                im.lo(xe.real, y.imag)
+                im.lo(xe.imag, y.real)
+                im.lo(x.real, ye.imag)
+                im.lo(x.imag, ye.real)
             W.append(re.result() + im.result())
         for b in range(3):
             re, im = _Acc(), _Acc()
@@ -359,8 +418,10 @@ def _tail_link(gh, gl, U, fh, fl):
                 re.prod_df(wih, wil, f.imag)
                 im.prod_df(wih, wil, f.real)
                 im.prod_df(-wrh, -wrl, f.imag)
-                re.l = F(re.l + F(F(wrh * fe.real) + F(wih * fe.imag)))
-                im.l = F(im.l + F(F(wih * fe.real) - F(wrh * fe.imag)))
+                re.lo(wrh, fe.real)
+                re.lo(wih, fe.imag)
+                im.lo(wih, fe.real)
+                im.lo(-wrh, fe.imag)
             rh, rl = re.result()
             ih, il = im.result()
             out[a, b] = (np.float64(rh) + np.float64(rl)) + 1j * (np.float64(ih) + np.float64(il))
