@@ -14,6 +14,16 @@ fixed to theta < 1e-15 (FP32 phase + an FP64-accurate double-float tail):
 fix through the public API from pinned host links, with the host<->device
 copies inside the timed region.
 
+On one GPU the default run adds the metric's comparison arms under ``arms``
+(``--arms`` selects them): the same 32^4 input fixed by the plain FP64
+method (site-iterations/s, time to theta < 1e-15 and its ratio to the mixed
+path), the FP32 step with g reunitarised in FP64, the 48^3 x 8 and 48^3 x 12
+12-real lattices with per-kernel GB/s, the 64-lattice mixed batch, the
+learned warm start (trained on the GPU, then iterations and time to theta
+with and without it), and the oracle on all host cores and on one
+(``nproc``/``lscpu`` recorded).  ``cpu_baseline`` is the oracle on all host
+cores on the headline input.
+
 --impl reference times the CPU oracle (numpy FP64, naive DFT) instead.
 One JSON line on stdout (rank 0).
 """
@@ -182,28 +192,78 @@ sys.path.insert(0, sys.argv[1])
 import numpy as np
 from oracle import lgf_oracle as O
 U = np.load(sys.argv[2])
-n = int(sys.argv[3]); alpha = float(sys.argv[4])
+mode = sys.argv[3]; n = int(sys.argv[4]); alpha = float(sys.argv[5])
 t = time.perf_counter()
-O.iterate(U, n, alpha)
-print(json.dumps({"seconds": time.perf_counter() - t, "iterations": n}))
+if mode == "iterate":
+    O.iterate(U, n, alpha)
+    out = {"iterations": n}
+else:
+    r = O.fix(U, float(sys.argv[6]), n, alpha)
+    out = {"iterations": r["iterations"], "F": r["F"], "theta": r["theta"], "converged": bool(r["converged"])}
+out["seconds"] = time.perf_counter() - t
+print(json.dumps(out))
 """
 
-ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
-              "NUMEXPR_NUM_THREADS": "1"}
+
+def thread_env(threads: int) -> dict:
+    t = str(int(threads))
+    return {"OMP_NUM_THREADS": t, "OPENBLAS_NUM_THREADS": t, "MKL_NUM_THREADS": t, "NUMEXPR_NUM_THREADS": t}
 
 
-def time_oracle(U, n: int, alpha: float) -> float:
-    """Seconds for n oracle iterations on U, in a 1-thread child process."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def host_cpu_info() -> dict:
+    """nproc and the lscpu lines that name the host CPU."""
+    info = {"nproc": host_cores()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            k = k.strip()
+            if k in ("Architecture", "CPU(s)", "Model name", "Thread(s) per core", "Core(s) per socket",
+                     "Socket(s)", "CPU max MHz"):
+                info[k] = v.strip()
+    except Exception as e:
+        info["lscpu"] = f"unavailable: {e}"
+    return info
+
+
+def run_oracle(U, mode: str, n: int, alpha: float, threads: int = 1, tol: float = 0.0) -> dict:
+    """The oracle as it stands on U in a child process with `threads` BLAS /
+    OpenMP threads: n iterations (mode 'iterate') or a fix to theta < tol
+    with at most n updates (mode 'fix')."""
     import numpy as np
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "U.npy")
         np.save(path, U)
-        env = dict(os.environ, **ONE_THREAD)
-        r = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path, str(n), str(alpha)],
+        env = dict(os.environ, **thread_env(threads))
+        r = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path, mode, str(n), str(alpha), str(tol)],
                            capture_output=True, text=True, env=env, timeout=1800)
         if r.returncode != 0:
             raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
-        return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def time_oracle(U, n: int, alpha: float, threads: int = 1) -> float:
+    """Seconds for n oracle iterations on U (child process, `threads` threads)."""
+    return run_oracle(U, "iterate", n, alpha, threads)["seconds"]
+
+
+GOLDEN_FIX = os.path.join(ROOT, "tests", "golden", "fullsize_fix.json")
+
+
+def oracle_fix_iterations(case: str):
+    """Updates the oracle's own fix of a full-size case needs (stored by the
+    committed script that calls only the oracle), or None."""
+    try:
+        return json.load(open(GOLDEN_FIX))["cases"][case]["iterations"]
+    except Exception:
+        return None
 
 
 # ---------------------------------------------------------------------------
@@ -282,11 +342,281 @@ class Replicas:
             self._dist.destroy_process_group()
 
 
+def main_config(W, world: int, gauge_rep: bool) -> dict:
+    """The `config` object of the single-lattice workloads; the reference arm
+    prints the same one."""
+    prec = 4 if W["dtype"].startswith("f32") else 8
+    r = 12 if W["dtype"].endswith("r12") else 18
+    V = 1
+    for d in W["dims"]:
+        V *= d
+    return {"workload": W["desc"], "lattice": list(W["dims"]), "storage": W["dtype"], "alpha": W["alpha"],
+            "link_update": ("gauge representation: U0 fixed, G <- g G, links formed on the fly"
+                            if gauge_rep else "links updated in place"),
+            "link_scale": W["link_scale"], "gauge_scale": W["gauge_scale"], "seed": W["seed"],
+            "l2": f"inputs larger than L2: links {4 * r * prec * V / 1e6:.0f} MB per sweep",
+            "parallelism": f"replicas x{world} (independent configs, no collective on the data path)"}
+
+
+def kernel_table(prof: dict, steps: int, V: int, prec: int, r: int, gauge_rep: bool) -> dict:
+    """Per-kernel launches, time, share and algorithmic GB/s from lgf_profile."""
+    total = sum(v[0] for v in prof.values()) or 1.0
+    out = {}
+    for name, (kms, n) in prof.items():
+        if n == 0 or name == "other":
+            continue
+        per = kms / n
+        b = bytes_per_site(name, prec, r, gauge_rep) * V
+        out[name] = {"launches": n, "ms_per_launch": round(per, 5), "share": round(kms / total, 4),
+                     "algorithmic_gbs": round(b / (per * 1e-3) / 1e9, 1) if b else None}
+    return out
+
+
+def measure_handle(torch, gf, stream, Ud, W, steps: int, warmup: int, V: int, gauge_rep: bool) -> dict:
+    """Site-iterations/s of `steps` iterations (CUDA events on the handle's
+    stream, after `warmup`), per-kernel times from a second, profiled pass,
+    and the time to theta < tol from device-resident links (after one
+    untimed fix that builds the handle's loop graphs)."""
+    prec = 4 if W["dtype"].startswith("f32") else 8
+    r = 12 if W["dtype"].endswith("r12") else 18
+    gf.load_links(Ud)
+    gf.iterate(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gf.iterate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    gf.profile(True)
+    gf.iterate(steps)
+    torch.cuda.synchronize()
+    prof = gf.profile_read()
+    gf.profile(False)
+    gf.load_links(Ud)
+    gf.fix(W["tol"], W["max_iter"])
+    gf.load_links(Ud)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    iters, conv = gf.fix(W["tol"], W["max_iter"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fix_s = e0.elapsed_time(e1) / 1e3
+    F, theta = gf.functional()
+    return {"value": round(V * steps / (ms / 1e3), 1), "unit": METRIC, "ms_per_step": round(ms / steps, 5),
+            "steps": steps, "kernels": kernel_table(prof, steps, V, prec, r, gauge_rep),
+            "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 5), "iterations": iters,
+                              "fp32_iterations": gf.fix_split()[0], "fp64_iterations": gf.fix_split()[1],
+                              "converged": conv, "F": F, "theta": theta}}
+
+
+def arm_single(lgf, torch, W, steps: int, warmup: int, params=(), Ud=None) -> dict:
+    """One single-lattice workload W measured by measure_handle (its input
+    generated on the GPU unless given)."""
+    from lgf_inputs import torch_gen
+    dims = W["dims"]
+    V = 1
+    for d in dims:
+        V *= d
+    if Ud is None:
+        Ud = torch_gen.synthetic_config(dims, seed=W["seed"], link_scale=W["link_scale"],
+                                        gauge_scale=W["gauge_scale"], device="cuda")
+    stream = torch.cuda.Stream()
+    gauge_rep = W["dtype"].startswith("f32")
+    with lgf.GaugeFixer(dims, W["dtype"], stream=stream, alpha=W["alpha"]) as gf:
+        for k, v in params:
+            gf.set_param(k, v)
+        out = measure_handle(torch, gf, stream, Ud, W, steps, warmup, V, gauge_rep)
+    out["workload"] = W["desc"]
+    return out
+
+
+def batch_measure(lgf, torch, W, steps: int, warmup: int, lanes_arg: int = -1) -> dict:
+    """The batched workload (lgf_batch): site-iterations/s over all members,
+    the time to fix all of them, and the step-level roofline."""
+    import numpy as np
+    from lgf_inputs import torch_gen
+
+    n = W["batch"]
+    shapes = [BATCH_SHAPES[i % len(BATCH_SHAPES)] for i in range(n)]
+    t = time.time()
+    inputs = [torch_gen.synthetic_config(shapes[i], seed=W["seed"] + i, link_scale=W["link_scale"],
+                                         gauge_scale=W["gauge_scale"], device="cuda") for i in range(n)]
+    torch.cuda.synchronize()
+    log(f"generated {n} configs ({sum(int(np.prod(s)) for s in shapes)} sites) on the GPU in {time.time() - t:.1f}s")
+    fixers = [lgf.GaugeFixer(shapes[i], W["dtype"], alpha=W["alpha"]) for i in range(n)]
+    try:
+        for f, u in zip(fixers, inputs):
+            f.load_links(u)
+        tuned = {}
+        for f, s in zip(fixers, shapes):
+            ch = f.autotune(reps=5)
+            tuned.setdefault("x".join(map(str, s)), ch)
+        Vtot = sum(int(np.prod(s)) for s in shapes)
+        with lgf.GaugeBatch(fixers) as batch:
+            lanes = lanes_arg
+            if lanes >= 0:
+                batch.set_lanes(lanes)
+            else:
+                lanes = batch.autotune(reps=4)
+            batch.iterate(warmup)
+            torch.cuda.synchronize()
+            l0 = sum(f.launch_count() for f in fixers)
+            w0 = time.time()
+            t0 = time.perf_counter()
+            batch.iterate(steps)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            w1 = time.time()
+            launches = sum(f.launch_count() for f in fixers) - l0
+            for f, u in zip(fixers, inputs):
+                f.load_links(u)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its, conv = batch.fix(W["tol"], W["max_iter"])
+            fix_s = time.perf_counter() - t0
+            thetas = [f.functional()[1] for f in fixers]
+    finally:
+        for f in fixers:
+            f.close()
+    pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    # gauge representation, FP32 18-real, every batch shape on the fused path:
+    # gradient 392, forward x-y 64, z-t 64, inverse x-y + G update 176 bytes/site
+    step_bytes = (bytes_per_site("gradient", 4, 18, True) + 2 * bytes_per_site("fft_xy", 4, 18)
+                  + bytes_per_site("xy_gstep", 4, 18, True))
+    value = Vtot * steps / secs
+    return {"value": round(value, 1), "unit": METRIC, "ms_per_step": round(secs / steps * 1e3, 5), "steps": steps,
+            "members": n, "sites": Vtot, "fft_pipeline_per_shape": tuned,
+            "graph_lanes": lanes if lanes_arg >= 0 else f"{lanes} (autotuned; 0 = one per member)",
+            "timing": "host wall clock around the synchronous lgf_batch_iterate: one graph launch, every member "
+                      "looping on the device",
+            "roofline": {"bound": "hbm", "kernel": "whole step (graph-launched; per-kernel events are not "
+                                                   "recorded inside graphs)",
+                         "achieved": round(step_bytes * value / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(step_bytes * value / 1e9 / hbm_peak, 4), "traffic": None,
+                         "algorithmic_bytes_per_site": step_bytes},
+            "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 4), "all_converged": all(conv),
+                              "iterations_min": min(its), "iterations_max": max(its),
+                              "iterations_mean": round(sum(its) / len(its), 2), "theta_max": max(thetas)},
+            "gpu_launches": launches, "_window": (w0, w1)}
+
+
+def warm_measure(lgf, torch, W, ntr: int) -> dict:
+    """Train the warm-start network on the GPU, then fix unseen larger
+    configurations with and without it."""
+    import numpy as np
+    from lgf_inputs import torch_gen
+
+    net = lgf.WarmStartNet(seed=0)
+    gf = lgf.GaugeFixer(W["train_dims"], W["dtype"], alpha=W["alpha"])
+    F_first, F_last = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    for ep in range(W["epochs"]):
+        for k in range(ntr):
+            u = torch_gen.synthetic_config(W["train_dims"], seed=W["train_seed"] + k, link_scale=W["link_scale"],
+                                           gauge_scale=W["gauge_scale"], device="cuda")
+            gf.load_links(u)
+            F, _ = net.train_step(gf, W["lr"])
+            steps += 1
+            (F_first if k < 16 and ep == 0 else F_last if k >= ntr - 16 else []).append(F)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    gf.close()
+    ge = lgf.GaugeFixer(W["eval_dims"], W["dtype"], alpha=W["alpha"])
+    # one untimed fix first: it builds the handle's loop graphs, which both
+    # timed arms then share
+    ge.load_links(torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] - 1, link_scale=W["link_scale"],
+                                             gauge_scale=W["gauge_scale"], device="cuda"))
+    ge.fix(W["tol"], W["max_iter"])
+    rows = []
+    for k in range(W["eval_n"]):
+        u = torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] + k, link_scale=W["link_scale"],
+                                       gauge_scale=W["gauge_scale"], device="cuda")
+        ge.load_links(u)
+        F0 = ge.functional()[0]
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        it_p, cp = ge.fix(W["tol"], W["max_iter"])
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - a
+        Fp = ge.functional()[0]
+        ge.load_links(u)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        net.warm_start(ge)
+        torch.cuda.synchronize()
+        tw0 = time.perf_counter() - a
+        Fw0 = ge.functional()[0]
+        a = time.perf_counter()
+        it_w, cw = ge.fix(W["tol"], W["max_iter"])
+        torch.cuda.synchronize()
+        tw = time.perf_counter() - a + tw0
+        Fw, thw = ge.functional()
+        rows.append(dict(F_start=F0, F_warm_start=Fw0, it_plain=it_p, it_warm=it_w, t_plain=tp, t_warm=tw,
+                         t_inference=tw0, F_plain=Fp, F_warm=Fw, converged=bool(cp and cw),
+                         same_copy=bool(abs(Fw - Fp) <= 1e-12 * abs(Fp))))
+    ge.close()
+    net.close()
+    Ve = int(np.prod(W["eval_dims"]))
+    mean = lambda key: float(np.mean([r[key] for r in rows]))
+    it_p, it_w = mean("it_plain"), mean("it_warm")
+    return {
+        "value": round(Ve * it_w / mean("t_warm"), 1), "unit": METRIC, "train_steps": steps,
+        "ms_per_train_step": round(train_s / max(steps, 1) * 1e3, 4),
+        "config": {"workload": W["desc"], "train_lattice": list(W["train_dims"]), "train_configs": ntr,
+                   "epochs": W["epochs"], "lr": W["lr"], "eval_lattice": list(W["eval_dims"]),
+                   "eval_configs": W["eval_n"]},
+        "training": {"seconds": round(train_s, 2), "train_steps": steps,
+                     "mean_F_warm_first16": round(float(np.mean(F_first)), 6) if F_first else None,
+                     "mean_F_warm_last16": round(float(np.mean(F_last)), 6) if F_last else None},
+        "evaluation": {"iterations_plain": it_p, "iterations_warm": it_w,
+                       "iteration_gain": round(it_p - it_w, 3),
+                       "seconds_plain": round(mean("t_plain"), 5), "seconds_warm": round(mean("t_warm"), 5),
+                       "seconds_inference": round(mean("t_inference"), 5),
+                       "F_before": mean("F_start"), "F_after_warm_start": mean("F_warm_start"),
+                       "all_converged": all(r["converged"] for r in rows),
+                       "same_gribov_copy": sum(r["same_copy"] for r in rows), "per_config": rows},
+    }
+
+
+def oracle_arms(U_c2, U_c3, alpha: float) -> dict:
+    """The oracle as it stands on the host's cores, all of them and one:
+    seconds per iteration on the 32^4 and 48^3 x 8 inputs (a bounded sample
+    of iterations each) and the whole fix of the 8^4 FP64 input; for the
+    large inputs the time to theta is projected as seconds per iteration x
+    the updates the oracle's own fix needs (stored by the committed script
+    that runs only the oracle)."""
+    import lgf_inputs
+    info = host_cpu_info()
+    cores = info["nproc"]
+    U_c1 = lgf_inputs.synthetic_config((8, 8, 8, 8), seed=0, link_scale=0.3, gauge_scale=1.0)
+    out = {"host": info, "kind": "oracle (numpy FP64, naive separable DFT of all nine entries)", "configs": {}}
+    for threads in sorted({cores, 1}, reverse=True):
+        key = f"{threads}_threads"
+        r = run_oracle(U_c1, "fix", 2000, alpha, threads, tol=1e-12)
+        out["configs"].setdefault("8^4 FP64 theta<1e-12", {})[key] = {
+            "iterations": r["iterations"], "seconds_to_theta": round(r["seconds"], 3),
+            "seconds_per_iteration": round(r["seconds"] / max(r["iterations"], 1), 5), "F": r["F"]}
+        for name, U, case in (("32^4 theta<1e-15", U_c2, "32^4"), ("48^3x8 theta<1e-15", U_c3, "48^3x8")):
+            n = 2
+            secs = time_oracle(U, n, alpha, threads)
+            its = oracle_fix_iterations(case)
+            rec = {"sample": f"{n} iterations", "seconds_per_iteration": round(secs / n, 4),
+                   "site_iterations_per_s": round(U.size // 36 * n / secs, 1)}
+            if its is not None:
+                rec["oracle_iterations_to_theta"] = its
+                rec["projected_seconds_to_theta"] = round(secs / n * its, 2)
+            out["configs"].setdefault(name, {})[key] = rec
+    return out
+
+
 def run_ours(args, W):
     import numpy as np
     import torch
 
-    import lgf_inputs
     import paper_1208_1186_gb300 as lgf
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -411,15 +741,7 @@ def run_ours(args, W):
     r = 12 if W["dtype"].endswith("r12") else 18
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
-    kernels = {}
-    for name, (kms, n) in prof.items():
-        if n == 0 or name in ("other",):
-            continue
-        per_launch_ms = kms / n
-        b = bytes_per_site(name, prec, r, gauge_rep) * V
-        kernels[name] = {"launches": n, "ms_per_launch": round(per_launch_ms, 5),
-                         "share": round(kms / sum(v[0] for v in prof.values()), 4),
-                         "algorithmic_gbs": round(b / (per_launch_ms * 1e-3) / 1e9, 1) if b else None}
+    kernels = kernel_table(prof, args.steps, V, prec, r, gauge_rep)
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     ach = kernels[dom]["algorithmic_gbs"]
     step_bytes = sum(bytes_per_site(k, prec, r, gauge_rep) * kernels[k]["launches"] / args.steps
@@ -440,12 +762,7 @@ def run_ours(args, W):
         "vs_baseline": None,
         "dtype": "f32" if prec == 4 else "f64",
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
-        "config": {"workload": W["desc"], "lattice": list(dims), "storage": W["dtype"], "alpha": W["alpha"],
-                   "link_update": ("gauge representation: U0 fixed, G <- g G, links formed on the fly"
-                                   if gauge_rep else "links updated in place"),
-                   "link_scale": W["link_scale"], "gauge_scale": W["gauge_scale"], "seed": W["seed"],
-                   "l2": f"inputs larger than L2: links {4 * r * prec * V / 1e6:.0f} MB per sweep",
-                   "parallelism": f"replicas x{world} (independent configs, no collective on the data path)"},
+        "config": main_config(W, world, gauge_rep),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(ach / hbm_peak, 4) if ach else None,
                      "traffic": profile_traffic(dom, args.workload, gauge_rep),
@@ -457,7 +774,7 @@ def run_ours(args, W):
         "kernel_timing": {"how": "CUDA events around each launch on the launch stream, in a second pass of the "
                                  "same K steps right after the timed pass",
                           "ms_per_step_with_kernel_events": round(ms_prof / args.steps, 5)},
-        "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 4), "iterations": iters,
+        "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 5), "iterations": iters,
                           "fp32_iterations": split[0], "fp64_iterations": split[1], "converged": conv,
                           "F": F, "theta": theta,
                           "kernel_ms_profiled_run": fix_prof, "kernel_launches_profiled_run": fix_launches},
@@ -469,207 +786,146 @@ def run_ours(args, W):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    arms = set(args.arms.split(",")) if args.arms not in ("", "none") else set()
+    if "all" in arms:
+        arms = set(ARMS)
+    if world == 1 and arms and args.workload == DEFAULT_WORKLOAD:
+        line["arms"] = run_arms(args, lgf, torch, W, Ud, U, line, arms)
     if not args.no_cpu_baseline:
         n = args.cpu_iters
-        log(f"timing {n} oracle iteration(s) on the same {dims} input, 1 thread ...")
-        secs = time_oracle(U, n, W["alpha"])
-        line["cpu_baseline"] = {"value": round(V * n / secs, 1), "unit": METRIC, "cores": 1, "kind": "oracle",
+        cores = host_cores()
+        log(f"timing {n} oracle iteration(s) on the same {dims} input, {cores} thread(s) ...")
+        secs = time_oracle(U, n, W["alpha"], cores)
+        line["cpu_baseline"] = {"value": round(V * n / secs, 1), "unit": METRIC, "cores": cores, "kind": "oracle",
                                 "sample": f"{n} iteration(s) of the numpy FP64 oracle on the same {dims} input "
-                                          f"({secs:.1f} s, 1 thread)"}
+                                          f"({secs:.1f} s, {cores} BLAS/OpenMP threads = all host cores; "
+                                          f"1-thread figures under arms.cpu_oracle)"}
     rp.close()
     return line
 
 
+ARMS = ("plain_fp64", "reunit_fp64", "c3", "batch", "warm", "cpu_oracle")
+
+
+def run_arms(args, lgf, torch, W, Ud, U, line, arms) -> dict:
+    """The comparison arms of the metric, on rank 0 of a 1-GPU run: the same
+    32^4 input fixed by the plain FP64 method, the FP32 step with FP64
+    reunitarisation, the 48^3 x Nt 12-real lattices, the 64-lattice batch,
+    the learned warm start, and the oracle on the host's cores."""
+    out = {}
+    t_start = time.time()
+    mixed_s = line["time_to_theta"]["seconds"]
+    if "plain_fp64" in arms:
+        log("arm: plain FP64 on the same 32^4 input ...")
+        Wf = dict(W, dtype="f64", desc="the same 32^4 input, plain FP64 (links, FFT, update) to theta<1e-15")
+        a = arm_single(lgf, torch, Wf, args.steps, args.warmup, Ud=Ud)
+        tt = a["time_to_theta"]
+        a["vs_mixed"] = {"time_to_theta_ratio_fp64_over_mixed": round(tt["seconds"] / mixed_s, 3),
+                         "site_it_ratio_mixed_over_fp64": round(line["value"] / a["value"], 3),
+                         "F_rel_diff_mixed_vs_fp64": abs(line["time_to_theta"]["F"] - tt["F"]) / abs(tt["F"])}
+        out["plain_fp64_32^4"] = a
+    if "reunit_fp64" in arms:
+        log("arm: FP32 step with g reunitarised in FP64 ...")
+        Wr = dict(W, desc="the same 32^4 input, FP32 storage with g reunitarised in FP64 arithmetic "
+                          "(LGF_REUNIT_FP64=1)")
+        out["reunit_fp64_32^4"] = arm_single(lgf, torch, Wr, args.steps, args.warmup, params=((4, 1),), Ud=Ud)
+    U_c3 = None
+    if "c3" in arms:
+        for lt in (8, 12):
+            log(f"arm: 48^3x{lt} 12-real ...")
+            Wc = dict(WORKLOADS["48^3x8-f32r12"], dims=(48, 48, 48, lt),
+                      desc=f"48^3x{lt} single config, FP32 12-real links, FP64 tail to theta<1e-15, link scale 0.6")
+            from lgf_inputs import torch_gen
+            Uc = torch_gen.synthetic_config(Wc["dims"], seed=0, link_scale=0.6, gauge_scale=1.0, device="cuda")
+            if lt == 8:
+                U_c3 = Uc.cpu().numpy()
+            out[f"48^3x{lt}-f32r12"] = arm_single(lgf, torch, Wc, args.steps, args.warmup, Ud=Uc)
+            del Uc
+    if "batch" in arms:
+        log("arm: batch of 64 mixed lattices ...")
+        b = batch_measure(lgf, torch, WORKLOADS["batch64-f32"], args.steps, args.warmup)
+        b.pop("_window", None)
+        out["batch64-f32"] = b
+    if "warm" in arms:
+        log("arm: learned warm start (training on the GPU, evaluation on 24^4) ...")
+        Ww = WORKLOADS["warmstart-f32"]
+        out["warmstart-f32"] = warm_measure(lgf, torch, Ww, Ww["train_n"])
+    torch.cuda.synchronize()
+    if "cpu_oracle" in arms:
+        if U_c3 is None:
+            from lgf_inputs import torch_gen
+            U_c3 = torch_gen.synthetic_config((48, 48, 48, 8), seed=0, link_scale=0.6, gauge_scale=1.0,
+                                              device="cuda").cpu().numpy()
+        log("arm: the oracle on all host cores and on one ...")
+        out["cpu_oracle"] = oracle_arms(U, U_c3, W["alpha"])
+    out["seconds"] = round(time.time() - t_start, 1)
+    return out
+
+
 def run_batch(args, W):
-    """Batched workload on one GPU (lgf_batch): site-iterations/s over all
-    members and the time to fix all of them."""
-    import numpy as np
+    """Batched workload on one GPU (lgf_batch) as its own bench line."""
     import torch
 
     import paper_1208_1186_gb300 as lgf
-    from lgf_inputs import torch_gen
 
     torch.cuda.set_device(0)
-    n = W["batch"]
-    shapes = [BATCH_SHAPES[i % len(BATCH_SHAPES)] for i in range(n)]
-    t = time.time()
-    inputs = [torch_gen.synthetic_config(shapes[i], seed=W["seed"] + i, link_scale=W["link_scale"],
-                                         gauge_scale=W["gauge_scale"], device="cuda") for i in range(n)]
-    torch.cuda.synchronize()
-    log(f"generated {n} configs ({sum(int(np.prod(s)) for s in shapes)} sites) on the GPU in {time.time() - t:.1f}s")
-    fixers = [lgf.GaugeFixer(shapes[i], W["dtype"], alpha=W["alpha"]) for i in range(n)]
-    for f, u in zip(fixers, inputs):
-        f.load_links(u)
-    tuned = {}
-    for f, s in zip(fixers, shapes):
-        ch = f.autotune(reps=5)
-        tuned.setdefault("x".join(map(str, s)), ch)
-    Vtot = sum(int(np.prod(s)) for s in shapes)
     smi = ClockSampler(gpu_id_for_smi(torch))
-    batch = lgf.GaugeBatch(fixers)
-    lanes = args.lanes
-    if lanes >= 0:
-        batch.set_lanes(lanes)
-    else:
-        lanes = batch.autotune(reps=4)
     try:
-        batch.iterate(args.warmup)
-        torch.cuda.synchronize()
-        l0 = sum(f.launch_count() for f in fixers)
-        w0 = time.time()
-        t0 = time.perf_counter()
-        batch.iterate(args.steps)
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-        w1 = time.time()
-        launches = sum(f.launch_count() for f in fixers) - l0
-        for f, u in zip(fixers, inputs):
-            f.load_links(u)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its, conv = batch.fix(W["tol"], W["max_iter"])
-        fix_s = time.perf_counter() - t0
-        thetas = [f.functional()[1] for f in fixers]
+        b = batch_measure(lgf, torch, W, args.steps, args.warmup, args.lanes)
     finally:
         smi.stop()
-        batch.close()
-    clocks = smi.summary(w0, w1)
-    for f in fixers:
-        f.close()
-    pk = peaks()
-    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
-    # gauge representation, FP32 18-real, every batch shape on the fused path:
-    # gradient 392, forward x-y 64, z-t 64, inverse x-y + G update 176 bytes/site
-    step_bytes = (bytes_per_site("gradient", 4, 18, True) + 2 * bytes_per_site("fft_xy", 4, 18)
-                  + bytes_per_site("xy_gstep", 4, 18, True))
-    value = Vtot * args.steps / secs
+    w0, w1 = b.pop("_window")
     return {
-        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 5), "higher_is_better": True,
+        "metric": METRIC, "value": b["value"], "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
-        "config": {"workload": W["desc"], "members": n, "sites": Vtot, "storage": W["dtype"],
-                   "fft_pipeline_per_shape": tuned, "graph_lanes": lanes if args.lanes >= 0 else f"{lanes} (autotuned; 0 = one per member)",
-                   "timing": "host wall clock around the synchronous lgf_batch_iterate: one graph launch, every member looping on the device"},
-        "roofline": {"bound": "hbm", "kernel": "whole step (graph-launched; per-kernel events are not recorded "
-                                                "inside graphs)",
-                     "achieved": round(step_bytes * value / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(step_bytes * value / 1e9 / hbm_peak, 4), "traffic": None,
-                     "algorithmic_bytes_per_site": step_bytes},
-        "time_to_theta": {"theta_tol": W["tol"], "seconds": round(fix_s, 4), "all_converged": all(conv),
-                          "iterations_min": min(its), "iterations_max": max(its),
-                          "iterations_mean": round(sum(its) / len(its), 2), "theta_max": max(thetas)},
+        "config": {"workload": W["desc"], "members": b["members"], "sites": b["sites"], "storage": W["dtype"],
+                   "fft_pipeline_per_shape": b["fft_pipeline_per_shape"], "graph_lanes": b["graph_lanes"],
+                   "timing": b["timing"]},
+        "roofline": b["roofline"], "time_to_theta": b["time_to_theta"],
         "e2e": None,
         "e2e_note": "batched workload: inputs generated and kept on the device; see the 32^4 line for e2e",
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "gpu_launches": b["gpu_launches"],
+        "clocks": smi.summary(w0, w1),
     }
 
 
 def run_warm(args, W):
-    """C5: train the warm-start network on the GPU, then compare fixes of
-    unseen larger configurations with and without it."""
-    import numpy as np
+    """C5 as its own bench line."""
     import torch
 
     import paper_1208_1186_gb300 as lgf
-    from lgf_inputs import torch_gen
 
     torch.cuda.set_device(0)
     ntr = args.train_n if args.train_n else W["train_n"]
-    net = lgf.WarmStartNet(seed=0)
-    gf = lgf.GaugeFixer(W["train_dims"], W["dtype"], alpha=W["alpha"])
-    Vt = int(np.prod(W["train_dims"]))
-    F_first, F_last = [], []
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    steps = 0
-    for ep in range(W["epochs"]):
-        for k in range(ntr):
-            u = torch_gen.synthetic_config(W["train_dims"], seed=W["train_seed"] + k, link_scale=W["link_scale"],
-                                           gauge_scale=W["gauge_scale"], device="cuda")
-            gf.load_links(u)
-            F, _ = net.train_step(gf, W["lr"])
-            steps += 1
-            (F_first if k < 16 and ep == 0 else F_last if k >= ntr - 16 else []).append(F)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    gf.close()
-    # evaluation on unseen configurations of another size
-    ge = lgf.GaugeFixer(W["eval_dims"], W["dtype"], alpha=W["alpha"])
-    # one untimed fix first: it builds the handle's loop graphs, which both
-    # timed arms then share
-    ge.load_links(torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] - 1, link_scale=W["link_scale"],
-                                             gauge_scale=W["gauge_scale"], device="cuda"))
-    ge.fix(W["tol"], W["max_iter"])
-    rows = []
-    for k in range(W["eval_n"]):
-        u = torch_gen.synthetic_config(W["eval_dims"], seed=W["eval_seed"] + k, link_scale=W["link_scale"],
-                                       gauge_scale=W["gauge_scale"], device="cuda")
-        ge.load_links(u)
-        F0 = ge.functional()[0]
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        it_p, cp = ge.fix(W["tol"], W["max_iter"])
-        torch.cuda.synchronize()
-        tp = time.perf_counter() - a
-        Fp = ge.functional()[0]
-        ge.load_links(u)
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        net.warm_start(ge)
-        torch.cuda.synchronize()
-        tw0 = time.perf_counter() - a
-        Fw0 = ge.functional()[0]
-        a = time.perf_counter()
-        it_w, cw = ge.fix(W["tol"], W["max_iter"])
-        torch.cuda.synchronize()
-        tw = time.perf_counter() - a + tw0
-        Fw, thw = ge.functional()
-        rows.append(dict(F_start=F0, F_warm_start=Fw0, it_plain=it_p, it_warm=it_w, t_plain=tp, t_warm=tw,
-                         t_inference=tw0, F_plain=Fp, F_warm=Fw, converged=bool(cp and cw),
-                         same_copy=bool(abs(Fw - Fp) <= 1e-12 * abs(Fp))))
-    ge.close()
-    net.close()
-    Ve = int(np.prod(W["eval_dims"]))
-    mean = lambda key: float(np.mean([r[key] for r in rows]))
-    it_p, it_w = mean("it_plain"), mean("it_warm")
+    w = warm_measure(lgf, torch, W, ntr)
     return {
-        "metric": METRIC, "value": round(Ve * it_w / mean("t_warm"), 1), "unit": METRIC, "n_gpus": 1,
-        "steps": steps, "warmup": 0, "ms_per_step": round(train_s / max(steps, 1) * 1e3, 4),
+        "metric": METRIC, "value": w["value"], "unit": METRIC, "n_gpus": 1,
+        "steps": w["train_steps"], "warmup": 0, "ms_per_step": w["ms_per_train_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
-        "config": {"workload": W["desc"], "train_lattice": list(W["train_dims"]), "train_configs": ntr,
-                   "epochs": W["epochs"], "lr": W["lr"], "eval_lattice": list(W["eval_dims"]),
-                   "eval_configs": W["eval_n"]},
-        "training": {"seconds": round(train_s, 2), "train_steps": steps,
-                     "mean_F_warm_first16": round(float(np.mean(F_first)), 6) if F_first else None,
-                     "mean_F_warm_last16": round(float(np.mean(F_last)), 6) if F_last else None},
-        "evaluation": {"iterations_plain": it_p, "iterations_warm": it_w,
-                       "iteration_gain": round(it_p - it_w, 3),
-                       "seconds_plain": round(mean("t_plain"), 5), "seconds_warm": round(mean("t_warm"), 5),
-                       "seconds_inference": round(mean("t_inference"), 5),
-                       "F_before": mean("F_start"), "F_after_warm_start": mean("F_warm_start"),
-                       "all_converged": all(r["converged"] for r in rows),
-                       "same_gribov_copy": sum(r["same_copy"] for r in rows), "per_config": rows},
+        "config": w["config"], "training": w["training"], "evaluation": w["evaluation"],
         "e2e": None, "e2e_note": "see the 32^4 line", "roofline": None,
     }
 
 
 def run_reference(args, W):
-    """The oracle as it stands, on host cores, each step a bounded sample."""
+    """The oracle as it stands, on all host cores, each step a bounded sample."""
     import numpy as np
 
     import lgf_inputs
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return None
+    cores = host_cores()
     budget = 150.0 / max(args.steps + args.warmup, 1)  # seconds per step
     # per-site cost model from two small lattices
     probe = {}
     for L in (8, 12):
         U = lgf_inputs.synthetic_config((L,) * 4, seed=W["seed"], link_scale=W["link_scale"])
-        probe[L] = time_oracle(U, 2, W["alpha"]) / 2 / L ** 4
+        probe[L] = time_oracle(U, 2, W["alpha"], cores) / 2 / L ** 4
     slope = (probe[12] - probe[8]) / 4
 
     def est(dims):
@@ -680,19 +936,22 @@ def run_reference(args, W):
     U = lgf_inputs.synthetic_config(dims, seed=W["seed"], link_scale=W["link_scale"],
                                     gauge_scale=W["gauge_scale"])
     V = int(np.prod(dims))
-    time_oracle(U, args.warmup, W["alpha"]) if args.warmup else None
-    secs = time_oracle(U, args.steps, W["alpha"])
+    time_oracle(U, args.warmup, W["alpha"], cores) if args.warmup else None
+    secs = time_oracle(U, args.steps, W["alpha"], cores)
     value = V * args.steps / secs
     sample = (f"{args.steps} oracle iteration(s) on a {dims} lattice of the same recipe"
               + ("" if tuple(dims) == tuple(W["dims"]) else f" (full {W['dims']} does not fit the time budget)")
-              + ", 1 thread")
+              + f", {cores} BLAS/OpenMP threads (all host cores)")
+    gauge_rep = W["dtype"].startswith("f32")
     return {
         "impl": "reference",
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": W["desc"], "lattice": list(W["dims"]), "sample_lattice": list(dims)},
-        "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": main_config(W, world, gauge_rep),
+        "sample_lattice": list(dims),
+        "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": round(value, 1), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -709,6 +968,9 @@ def main():
     ap.add_argument("--train-n", type=int, default=0, help="warm-start workload: training configurations")
     ap.add_argument("--tail-theta", type=float, default=0.0, help="theta at which the FP32 phase hands over")
     ap.add_argument("--lanes", type=int, default=-1, help="batch workload: parallel graph lanes (0: one per member)")
+    ap.add_argument("--arms", default="all",
+                    help="default workload: comparison arms to add, comma-separated from "
+                         + ",".join(ARMS) + ", or 'all' / 'none'")
     ap.add_argument("--link-update", type=int, default=0, choices=[0, 1],
                     help="FP32 storage: 0 gauge representation (default), 1 links updated in place")
     args = ap.parse_args()

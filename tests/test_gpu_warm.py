@@ -142,31 +142,52 @@ def test_training_raises_F(lgf):
     assert max(Fs[-5:]) > F0 + 1e-3
 
 
-def test_warm_started_fix_converges_and_reports_gain(lgf):
+def test_warm_start_cuts_iterations(lgf):
+    """What the trained network gains: trained on 16 configurations of 8^4
+    (8 epochs), it starts unseen 8^4 configurations at a higher F and the
+    warm-started fixes need fewer updates to theta < 1e-15 in total than the
+    plain fixes of the same inputs.  Every fix converges; the final F of each
+    pair is reported with whether the Gribov copy is the same (a different
+    copy is allowed: the plain method is the judge, through theta and F)."""
+    import time
+
+    import torch
     dims = (8, 8, 8, 8)
-    train = [I.synthetic_config(dims, seed=100 + k, link_scale=0.5) for k in range(4)]
-    Ue = I.synthetic_config(dims, seed=200, link_scale=0.5)
+    train = [I.synthetic_config(dims, seed=100 + k, link_scale=0.5) for k in range(16)]
+    evals = [I.synthetic_config(dims, seed=200 + k, link_scale=0.5) for k in range(6)]
     net = lgf.WarmStartNet(seed=5)
+    rows = []
     try:
         with lgf.GaugeFixer(dims, "f32") as gf:
-            for _ in range(10):
+            for _ in range(8):
                 for U in train:
                     gf.load_links(U)
                     net.train_step(gf, 1e-5)
         with lgf.GaugeFixer(dims, "f32") as gf:
-            gf.load_links(Ue)
-            it_plain, conv_p = gf.fix(1e-15, 2000)
-            F_plain = gf.functional()[0]
-            gf.load_links(Ue)
-            net.warm_start(gf)
-            F_start = gf.functional()[0]
-            it_warm, conv_w = gf.fix(1e-15, 2000)
-            F_warm, th = gf.functional()
+            gf.load_links(evals[0])
+            gf.fix(1e-15, 2000)  # builds the handle's loop graphs for both arms
+            for Ue in evals:
+                gf.load_links(Ue)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                it_plain, conv_p = gf.fix(1e-15, 2000)
+                t_plain = time.perf_counter() - t0
+                F_plain = gf.functional()[0]
+                gf.load_links(Ue)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                net.warm_start(gf)
+                F_start = gf.functional()[0]
+                it_warm, conv_w = gf.fix(1e-15, 2000)
+                t_warm = time.perf_counter() - t0
+                F_warm, th = gf.functional()
+                assert conv_p and conv_w and th < 1e-15
+                assert F_start > O.functional(Ue)[0]
+                rows.append((it_plain, it_warm, t_plain, t_warm, F_plain, F_warm))
     finally:
         net.close()
-    assert conv_p and conv_w and th < 1e-15
-    same_copy = abs(F_warm - F_plain) < 1e-12 * abs(F_plain)
-    print(f"\nwarm start on 8^4: F {O.functional(Ue)[0]:.6f} -> {F_start:.6f} before fixing; "
-          f"iterations plain {it_plain}, warm {it_warm}; final F plain {F_plain:.15f}, "
-          f"warm {F_warm:.15f} ({'same' if same_copy else 'different'} Gribov copy)")
-    assert F_start > O.functional(Ue)[0]
+    for it_p, it_w, t_p, t_w, F_p, F_w in rows:
+        same = abs(F_w - F_p) < 1e-12 * abs(F_p)
+        print(f"\nwarm start on 8^4: iterations plain {it_p}, warm {it_w}; time plain {t_p * 1e3:.2f} ms, "
+              f"warm (with inference) {t_w * 1e3:.2f} ms; {'same' if same else 'different'} Gribov copy")
+    assert sum(r[1] for r in rows) < sum(r[0] for r in rows)
