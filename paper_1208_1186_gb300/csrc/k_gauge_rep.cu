@@ -57,6 +57,60 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
+// The per-site work of k_gradient_grep: Delta(x) stored packed, the F and
+// theta terms added to the thread's compensated sums.
+template <class T, int NC>
+__device__ __forceinline__ void grep_site(const cx<T>* __restrict__ U0, const cx<T>* __restrict__ G,
+                                          cx<T>* __restrict__ D, const Geom& geo, int V, int s, const int c[4],
+                                          T& fs, T& fc, T& ts, T& tc) {
+  M3<T> B, C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) B.e[i][j] = C.e[i][j] = mk<T>(0, 0);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const cx<T>* base = U0 + mu * NC * V;
+    const int st_mu = (int)geo.stride[mu];
+    const int span = (geo.L[mu] - 1) * st_mu;
+    {
+      const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - span;
+      const M3<T> u = load_m3i<T, NC>(base, V, s);
+      const M3<T> gf = load_m3i<T, NC>(G, V, sf);
+      mm_dag_acc(C, u, gf);
+    }
+    {
+      const int sb = c[mu] > 0 ? s - st_mu : s + span;
+      const M3<T> gb = load_m3i<T, NC>(G, V, sb);
+      const M3<T> ub = load_m3i<T, NC>(base, V, sb);
+      mm_acc(B, gb, ub);
+    }
+  }
+  const M3<T> gx = load_m3i<T, NC>(G, V, s);
+  M3<T> Uf, Ub;
+  mm<T, 3>(Uf, gx, C);      // sum of the links leaving x
+  mm_dag<T, 3>(Ub, B, gx);  // sum of the links arriving at x
+  const T fsum = Uf.e[0][0].re + Uf.e[1][1].re + Uf.e[2][2].re;
+  M3<T> A;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A.e[i][j] = Ub.e[i][j] - Uf.e[i][j];
+  const cx<T> d01 = A.e[0][1] - conj(A.e[1][0]);
+  const cx<T> d02 = A.e[0][2] - conj(A.e[2][0]);
+  const cx<T> d12 = A.e[1][2] - conj(A.e[2][1]);
+  const T a0 = 2 * A.e[0][0].im, a1 = 2 * A.e[1][1].im, a2 = 2 * A.e[2][2].im;
+  const T tr = (a0 + a1 + a2) / (T)3;
+  const T i0 = a0 - tr, i1 = a1 - tr, i2 = -(i0 + i1);
+  D[s] = d01;
+  D[V + s] = d02;
+  D[2 * V + s] = d12;
+  D[3 * V + s] = mk<T>(i0, i1);
+  const T tsum = 2 * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
+  kahan_add(fs, fc, fsum);
+  kahan_add(ts, tc, tsum);
+}
+
 template <class T, int NC>
 __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* __restrict__ U0,
                                                                 const cx<T>* __restrict__ G, cx<T>* __restrict__ D,
@@ -66,56 +120,11 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
   if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;  // 36 V < 2^31 for extents <= 64
   T fs = 0, fc = 0, ts = 0, tc = 0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
-    T fsum, tsum;
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
     int c[4];
-    site_coords_i(geo.L, s, c);
-    M3<T> B, C;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) B.e[i][j] = C.e[i][j] = mk<T>(0, 0);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const cx<T>* base = U0 + mu * NC * V;
-      const int st_mu = (int)geo.stride[mu];
-      const int span = (geo.L[mu] - 1) * st_mu;
-      {
-        const int sf = c[mu] < geo.L[mu] - 1 ? s + st_mu : s - span;
-        const M3<T> u = load_m3i<T, NC>(base, V, s);
-        const M3<T> gf = load_m3i<T, NC>(G, V, sf);
-        mm_dag_acc(C, u, gf);
-      }
-      {
-        const int sb = c[mu] > 0 ? s - st_mu : s + span;
-        const M3<T> gb = load_m3i<T, NC>(G, V, sb);
-        const M3<T> ub = load_m3i<T, NC>(base, V, sb);
-        mm_acc(B, gb, ub);
-      }
-    }
-    const M3<T> gx = load_m3i<T, NC>(G, V, s);
-    M3<T> Uf, Ub;
-    mm<T, 3>(Uf, gx, C);      // sum of the links leaving x
-    mm_dag<T, 3>(Ub, B, gx);  // sum of the links arriving at x
-    fsum = Uf.e[0][0].re + Uf.e[1][1].re + Uf.e[2][2].re;
-    M3<T> A;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) A.e[i][j] = Ub.e[i][j] - Uf.e[i][j];
-    const cx<T> d01 = A.e[0][1] - conj(A.e[1][0]);
-    const cx<T> d02 = A.e[0][2] - conj(A.e[2][0]);
-    const cx<T> d12 = A.e[1][2] - conj(A.e[2][1]);
-    const T a0 = 2 * A.e[0][0].im, a1 = 2 * A.e[1][1].im, a2 = 2 * A.e[2][2].im;
-    const T tr = (a0 + a1 + a2) / (T)3;
-    const T i0 = a0 - tr, i1 = a1 - tr, i2 = -(i0 + i1);
-    D[s] = d01;
-    D[V + s] = d02;
-    D[2 * V + s] = d12;
-    D[3 * V + s] = mk<T>(i0, i1);
-    tsum = 2 * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
-    kahan_add(fs, fc, fsum);
-    kahan_add(ts, tc, tsum);
+    site_coords_r(geo, s, c);
+    grep_site<T, NC>(U0, G, D, geo, V, s, c, fs, fc, ts, tc);
   }
   grid_reduce<T>(fs - fc, ts - tc, partial, st, normF, normT, mode);
 }
@@ -192,11 +201,12 @@ cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D,
   const double nF = 1.0 / (12.0 * (double)geo.V), nT = 1.0 / (3.0 * (double)geo.V);
   const int64_t full = (geo.V + kGrepThreads - 1) / kGrepThreads;
   const unsigned nb = (unsigned)(full < 2 * sm_count() ? full : 2 * sm_count());
+  const auto u = static_cast<const cx<float>*>(U0);
+  const auto g = static_cast<const cx<float>*>(G);
+  const auto d = static_cast<cx<float>*>(D);
   if (nc == 9)
-    return launch_pdl(k_gradient_grep<float, 9>, nb, kGrepThreads, 0, s, static_cast<const cx<float>*>(U0),
-                      static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D), partial, geo, st, mode, nF, nT);
-  return launch_pdl(k_gradient_grep<float, 6>, nb, kGrepThreads, 0, s, static_cast<const cx<float>*>(U0),
-                    static_cast<const cx<float>*>(G), static_cast<cx<float>*>(D), partial, geo, st, mode, nF, nT);
+    return launch_pdl(k_gradient_grep<float, 9>, nb, kGrepThreads, 0, s, u, g, d, partial, geo, st, mode, nF, nT);
+  return launch_pdl(k_gradient_grep<float, 6>, nb, kGrepThreads, 0, s, u, g, d, partial, geo, st, mode, nF, nT);
 }
 
 cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,

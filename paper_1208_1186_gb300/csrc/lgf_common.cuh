@@ -242,7 +242,28 @@ struct Geom {
   int L[4];         // Lx, Ly, Lz, Lt
   int64_t stride[4];  // 1, Lx, Lx*Ly, Lx*Ly*Lz
   int64_t V;
+  // ceil(2^32 / L) for L = Lx, Ly, Lz (geom_init_rcp): the quotient s / L is
+  // __umulhi(s, rcp) exactly for 0 <= s < 2^32 / L, i.e. for every site index
+  // of a lattice with extents <= 64 (V <= 2^24 < 2^26)
+  unsigned rcp[3];
 };
+
+inline void geom_init_rcp(Geom& g) {
+  for (int a = 0; a < 3; ++a) g.rcp[a] = 0xFFFFFFFFu / (unsigned)g.L[a] + 1u;
+}
+
+// coordinates of site s by multiply-high reciprocals (three integer
+// multiplies instead of three divisions); needs geom_init_rcp
+__device__ __forceinline__ void site_coords_r(const Geom& g, int s, int c[4]) {
+  const unsigned u = (unsigned)s;
+  const unsigned q0 = __umulhi(u, g.rcp[0]);
+  const unsigned q1 = __umulhi(q0, g.rcp[1]);
+  const unsigned q2 = __umulhi(q1, g.rcp[2]);
+  c[0] = (int)(u - q0 * (unsigned)g.L[0]);
+  c[1] = (int)(q0 - q1 * (unsigned)g.L[1]);
+  c[2] = (int)(q1 - q2 * (unsigned)g.L[2]);
+  c[3] = (int)q2;
+}
 
 __device__ __forceinline__ void site_coords(const Geom& g, int64_t s, int c[4]) {
   int64_t r = s;

@@ -179,6 +179,7 @@ extern "C" int lgf_functional_noalloc(const void* links, int Lx, int Ly, int Lz,
     V *= Ls[a];
   }
   geo.V = V;
+  geom_init_rcp(geo);
   if (V > kNoallocMaxSites)
     return noalloc_fail(LGF_ERR_ARG, "lgf_functional_noalloc: the lattice has " + std::to_string(V) +
                                          " sites; this entry point supports at most " +
