@@ -273,15 +273,49 @@ int lgf_batch_set_lanes(lgf_batch b, int lanes);
  * the members' links (like warm-up iterations) and counted as updates. */
 int lgf_batch_autotune(lgf_batch b, int reps, int* lanes_out);
 
-/* Autotuner: time every FFT pipeline that applies to this lattice (x-y/z-t
- * register planes, per-axis register passes, shared-memory Stockham planes)
- * on each of the handle's engines, reps accelerations each, and use the
- * fastest from now on (unless LGF_FFT_PIPELINE forces one).  Results are
- * cached per (precision, lattice shape) for the process.  *chosen (may be
- * NULL) receives the pipeline of the engine that iterates first (1 Stockham
- * planes, 2 axis passes, 3 register planes).  Overwrites the gradient
- * scratch only; the links are untouched. */
+/* Autotuner: time every FFT schedule that applies to this lattice on each of
+ * the handle's engines, reps Fourier accelerations each, and use the fastest
+ * from now on (unless LGF_FFT_PIPELINE forces a pipeline).  The schedules
+ * are the pipelines (x-y/z-t register planes, per-axis register passes,
+ * shared-memory Stockham planes) and, for the register planes, the x-run
+ * width of the z-t tiles (4 or 8 FP32 complex numbers, 2 or 4 FP64) and
+ * the radix order of the z and t transforms (0: radix 4 first, 32 = 4 4 2;
+ * 1: the same factors reversed, 32 = 2 4 4; FP32 only, where the stages
+ * differ).  The paper (Sec. 2.2) transforms with cuFFT's fixed plans; this
+ * search has no counterpart there.  Results are cached per (precision,
+ * lattice shape) for the process; if the environment variable
+ * LGF_TUNE_CACHE names a file, the cache is written there (JSON) after each
+ * tuning.  *chosen (may be NULL) receives the pipeline of the engine that
+ * iterates first (1 Stockham planes, 2 axis passes, 3 register planes).
+ * Overwrites the gradient scratch only; the links are untouched.  Tile
+ * widths give bit-identical results; radix orders round differently in
+ * FP32 (the fix still ends at the same F to the FP64 tail's accuracy). */
 int lgf_autotune(lgf_handle h, int reps, int* chosen);
+
+/* The FFT schedule engine `engine` (0: the FP64 engine, 1: the FP32 engine of
+ * a mixed handle) uses: pipeline (1, 2, 3), z-t tile width (0 = default) and
+ * radix order.  Any pointer may be NULL. */
+int lgf_tune_schedule(lgf_handle h, int engine, int* pipeline, int* zt_bx, int* zt_ro);
+
+/* Force a schedule on an engine (the values lgf_tune_schedule reports);
+ * LGF_ERR_ARG if it does not apply to the lattice and precision. */
+int lgf_set_schedule(lgf_handle h, int engine, int pipeline, int zt_bx, int zt_ro);
+
+/* The schedule cache as a JSON file: {"lgf_fft_schedules": [ ... ]}, one
+ * object per line, {"prec": bytes per real, "L": [Lx, Ly, Lz, Lt],
+ * "pipeline": p, "zt_bx": b, "zt_ro": r, "ms": per acceleration}.
+ * lgf_tune_load merges a file's valid entries into the process cache
+ * (*n_loaded, may be NULL, receives their count) and from then on
+ * lgf_create gives new handles the cached schedule of their shape; the first
+ * lgf_create of a process loads LGF_TUNE_CACHE this way when it is set.
+ * lgf_tune_save writes the whole cache (through a temporary file, renamed
+ * into place).  lgf_tune_lookup reads one entry (LGF_ERR_ARG if absent);
+ * lgf_tune_clear empties the cache and stops applying it at creation.
+ * Host-only: none of these touch a GPU. */
+int lgf_tune_load(const char* path, int* n_loaded);
+int lgf_tune_save(const char* path);
+int lgf_tune_lookup(int prec_bytes, int Lx, int Ly, int Lz, int Lt, int* pipeline, int* zt_bx, int* zt_ro);
+int lgf_tune_clear(void);
 
 /* ------------------------------------------------------------------------
  * Learned warm start.  A 4D convolutional network (three periodic 3^4-tap
@@ -329,6 +363,22 @@ int lgf_net_train_step(lgf_net n, lgf_handle h, double lr, double* F_out, float*
 /* Install the predicted g0 as the initial gauge transformation of h; call
  * right after lgf_load_links (the following lgf_fix starts from U^{g0}). */
 int lgf_net_warm_start(lgf_net n, lgf_handle h);
+
+/* One convolution layer of the network on caller-held device activations
+ * (bf16, [V][channels], site order as everywhere), with the network's
+ * current weights, on a periodic Lx x Ly x Lz x Lt lattice; queued on
+ * `stream` (NULL: the legacy default stream) and finished before the call
+ * returns.  backward = 0: layer 1 (48 -> 32 channels), 2 (32 -> 32) or 3
+ * (32 -> 16, the last 8 zero-weight padding), bias and (layers 1, 2) ReLU;
+ * out_f32 (may be NULL) also receives the FP32 result [V][out channels].
+ * backward = 1: the data gradient of layer 2 or 3 (in: the gradient with
+ * respect to the layer's output, [V][32] or [V][16]; out: [V][32]), zeroed
+ * where mask (the layer's input activation, may be NULL) is not positive.
+ * The kernels are the tcgen05 implicit GEMMs the network runs on; this entry
+ * point exposes them for testing and reuse.  LGF_ERR_TIMEOUT if a bounded
+ * wait inside a kernel expired. */
+int lgf_net_conv(lgf_net n, int layer, int backward, const void* in, const void* mask, void* out, float* out_f32,
+                 int Lx, int Ly, int Lz, int Lt, void* stream);
 
 /* Text of the last error of a network call (NULL: of lgf_net_create). */
 const char* lgf_net_last_error(lgf_net n);

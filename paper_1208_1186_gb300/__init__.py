@@ -147,12 +147,28 @@ class GaugeFixer:
         return {self.lib.lgf_kernel_name(k).decode(): (float(ms[k]), int(cnt[k])) for k in range(n)}
 
     def autotune(self, reps: int = 10) -> int:
-        """Time the FFT pipelines that apply to this lattice and use the
-        fastest; returns its number (1 Stockham planes, 2 axis passes, 3
-        register planes)."""
+        """Time the FFT schedules that apply to this lattice (pipelines, z-t
+        tile widths, radix orders) and use the fastest; returns the pipeline
+        (1 Stockham planes, 2 axis passes, 3 register planes)."""
         ch = ctypes.c_int(0)
         _lib.check(self.lib.lgf_autotune(self.h, int(reps), ctypes.byref(ch)), "lgf_autotune", self.h)
         return ch.value
+
+    def schedule(self, engine: int | None = None):
+        """(pipeline, z-t tile width, radix order) of an engine (0 FP64, 1 the
+        FP32 engine of a mixed handle; default: the one that iterates first)."""
+        if engine is None:
+            engine = 1 if self.dtype.startswith("f32") else 0
+        p, b, r = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _lib.check(self.lib.lgf_tune_schedule(self.h, int(engine), ctypes.byref(p), ctypes.byref(b), ctypes.byref(r)),
+                   "lgf_tune_schedule", self.h)
+        return p.value, b.value, r.value
+
+    def set_schedule(self, pipeline: int, zt_bx: int = 0, zt_ro: int = 0, engine: int | None = None):
+        if engine is None:
+            engine = 1 if self.dtype.startswith("f32") else 0
+        _lib.check(self.lib.lgf_set_schedule(self.h, int(engine), int(pipeline), int(zt_bx), int(zt_ro)),
+                   "lgf_set_schedule", self.h)
 
 
 class GaugeBatch:
@@ -254,6 +270,21 @@ class WarmStartNet:
         self._check(self.lib.lgf_net_train_step(self.n, gf.h, float(lr), ctypes.byref(F),
                                                 _as_ptr(g) if want_grad else None), "lgf_net_train_step")
         return F.value, g
+
+    def conv(self, layer: int, backward: bool, x, dims, mask=None, out_f32=None):
+        """One layer on device bf16 activations (torch tensors [V][channels]);
+        returns the bf16 output tensor (see lgf_net_conv)."""
+        import torch
+        V = int(np.prod(dims))
+        nout = 32 if (backward or layer < 3) else 16
+        out = torch.empty((V, nout), dtype=torch.bfloat16, device=x.device)
+        st = torch.cuda.current_stream().cuda_stream
+        self._check(self.lib.lgf_net_conv(self.n, int(layer), int(bool(backward)), ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
+                                          ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(out_f32.data_ptr()) if out_f32 is not None else None,
+                                          *[int(d) for d in dims], ctypes.c_void_p(st)), "lgf_net_conv")
+        return out
 
     def warm_start(self, gf: "GaugeFixer"):
         self._check(self.lib.lgf_net_warm_start(self.n, gf.h), "lgf_net_warm_start")

@@ -62,6 +62,12 @@ SIGNATURES = {
     "lgf_batch_set_lanes": (ctypes.c_int, [_P, ctypes.c_int]),
     "lgf_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lgf_autotune": (ctypes.c_int, [_P, ctypes.c_int, _IP]),
+    "lgf_tune_schedule": (ctypes.c_int, [_P, ctypes.c_int, _IP, _IP, _IP]),
+    "lgf_set_schedule": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lgf_tune_load": (ctypes.c_int, [ctypes.c_char_p, _IP]),
+    "lgf_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "lgf_tune_lookup": (ctypes.c_int, [ctypes.c_int] * 5 + [_IP, _IP, _IP]),
+    "lgf_tune_clear": (ctypes.c_int, []),
     "lgf_net_param_count": (ctypes.c_int, []),
     "lgf_net_create": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(_P)]),
     "lgf_net_destroy": (ctypes.c_int, [_P]),
@@ -71,6 +77,7 @@ SIGNATURES = {
     "lgf_net_train_step": (ctypes.c_int, [_P, _P, ctypes.c_double, _DP, _P]),
     "lgf_net_warm_start": (ctypes.c_int, [_P, _P]),
     "lgf_net_last_error": (ctypes.c_char_p, [_P]),
+    "lgf_net_conv": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P] + [ctypes.c_int] * 4 + [_P]),
 }
 LGF_NUM_KERNELS = 10
 

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblgf.so")
-SOURCES = ["k_links.cu", "k_gauge_rep.cu", "k_fft.cu", "k_fft_axis.cu", "k_fft_plane.cu", "k_warm.cu", "k_tail.cu", "lgf_api.cu", "lgf_noalloc.cu"]
+SOURCES = ["k_links.cu", "k_gauge_rep.cu", "k_fft.cu", "k_fft_axis.cu", "k_fft_plane.cu", "k_fft_zt.cu", "k_warm.cu", "k_tail.cu", "lgf_api.cu", "lgf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

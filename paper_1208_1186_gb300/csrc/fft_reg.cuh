@@ -1,6 +1,13 @@
 // In-register FFT of one line of compile-time length L (mixed radix 4, 2, 3,
 // 5), used by the per-axis Fourier-acceleration passes.
 //
+// Radix order RO: 0 takes the radices greedily (4 while 4 divides what is
+// left, then 2, 3, 5: 32 = 4 4 2, 48 = 4 4 3); 1 takes the same factors in
+// the reverse order (32 = 2 4 4, 48 = 3 4 4).  Both are exact transforms of
+// the same line; they differ in which twiddles multiply which stage, hence in
+// instruction count and FP32 rounding, and the autotuner chooses between them
+// per extent.  The digit-reversed output order depends on RO.
+//
 // Forward: decimation in frequency (Sande-Tukey), in place, natural-order
 // input, output in mixed-radix digit-reversed order: after dif<L>, element p
 // holds frequency digit_rev(L, p).  Inverse: decimation in time, the exact
@@ -26,6 +33,31 @@ namespace regfft {
 
 constexpr int next_radix(int n) { return n % 4 == 0 ? 4 : (n % 2 == 0 ? 2 : (n % 3 == 0 ? 3 : 5)); }
 
+// the last radix of n's order-0 factorisation
+constexpr int last_radix0(int n) {
+  int r = 1;
+  while (n > 1) {
+    r = next_radix(n);
+    n /= r;
+  }
+  return r;
+}
+
+// radix of the stage that splits a sub-transform of length n, in order RO
+constexpr int stage_radix(int n, int ro) { return ro == 0 ? next_radix(n) : last_radix0(n); }
+
+// true if the two radix orders give different stage sequences for length L
+constexpr bool orders_differ(int L) {
+  int a = L, b = L;
+  while (a > 1 && b > 1) {
+    const int ra = stage_radix(a, 0), rb = stage_radix(b, 1);
+    if (ra != rb) return true;
+    a /= ra;
+    b /= rb;
+  }
+  return false;
+}
+
 constexpr bool supported(int n) {
   if (n < 2) return false;
   while (n > 1) {
@@ -37,10 +69,10 @@ constexpr bool supported(int n) {
 }
 
 // frequency index held at position p after the forward transform
-constexpr int digit_rev(int L, int p) {
+constexpr int digit_rev(int L, int p, int ro = 0) {
   int k = 0, rem = p, n = L, mult = 1;
   while (n > 1) {
-    const int R = next_radix(n);
+    const int R = stage_radix(n, ro);
     n /= R;
     const int d = rem / n;
     rem %= n;
@@ -136,10 +168,10 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // 4 sin^2(pi k / L) (the lattice momentum squared of one axis), for the
-// frequency k held at position P after the forward transform
-template <int L, int P>
+// frequency k held at position P after the forward transform of order RO
+template <int L, int P, int RO = 0>
 struct MomentumSq {
-  static constexpr double s = turn_cs(digit_rev(L, P), 2 * L, 1);  // sin(2 pi k / (2 L))
+  static constexpr double s = turn_cs(digit_rev(L, P, RO), 2 * L, 1);  // sin(2 pi k / (2 L))
   static constexpr double value = 4.0 * s * s;
 };
 
@@ -189,10 +221,10 @@ __device__ __forceinline__ void dft(cx<T>* v) {
 }
 
 // Forward stages on sub-transforms of length N (called with N = L).
-template <class T, int L, int N>
+template <class T, int L, int N, int RO>
 __device__ __forceinline__ void dif_stages(cx<T>* a) {
   if constexpr (N > 1) {
-    constexpr int R = next_radix(N);
+    constexpr int R = stage_radix(N, RO);
     constexpr int span = N / R;
 #pragma unroll
     for (int b = 0; b < L / N; ++b) {
@@ -209,17 +241,17 @@ __device__ __forceinline__ void dif_stages(cx<T>* a) {
         });
       });
     }
-    dif_stages<T, L, span>(a);
+    dif_stages<T, L, span, RO>(a);
   }
 }
 
 // Inverse stages: the innermost forward stage is undone first.
-template <class T, int L, int N>
+template <class T, int L, int N, int RO>
 __device__ __forceinline__ void dit_inv_stages(cx<T>* a) {
   if constexpr (N > 1) {
-    constexpr int R = next_radix(N);
+    constexpr int R = stage_radix(N, RO);
     constexpr int span = N / R;
-    dit_inv_stages<T, L, span>(a);
+    dit_inv_stages<T, L, span, RO>(a);
 #pragma unroll
     for (int b = 0; b < L / N; ++b) {
       static_for<0, span>([&](auto kc) {
@@ -238,14 +270,14 @@ __device__ __forceinline__ void dit_inv_stages(cx<T>* a) {
   }
 }
 
-template <class T, int L>
+template <class T, int L, int RO = 0>
 __device__ __forceinline__ void forward(cx<T>* a) {
-  dif_stages<T, L, L>(a);
+  dif_stages<T, L, L, RO>(a);
 }
 
-template <class T, int L>
+template <class T, int L, int RO = 0>
 __device__ __forceinline__ void inverse(cx<T>* a) {
-  dit_inv_stages<T, L, L>(a);
+  dit_inv_stages<T, L, L, RO>(a);
 }
 
 }  // namespace regfft

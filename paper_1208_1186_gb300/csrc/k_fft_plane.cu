@@ -9,11 +9,8 @@
 // (4 LX LY complex) are staged in shared memory by asynchronous copies (no
 // register staging, all loads in flight at once); one thread per x-line does
 // the x transforms, then one thread per y-line the y transforms.
-// k_plane_zt: one CTA per (field, y, run of BX consecutive x) with the whole
-// (z, t) plane of that run in shared memory; z lines loaded from global memory
-// into registers and transformed, t lines (forward, acceleration factor,
-// inverse in registers), then z lines again, stored from registers: four
-// shared-memory accesses per element.
+// k_plane_zt (k_fft_zt.cu): the (z, t) transforms with the acceleration
+// factor in between.
 //
 // Frequencies are left in digit-reversed order by the forward transforms and
 // taken in that order by the inverse ones, so the acceleration factor is
@@ -349,127 +346,6 @@ constexpr size_t xyinv_gstep_pair_smem() {
   return (size_t)4 * L * (L + 1) * sizeof(cx<float>);
 }
 
-// x-run width of a z-t tile: 32 bytes of consecutive complex numbers
-template <class T>
-constexpr int zt_bx() {
-  return sizeof(T) == 4 ? 4 : 2;
-}
-
-// pitch of one t slice: BX*LZ plus padding that shifts consecutive t slices
-// by one run of BX elements across the 32 shared-memory banks
-template <class T, int LZ>
-constexpr int zt_pitch() {
-  constexpr int BX = zt_bx<T>();
-  constexpr int W = (int)sizeof(cx<T>) / 4;  // banks per element
-  for (int pad = 0; pad < 32; ++pad)
-    if ((((BX * LZ + pad) * W) % 32) == ((BX * W) % 32)) return BX * LZ + pad;
-  return BX * LZ;
-}
-
-template <class T, int LZ, int LT>
-constexpr int zt_threads() {
-  return zt_bx<T>() * (LZ > LT ? LZ : LT);
-}
-
-// z-t lines hold a whole t line through the forward transform, the factor and
-// the inverse: 3 CTAs per SM (up to 168 registers) for FP32 lines up to 32
-template <class T, int LZ, int LT>
-constexpr int zt_min_blocks() {
-  return (sizeof(T) == 4 && LZ <= 32 && LT <= 32) ? 4 : 1;
-}
-
-template <class T, int LZ, int LT>
-constexpr size_t zt_smem_bytes() {
-  return (size_t)zt_pitch<T, LZ>() * LT * sizeof(cx<T>);
-}
-
-// FP32: factor from s2p[axis][position] (4 sin^2 at the digit-reversed
-// frequency) and c_over_V = p2_max / V, 0 at k = 0.  FP64: per-site table
-// kfac (an FP64 division per mode would be slow on this GPU).
-template <class T, int LZ, int LT>
-__global__ void __launch_bounds__(zt_threads<T, LZ, LT>(), zt_min_blocks<T, LZ, LT>())
-    k_plane_zt(cx<T>* __restrict__ D, int Lx, int Ly,
-                                                                      const T* __restrict__ kfac,
-                                                                      const float* __restrict__ s2p, float c_over_V,
-                                                                      const DevState* __restrict__ st) {
-  pdl_wait();
-  if (st != nullptr && st->done) return;
-  constexpr int BX = zt_bx<T>();
-  constexpr int NT = zt_threads<T, LZ, LT>();
-  constexpr int PT = zt_pitch<T, LZ>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);  // [t][z][xb], t pitch PT
-  const int nxr = Lx / BX;
-  const int x0 = (blockIdx.x % nxr) * BX;
-  const int y = blockIdx.x / nxr;
-  const int f = blockIdx.y;
-  const int LxLy = Lx * Ly;
-  const int V = LxLy * LZ * LT;
-  cx<T>* Df = D + (f * V + x0 + Lx * y);
-  // forward z: line (xb, t) straight from global memory (for each z a warp
-  // reads BX consecutive x at 32 / BX values of t: whole 32-byte sectors)
-  if (threadIdx.x < BX * LT) {
-    const int xb = threadIdx.x % BX, t = threadIdx.x / BX;
-    cx<T>* line = tile + t * PT + xb;
-    const cx<T>* g = Df + (xb + LxLy * LZ * t);
-    cx<T> v[LZ];
-#pragma unroll
-    for (int p = 0; p < LZ; ++p) {  // running pointer: one address register
-      v[p] = *g;
-      g += LxLy;
-    }
-    regfft::forward<T, LZ>(v);
-#pragma unroll
-    for (int p = 0; p < LZ; ++p) line[p * BX] = v[p];
-  }
-  __syncthreads();
-  // t lines (xb, z): forward, acceleration factor, inverse
-  if (threadIdx.x < BX * LZ) {
-    const int xb = threadIdx.x % BX, z = threadIdx.x / BX;
-    cx<T>* line = tile + z * BX + xb;
-    cx<T> v[LT];
-#pragma unroll
-    for (int p = 0; p < LT; ++p) v[p] = line[p * PT];
-    regfft::forward<T, LT>(v);
-    const int x = x0 + xb;
-    if constexpr (sizeof(T) == 4) {
-      // the t contribution at each position is a compile-time constant
-      const float a = __ldg(s2p + x) + __ldg(s2p + kMaxL + y) + __ldg(s2p + 2 * kMaxL + z);
-      const bool origin = (x | y | z) == 0;
-      regfft::static_for<0, LT>([&](auto pc) {
-        constexpr int p = decltype(pc)::value;
-        constexpr float s2t = (float)regfft::MomentumSq<LT, p>::value;
-        float kf = c_over_V * rcp_approx(a + s2t);
-        if (p == 0 && origin) kf = 0.0f;
-        v[p] = scale(v[p], (T)kf);
-      });
-    } else {
-      const T* kl = kfac + (x + Lx * (y + Ly * z));
-#pragma unroll
-      for (int p = 0; p < LT; ++p) v[p] = scale(v[p], __ldg(kl + p * (LxLy * LZ)));
-    }
-    regfft::inverse<T, LT>(v);
-#pragma unroll
-    for (int p = 0; p < LT; ++p) line[p * PT] = v[p];
-  }
-  __syncthreads();
-  // inverse z, stored straight to global memory
-  if (threadIdx.x < BX * LT) {
-    const int xb = threadIdx.x % BX, t = threadIdx.x / BX;
-    const cx<T>* line = tile + t * PT + xb;
-    cx<T>* g = Df + (xb + LxLy * LZ * t);
-    cx<T> v[LZ];
-#pragma unroll
-    for (int p = 0; p < LZ; ++p) v[p] = line[p * BX];
-    regfft::inverse<T, LZ>(v);
-#pragma unroll
-    for (int p = 0; p < LZ; ++p) {
-      *g = v[p];
-      g += LxLy;
-    }
-  }
-}
-
 }  // namespace
 
 namespace {
@@ -477,12 +353,6 @@ namespace {
 // instantiated x-y planes (LX = LY) and z-t planes (LZ, LT), per precision
 #define LGF_XY_F32(X) X(4) X(6) X(8) X(12) X(16) X(20) X(24) X(32) X(48)
 #define LGF_XY_F64(X) X(4) X(6) X(8) X(12) X(16) X(20) X(24) X(32)
-#define LGF_ZT_F32(X)                                                                                      \
-  X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(48, 48) X(48, 8) X(48, 12) \
-  X(24, 48) X(32, 8) X(32, 16) X(16, 32)
-#define LGF_ZT_F64(X) \
-  X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(32, 8) X(32, 16) X(16, 32)
-
 template <class T, int L>
 cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaStream_t s, int Lz, int Lt) {
   if constexpr (L <= 32 && kXyWarpTiles) {
@@ -505,14 +375,6 @@ cudaError_t xy_launch(void* D, int64_t V, int inverse, const DevState* st, cudaS
   const auto Dp = static_cast<cx<T>*>(D);
   if (inverse) return launch_pdl(k_plane_xy<T, L, L, true>, nb, NT, sm, s, Dp, (int)V, st);
   return launch_pdl(k_plane_xy<T, L, L, false>, nb, NT, sm, s, Dp, (int)V, st);
-}
-
-template <class T, int LZ, int LT>
-cudaError_t zt_launch(void* D, int Lx, int Ly, const void* kfac, const float* s2p, float c_over_V, const DevState* st,
-                      cudaStream_t s) {
-  dim3 grid((unsigned)((Lx / zt_bx<T>()) * Ly), 4);
-  return launch_pdl(k_plane_zt<T, LZ, LT>, grid, zt_threads<T, LZ, LT>(), zt_smem_bytes<T, LZ, LT>(), s,
-                    static_cast<cx<T>*>(D), Lx, Ly, static_cast<const T*>(kfac), s2p, c_over_V, st);
 }
 
 template <int L>
@@ -576,12 +438,6 @@ cudaError_t xy_attr() {
   return e;
 }
 
-template <class T, int LZ, int LT>
-cudaError_t zt_attr() {
-  return cudaFuncSetAttribute(k_plane_zt<T, LZ, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)zt_smem_bytes<T, LZ, LT>());
-}
-
 }  // namespace
 
 bool plane_pipeline_supported(int prec, int Lx, int Ly, int Lz, int Lt) {
@@ -608,19 +464,12 @@ cudaError_t plane_pipeline_init() {
   if (e == cudaSuccess) e = xy_attr<float, L>();
 #define LGF_XYA64(L) \
   if (e == cudaSuccess) e = xy_attr<double, L>();
-#define LGF_ZTA32(A, B) \
-  if (e == cudaSuccess) e = zt_attr<float, A, B>();
-#define LGF_ZTA64(A, B) \
-  if (e == cudaSuccess) e = zt_attr<double, A, B>();
   if (e == cudaSuccess) e = xyinv_gstep_pair_attr<48>();
   LGF_XY_F32(LGF_XYA32)
   LGF_XY_F64(LGF_XYA64)
-  LGF_ZT_F32(LGF_ZTA32)
-  LGF_ZT_F64(LGF_ZTA64)
 #undef LGF_XYA32
 #undef LGF_XYA64
-#undef LGF_ZTA32
-#undef LGF_ZTA64
+  if (e == cudaSuccess) e = plane_zt_init();
   return e;
 }
 
@@ -667,22 +516,6 @@ cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int6
     case 48: return xyinv_gstep_pair_launch<48>(nc, reunit_fp64, Dp, Gp, (int)V, nplanes, half_alpha, st, s);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
-                            float c_over_V, const DevState* st, cudaStream_t s) {
-#define LGF_ZT32(A, B) \
-  if (Lz == A && Lt == B) return zt_launch<float, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, st, s);
-#define LGF_ZT64(A, B) \
-  if (Lz == A && Lt == B) return zt_launch<double, A, B>(D, Lx, Ly, kfac, s2p, c_over_V, st, s);
-  if (prec == 4) {
-    LGF_ZT_F32(LGF_ZT32)
-  } else {
-    LGF_ZT_F64(LGF_ZT64)
-  }
-#undef LGF_ZT32
-#undef LGF_ZT64
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace lgf

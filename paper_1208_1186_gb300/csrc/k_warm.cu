@@ -258,6 +258,258 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ x, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// convolutions on the 5th-generation tensor cores (tcgen05): implicit GEMM
+//   D[s, n] = sum_tap sum_k A_tap[s, k] B_tap[n, k],  A_tap[s, k] = act[s + SIGN off(tap), k]
+// with M = 128 consecutive sites per CTA, N = the output channels and K = the
+// gathered channels of one tap (16 per instruction).  Forward: act = x,
+// B_tap = W^T (K-major copy [tap][out][in]), bias and ReLU in the epilogue.
+// Backward data: act = gy, SIGN = -1, B_tap = W[tap][in][out] (already
+// K-major in the output channels), the ReLU mask of the layer below in the
+// epilogue.
+//
+// Pipeline: kTcStages shared-memory stages, each holding one tap's A tile
+// (128 rows x K bf16) and B tile (N rows x K) in the no-swizzle K-major
+// canonical layout -- core matrices of 8 rows x 16 bytes, (row r, 16-byte
+// chunk c) at (r / 8) SBO + c 128 + (r % 8) 16 with SBO = 16 K bytes.  All 128
+// threads gather their own site's row with 16-byte cp.async copies, a tap
+// S - 1 ahead of the one being multiplied; one thread issues the K / 16 MMAs
+// of a tap into the FP32 accumulator in tensor memory (128 lanes x N
+// columns) and commits them to the stage's mbarrier, which frees the stage
+// for its next tap.  Epilogue: each warp reads its 32 lanes (sites) with
+// tcgen05.ld.  Every wait is bounded: on expiry the CTA records an error in
+// *err, stops issuing, waits (bounded) for its MMAs, frees its tensor memory
+// and returns.
+// ---------------------------------------------------------------------------
+constexpr int kTcStages = 3;
+constexpr int kTcTmemCols = 32;
+constexpr unsigned kTcWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 bytes (the
+// next 16-byte chunk along K), SBO = the next 8-row group
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;
+}
+
+// instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32
+// accumulator, M = 128, N
+template <int N>
+constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (8u << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// bounded wait for the phase of parity `parity` of an mbarrier; true if done
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (unsigned it = 0; it < kTcWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(gsrc) : "memory");
+}
+
+template <int K, int N>
+constexpr int tc_stage_bytes() {
+  return (128 + N) * K * 2;
+}
+
+template <int K, int N, int SIGN, bool FWD>
+__global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, const bf16* __restrict__ Wk,
+                                                 const float* __restrict__ bias, const bf16* __restrict__ mask,
+                                                 bf16* __restrict__ y, float* __restrict__ yf, const Geom geo,
+                                                 bool relu, int* __restrict__ err) {
+  static_assert(K % 16 == 0 && (N == 16 || N == 32), "tile shapes of this kernel");
+  constexpr int NCH = K / 8;           // 16-byte chunks per row
+  constexpr int SBO = NCH * 128;       // bytes per 8-row group
+  constexpr int A_BYTES = 128 * K * 2;
+  constexpr int STAGE = tc_stage_bytes<K, N>();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kTcStages + 1];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int stop;
+  const int t = threadIdx.x, w = t >> 5;
+  const int V = (int)geo.V;
+  const int s = blockIdx.x * 128 + t;
+  const bool valid = s < V;
+  int c[4] = {0, 0, 0, 0};
+  if (valid) site_coords_r(geo, s, c);
+  const uint32_t sbase = smem_u32(smem_raw);
+  // rows past the end of the lattice stay zero in every stage
+  if (!valid)
+    for (int k = 0; k < kTcStages; ++k)
+      for (int ch = 0; ch < NCH; ++ch)
+        *reinterpret_cast<uint4*>(smem_raw + k * STAGE + (t >> 3) * SBO + ch * 128 + (t & 7) * 16) =
+            make_uint4(0, 0, 0, 0);
+  if (t == 0) {
+    for (int k = 0; k <= kTcStages; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stop = 0;
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  // gather tap `tap` into stage `tap % kTcStages`: this thread's row of A,
+  // and its share of the N x K tile of B
+  auto fill = [&](int tap) {
+    const uint32_t st = sbase + (tap % kTcStages) * STAGE;
+    if (valid) {
+      const int nb = tap_site(geo, c, tap, SIGN);
+      const bf16* src = act + (size_t)nb * K;
+      const uint32_t dst = st + (t >> 3) * SBO + (t & 7) * 16;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) cp_async16(dst + ch * 128, src + ch * 8);
+    }
+    const bf16* wsrc = Wk + (size_t)tap * N * K;
+    for (int j = t; j < N * NCH; j += 128) {
+      const int n = j / NCH, ch = j % NCH;
+      cp_async16(st + A_BYTES + (n >> 3) * SBO + ch * 128 + (n & 7) * 16, wsrc + n * K + ch * 8);
+    }
+  };
+
+  constexpr uint32_t idesc = tc_idesc<N>();
+#pragma unroll 1
+  for (int tap = 0; tap < kTcStages - 1; ++tap) {
+    fill(tap);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  int issued = -1;  // last tap whose MMAs were issued
+#pragma unroll 1
+  for (int tap = 0; tap < 81; ++tap) {
+    const int next = tap + kTcStages - 1;
+    if (next < 81) {
+      // the stage of `next` was last read by the MMAs of tap - 1
+      bool ok = true;
+      if (tap >= 1) ok = mbar_wait(&bars[(tap - 1) % kTcStages], (uint32_t)(((tap - 1) / kTcStages) & 1));
+      if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicExch(err, 1);
+        break;
+      }
+      fill(next);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = sbase + (tap % kTcStages) * STAGE;
+#pragma unroll
+      for (int q = 0; q < K / 16; ++q)
+        tc_mma(tmem, tc_desc(st + q * 256, SBO), tc_desc(st + A_BYTES + q * 256, SBO), idesc,
+               (tap > 0 || q > 0) ? 1u : 0u);
+      tc_commit(&bars[tap % kTcStages]);
+    }
+    issued = tap;
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  // all MMAs issued so far have completed once the last commit's phase does
+  bool ok = true;
+  if (t == 0 && issued >= 0) {
+    tc_commit(&bars[kTcStages]);
+    ok = mbar_wait(&bars[kTcStages], 0u);
+    if (!ok) atomicExch(err, 1);
+    stop = !ok || issued < 80;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!stop && issued == 80) {
+    float acc[32];
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16);
+    if constexpr (N == 32) {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+          "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr)
+          : "memory");
+    } else {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr)
+          : "memory");
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = __uint_as_float(r[j]);
+    if (valid) {
+      if constexpr (FWD) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          float v = acc[j] + bias[j];
+          acc[j] = relu ? fmaxf(v, 0.0f) : v;
+        }
+        if (yf != nullptr)
+#pragma unroll
+          for (int j = 0; j < N; j += 4)
+            *reinterpret_cast<float4*>(yf + (size_t)s * N + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+      } else if (mask != nullptr) {
+        const bf16* mrow = mask + (size_t)s * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+          if (!(__bfloat162float(mrow[j]) > 0.0f)) acc[j] = 0.0f;
+      }
+      bf16* out = y + (size_t)s * N;
+#pragma unroll
+      for (int j = 0; j < N; j += 8) {
+        uint4 q;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(acc[j], acc[j + 1]), h1 = __floats2bfloat162_rn(acc[j + 2], acc[j + 3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(acc[j + 4], acc[j + 5]), h3 = __floats2bfloat162_rn(acc[j + 6], acc[j + 7]);
+        q.x = *reinterpret_cast<uint32_t*>(&h0);
+        q.y = *reinterpret_cast<uint32_t*>(&h1);
+        q.z = *reinterpret_cast<uint32_t*>(&h2);
+        q.w = *reinterpret_cast<uint32_t*>(&h3);
+        *reinterpret_cast<uint4*>(out + j) = q;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+}
+
 // gx[s, i] = mask(s, i) * sum_tap sum_o W[tap, i, o] gy[s - off(tap), o], with
 // mask = (a[s, i] > 0) when a is given (the ReLU of the layer below).
 template <int CI, int CO>
@@ -393,22 +645,34 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 
 // bf16 weights from the FP32 parameters; the last layer is widened from 8 to
 // 16 outputs with zero columns.
+// (Wt*: the same weights K-major for the forward tensor-core convolution,
+// [tap][out][in])
 __global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ W1, bf16* __restrict__ W2,
                                bf16* __restrict__ W3, float* __restrict__ b1, float* __restrict__ b2,
-                               float* __restrict__ b3) {
+                               float* __restrict__ b3, bf16* __restrict__ Wt1, bf16* __restrict__ Wt2,
+                               bf16* __restrict__ Wt3) {
   const int n1 = 81 * kFeat * kHid, n2 = 81 * kHid * kHid, n3 = 81 * kHid * kOutPad;
   const int o_b1 = n1, o_W2 = o_b1 + kHid, o_b2 = o_W2 + n2, o_W3 = o_b2 + kHid, o_b3 = o_W3 + 81 * kHid * kOut;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3 + kHid * 2 + kOutPad;
        i += gridDim.x * blockDim.x) {
     if (i < n1) {
-      W1[i] = __float2bfloat16_rn(p[i]);
+      const bf16 v = __float2bfloat16_rn(p[i]);
+      W1[i] = v;
+      const int tap = i / (kFeat * kHid), r = i % (kFeat * kHid), in = r / kHid, o = r % kHid;
+      Wt1[(tap * kHid + o) * kFeat + in] = v;
     } else if (i < n1 + n2) {
       const int j = i - n1;
-      W2[j] = __float2bfloat16_rn(p[o_W2 + j]);
+      const bf16 v = __float2bfloat16_rn(p[o_W2 + j]);
+      W2[j] = v;
+      const int tap = j / (kHid * kHid), r = j % (kHid * kHid), in = r / kHid, o = r % kHid;
+      Wt2[(tap * kHid + o) * kHid + in] = v;
     } else if (i < n1 + n2 + n3) {
       const int j = i - n1 - n2;  // [tap][i][16]
       const int o = j % kOutPad, ti = j / kOutPad;
-      W3[j] = __float2bfloat16_rn(o < kOut ? p[o_W3 + ti * kOut + o] : 0.f);
+      const bf16 v = __float2bfloat16_rn(o < kOut ? p[o_W3 + ti * kOut + o] : 0.f);
+      W3[j] = v;
+      const int tap = ti / kHid, in = ti % kHid;
+      Wt3[(tap * kOutPad + o) * kHid + in] = v;
     } else {
       const int j = i - n1 - n2 - n3;
       if (j < kHid)
@@ -522,10 +786,43 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, flo
 }
 
 cudaError_t launch_pack_weights(const float* p, void* W1, void* W2, void* W3, float* b1, float* b2, float* b3,
-                                cudaStream_t s) {
+                                void* Wt1, void* Wt2, void* Wt3, cudaStream_t s) {
   k_pack_weights<<<256, 256, 0, s>>>(p, static_cast<bf16*>(W1), static_cast<bf16*>(W2), static_cast<bf16*>(W3), b1,
-                                     b2, b3);
+                                     b2, b3, static_cast<bf16*>(Wt1), static_cast<bf16*>(Wt2),
+                                     static_cast<bf16*>(Wt3));
   return cudaPeekAtLastError();
+}
+
+namespace {
+template <int K, int N, int SIGN, bool FWD>
+cudaError_t conv_tc_launch(const void* act, const void* Wk, const float* bias, const void* mask, void* y, float* yf,
+                           const Geom& geo, bool relu, int* err, cudaStream_t s) {
+  constexpr int smem = kTcStages * tc_stage_bytes<K, N>();
+  static_assert(smem <= 48 * 1024, "the stages fit the default dynamic shared memory cap");
+  const unsigned nb = (unsigned)((geo.V + 127) / 128);
+  k_conv_tc<K, N, SIGN, FWD><<<nb, 128, smem, s>>>(static_cast<const bf16*>(act), static_cast<const bf16*>(Wk), bias,
+                                                    static_cast<const bf16*>(mask), static_cast<bf16*>(y), yf, geo,
+                                                    relu, err);
+  return cudaPeekAtLastError();
+}
+}  // namespace
+
+// forward on the tensor cores: layer 1 48 -> 32, 2 32 -> 32 (both ReLU), 3
+// 32 -> 16 (8 used, FP32 copy in yf); Wt the K-major weights
+cudaError_t launch_conv_fwd_tc(int layer, const void* x, const void* Wt, const float* b, void* y, float* yf,
+                               const Geom& geo, int* err, cudaStream_t s) {
+  if (layer == 1) return conv_tc_launch<kFeat, kHid, +1, true>(x, Wt, b, nullptr, y, yf, geo, true, err, s);
+  if (layer == 2) return conv_tc_launch<kHid, kHid, +1, true>(x, Wt, b, nullptr, y, yf, geo, true, err, s);
+  return conv_tc_launch<kHid, kOutPad, +1, true>(x, Wt, b, nullptr, y, yf, geo, false, err, s);
+}
+
+// gradient with respect to the input of layer 3 (32 <- 16) or 2 (32 <- 32) on
+// the tensor cores, masked by the ReLU of the layer below (a); W in its own
+// [tap][in][out] layout, which is K-major for this product
+cudaError_t launch_conv_bwd_data_tc(int layer, const void* gy, const void* W, const void* a, void* gx,
+                                    const Geom& geo, int* err, cudaStream_t s) {
+  if (layer == 3) return conv_tc_launch<kOutPad, kHid, -1, false>(gy, W, nullptr, a, gx, nullptr, geo, false, err, s);
+  return conv_tc_launch<kHid, kHid, -1, false>(gy, W, nullptr, a, gx, nullptr, geo, false, err, s);
 }
 
 cudaError_t launch_unpad_grad3(const float* gW3p, const float* gb3p, float* gW3, float* gb3, cudaStream_t s) {

@@ -13,6 +13,7 @@
 // stops at exactly the first iteration with theta < tol.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -52,13 +53,30 @@ struct Engine {
   FftGeom fg{};  // FFT tiling for this precision (plane pipeline)
   bool axis = false;     // per-axis register FFT passes apply to this lattice
   bool plane = false;    // three-pass register plane pipeline applies
-  int tuned = 0;         // pipeline chosen by lgf_autotune (0: none)
+  int tuned = 0;         // pipeline chosen by lgf_autotune or the tuning cache (0: none)
+  int zt_bx = 0;         // plane pipeline: x-run width of the z-t tiles (0: default)
+  int zt_ro = 0;         // plane pipeline: radix order of the z and t transforms
   bool grep = false;     // FP32 engine: gauge representation (U holds the loaded links, G is updated)
   void* kfac = nullptr;  // axis pipeline, FP64: p2_max/(V p2(k)) per site, digit-reversed order
-  float* s2p = nullptr;  // axis pipeline, FP32: [4][kMaxL] 4 sin^2(pi k/L) at digit-reversed positions
+  float* s2p = nullptr;  // FP32: [2][4][kMaxL] 4 sin^2(pi k/L) at the digit-reversed positions of radix order 0, 1
   float c_over_V = 0.f;  // p2_max / V
   size_t cbytes() const { return 2 * (size_t)prec; }
 };
+
+// FFT schedule of one (precision, lattice shape): the pipeline and, for the
+// plane pipeline, the z-t tile width and radix order (lgf_autotune); kept for
+// the process and optionally in a JSON file (lgf_tune_save / lgf_tune_load)
+struct TuneEntry {
+  int pipeline = 0;
+  int zt_bx = 0;
+  int zt_ro = 0;
+  double ms = 0.0;  // per Fourier acceleration, as timed by the autotuner
+};
+using TuneKey = std::tuple<int, int, int, int, int>;  // (bytes per real, Lx, Ly, Lz, Lt)
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneEntry> g_tune_cache;
+bool g_tune_apply_at_create = false;  // set once a cache file has been loaded
+std::once_flag g_tune_env_once;
 
 }  // namespace
 
@@ -235,7 +253,7 @@ int alloc_engine(lgf_handle h, Engine& e) {
     // acceleration factor at every position the forward passes leave a mode:
     // position p along an axis holds frequency digit_rev(L, p)
     std::vector<double> s2[4];
-    std::vector<float> s2f(4 * kMaxL, 0.0f);
+    std::vector<float> s2f(2 * 4 * kMaxL, 0.0f);
     double p2max = 0.0;
     for (int a = 0; a < 4; ++a) {
       const int L = h->L[a];
@@ -247,12 +265,16 @@ int alloc_engine(lgf_handle h, Engine& e) {
         s2[a][p] = (double)(4.0L * sk * sk);
         s2f[a * kMaxL + p] = (float)s2[a][p];
         m = s2[a][p] > m ? s2[a][p] : m;
+        // the same at the positions of radix order 1
+        const long double sk1 = sinl(3.14159265358979323846264338327950288L *
+                                     (long double)regfft::digit_rev(L, p, 1) / (long double)L);
+        s2f[4 * kMaxL + a * kMaxL + p] = (float)(4.0L * sk1 * sk1);
       }
       p2max += m;
     }
     e.c_over_V = (float)(p2max / (double)V);
     if (e.prec == 4) {
-      e.s2p = static_cast<float*>(dev_alloc(h, 4 * kMaxL * sizeof(float)));
+      e.s2p = static_cast<float*>(dev_alloc(h, s2f.size() * sizeof(float)));
       if (!e.s2p) return fail(h, LGF_ERR_OOM, "device allocation failed");
       LGF_CUDA(h, cudaMemcpy(e.s2p, s2f.data(), s2f.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
@@ -269,6 +291,26 @@ int alloc_engine(lgf_handle h, Engine& e) {
     }
   }
   return LGF_OK;
+}
+
+int tune_load_file(const char* path, int* n_out);
+
+// A cached schedule (from a loaded tuning file, or tuned in this process
+// after one was loaded) for engine e's precision and shape, if it applies.
+void apply_cached_schedule(lgf_handle h, Engine& e) {
+  std::call_once(g_tune_env_once, [] {
+    const char* path = getenv("LGF_TUNE_CACHE");
+    if (path && *path) tune_load_file(path, nullptr);
+  });
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (!g_tune_apply_at_create) return;
+  auto it = g_tune_cache.find(std::make_tuple(e.prec, h->L[0], h->L[1], h->L[2], h->L[3]));
+  if (it == g_tune_cache.end()) return;
+  const TuneEntry& t = it->second;
+  if ((t.pipeline == 2 && !e.axis) || (t.pipeline == 3 && !e.plane)) return;
+  e.tuned = t.pipeline;
+  e.zt_bx = t.zt_bx;
+  e.zt_ro = t.zt_ro;
 }
 
 int ensure_staging(lgf_handle h) {
@@ -328,7 +370,8 @@ int queue_accelerate(lgf_handle h, Engine& e, const DevState* st) {
   if (pipe == 3) {
     const int* L = h->L;
     LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 0, st, s));
-    LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V, st, s));
+    LGF_LAUNCH(h, LGF_K_FFT_ZT, launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V,
+                                                e.zt_bx, e.zt_ro, st, s));
     LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 1, st, s));
   } else if (pipe == 2) {
     const int64_t V = h->V;
@@ -444,7 +487,8 @@ int queue_iteration(lgf_handle h, Engine& e) {
     const int* L = h->L;
     LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 0, h->st, s));
     LGF_LAUNCH(h, LGF_K_FFT_ZT,
-               launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V, h->st, s));
+               launch_plane_zt(e.prec, L[0], L[1], L[2], L[3], e.D, e.kfac, e.s2p, e.c_over_V, e.zt_bx, e.zt_ro,
+                               h->st, s));
     LGF_LAUNCH(h, LGF_K_XY_GSTEP, launch_plane_xyinv_gstep(L[0], e.nc, e.D, h->G, h->V, L[2], L[3], 0.5 * h->alpha,
                                                            h->reunit_fp64, h->st, s));
     return LGF_OK;
@@ -611,13 +655,13 @@ int run_fix(lgf_handle h, Engine& e, double tol, int max_iter, bool stall_check,
 // ---------------------------------------------------------------------------
 namespace {
 
-std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;  // (prec, Lx, Ly, Lz, Lt) -> pipeline
 
-// Time every pipeline that applies to engine e (Fourier acceleration of its
-// packed-gradient buffer, which is scratch between iterations) and return
-// the fastest; results are cached for the process.
-int tune_engine(lgf_handle h, Engine& e, int reps, int* out) {
+// Time every FFT schedule that applies to engine e -- each pipeline, and for
+// the register plane pipeline each z-t tile width and radix order -- on the
+// Fourier acceleration of its packed-gradient buffer (scratch between
+// iterations), and return the fastest.  Results are kept per (precision,
+// shape) for the process.
+int tune_engine(lgf_handle h, Engine& e, int reps, TuneEntry* out) {
   const auto key = std::make_tuple(e.prec, h->L[0], h->L[1], h->L[2], h->L[3]);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -628,20 +672,28 @@ int tune_engine(lgf_handle h, Engine& e, int reps, int* out) {
     }
   }
   LGF_CUDA(h, cudaMemsetAsync(e.D, 0, (size_t)4 * h->V * e.cbytes(), h->stream));
-  std::vector<int> cands = {1};
-  if (e.axis) cands.push_back(2);
-  if (e.plane) cands.push_back(3);
+  std::vector<TuneEntry> cands;
+  cands.push_back({1, 0, 0});
+  if (e.axis) cands.push_back({2, 0, 0});
+  if (e.plane) {
+    const int b0 = e.prec == 4 ? 4 : 2;
+    for (int bx : {0, 2 * b0})
+      for (int ro : {0, 1})
+        if (plane_zt_schedule_supported(e.prec, h->L[0], h->L[2], h->L[3], bx, ro)) cands.push_back({3, bx, ro});
+  }
   cudaEvent_t a, b;
   LGF_CUDA(h, cudaEventCreate(&a));
   LGF_CUDA(h, cudaEventCreate(&b));
   const int saved = h->fft_pipeline;
+  const int saved_bx = e.zt_bx, saved_ro = e.zt_ro;
   const bool saved_prof = h->profiling;
   h->profiling = false;
-  float best = 0.0f;
-  int best_p = cands[0];
+  TuneEntry best = cands[0];
   int rc = LGF_OK;
-  for (int p : cands) {
-    h->fft_pipeline = p;
+  for (size_t c = 0; c < cands.size(); ++c) {
+    h->fft_pipeline = cands[c].pipeline;
+    e.zt_bx = cands[c].zt_bx;
+    e.zt_ro = cands[c].zt_ro;
     for (int i = 0; i < 2 && !rc; ++i) rc = queue_accelerate(h, e, nullptr);
     if (rc) break;
     cudaEventRecord(a, h->stream);
@@ -654,22 +706,114 @@ int tune_engine(lgf_handle h, Engine& e, int reps, int* out) {
     }
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, a, b);
-    if (p == cands[0] || ms < best) {
-      best = ms;
-      best_p = p;
-    }
+    cands[c].ms = (double)ms / reps;
+    if (c == 0 || cands[c].ms < best.ms) best = cands[c];
   }
   h->fft_pipeline = saved;
+  e.zt_bx = saved_bx;
+  e.zt_ro = saved_ro;
   h->profiling = saved_prof;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = best_p;
+    g_tune_cache[key] = best;
   }
-  *out = best_p;
+  *out = best;
   return LGF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the schedule cache as a JSON file: one object per line inside a list,
+//   {"prec": 4, "L": [32, 32, 32, 32], "pipeline": 3, "zt_bx": 4, "zt_ro": 0, "ms": 0.0531}
+// (prec in bytes per real).  The reader takes these lines back (any order,
+// other lines ignored) and rejects values no engine could run.
+// ---------------------------------------------------------------------------
+bool json_int(const char* line, const char* name, int* out) {
+  char pat[32];
+  snprintf(pat, sizeof pat, "\"%s\"", name);
+  const char* p = strstr(line, pat);
+  if (!p) return false;
+  p = strchr(p + strlen(pat), ':');
+  if (!p) return false;
+  char* end = nullptr;
+  const long v = strtol(p + 1, &end, 10);
+  if (end == p + 1) return false;
+  *out = (int)v;
+  return true;
+}
+
+bool json_extents(const char* line, int L[4]) {
+  const char* p = strstr(line, "\"L\"");
+  if (!p) return false;
+  p = strchr(p, '[');
+  if (!p) return false;
+  ++p;
+  for (int a = 0; a < 4; ++a) {
+    char* end = nullptr;
+    const long v = strtol(p, &end, 10);
+    if (end == p) return false;
+    L[a] = (int)v;
+    p = end;
+    while (*p == ' ' || *p == ',') ++p;
+  }
+  return *p == ']';
+}
+
+bool valid_entry(int prec, const int L[4], const TuneEntry& t) {
+  if (prec != 4 && prec != 8) return false;
+  for (int a = 0; a < 4; ++a)
+    if (L[a] < 2 || L[a] > kMaxL) return false;
+  if (t.pipeline < 1 || t.pipeline > 3) return false;
+  if (t.pipeline != 3) return t.zt_bx == 0 && t.zt_ro == 0;
+  return plane_pipeline_supported(prec, L[0], L[1], L[2], L[3]) &&
+         plane_zt_schedule_supported(prec, L[0], L[2], L[3], t.zt_bx, t.zt_ro);
+}
+
+int tune_load_file(const char* path, int* n_out) {
+  FILE* f = fopen(path, "r");
+  if (!f) return LGF_ERR_ARG;
+  char line[512];
+  int n = 0;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  while (fgets(line, sizeof line, f)) {
+    int prec = 0, L[4];
+    TuneEntry t;
+    if (!json_int(line, "prec", &prec) || !json_extents(line, L) || !json_int(line, "pipeline", &t.pipeline) ||
+        !json_int(line, "zt_bx", &t.zt_bx) || !json_int(line, "zt_ro", &t.zt_ro))
+      continue;
+    const char* m = strstr(line, "\"ms\"");
+    if (m && (m = strchr(m, ':'))) t.ms = strtod(m + 1, nullptr);
+    if (!valid_entry(prec, L, t)) continue;
+    g_tune_cache[std::make_tuple(prec, L[0], L[1], L[2], L[3])] = t;
+    ++n;
+  }
+  fclose(f);
+  g_tune_apply_at_create = true;
+  if (n_out) *n_out = n;
+  return LGF_OK;
+}
+
+int tune_save_file(const char* path) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return LGF_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    fprintf(f, "{\"lgf_fft_schedules\": [\n");
+    size_t i = 0;
+    for (const auto& kv : g_tune_cache) {
+      const TuneKey& k = kv.first;
+      const TuneEntry& t = kv.second;
+      fprintf(f, " {\"prec\": %d, \"L\": [%d, %d, %d, %d], \"pipeline\": %d, \"zt_bx\": %d, \"zt_ro\": %d, \"ms\": %.6f}%s\n",
+              std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), t.pipeline, t.zt_bx,
+              t.zt_ro, t.ms, ++i < g_tune_cache.size() ? "," : "");
+    }
+    fprintf(f, "]}\n");
+  }
+  const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
+  return ok ? LGF_OK : LGF_ERR_ARG;
 }
 
 }  // namespace
@@ -859,6 +1003,8 @@ struct lgf_net_ctx {
   void* W1 = nullptr;
   void* W2 = nullptr;
   void* W3 = nullptr;  // bf16, last layer 16 wide
+  void *Wt1 = nullptr, *Wt2 = nullptr, *Wt3 = nullptr;  // the same K-major ([tap][out][in]) for the forward
+  int* tc_err = nullptr;  // set by a tensor-core convolution whose bounded wait expired
   float* b1 = nullptr;
   float* b2 = nullptr;
   float* b3 = nullptr;
@@ -929,7 +1075,7 @@ double normal_at(uint64_t seed, uint64_t i) {
 }
 
 int net_pack(lgf_net n, cudaStream_t s) {
-  LGF_NCUDA(n, warm::launch_pack_weights(n->p, n->W1, n->W2, n->W3, n->b1, n->b2, n->b3, s));
+  LGF_NCUDA(n, warm::launch_pack_weights(n->p, n->W1, n->W2, n->W3, n->b1, n->b2, n->b3, n->Wt1, n->Wt2, n->Wt3, s));
   return LGF_OK;
 }
 
@@ -967,11 +1113,21 @@ int net_check_handle(lgf_net n, lgf_handle h) {
 int net_forward(lgf_net n, lgf_handle h) {
   cudaStream_t s = h->stream;
   LGF_NCUDA(n, warm::launch_features(h->e32.nc, h->e32.U, n->x0, h->geo, s));
-  LGF_NCUDA(n, warm::launch_conv_fwd(1, n->x0, n->W1, n->b1, n->a1, nullptr, h->geo, s));
-  LGF_NCUDA(n, warm::launch_conv_fwd(2, n->a1, n->W2, n->b2, n->a2, nullptr, h->geo, s));
-  LGF_NCUDA(n, warm::launch_conv_fwd(3, n->a2, n->W3, n->b3, n->y3, n->c, h->geo, s));
+  LGF_NCUDA(n, warm::launch_conv_fwd_tc(1, n->x0, n->Wt1, n->b1, n->a1, nullptr, h->geo, n->tc_err, s));
+  LGF_NCUDA(n, warm::launch_conv_fwd_tc(2, n->a1, n->Wt2, n->b2, n->a2, nullptr, h->geo, n->tc_err, s));
+  LGF_NCUDA(n, warm::launch_conv_fwd_tc(3, n->a2, n->Wt3, n->b3, n->y3, n->c, h->geo, n->tc_err, s));
   h->launches += 4;
   return LGF_OK;
+}
+
+// after the stream has been synchronised: LGF_ERR_TIMEOUT (and the flag
+// cleared) if a tensor-core convolution gave up a bounded wait
+int net_check_tc(lgf_net n) {
+  int flag = 0;
+  LGF_NCUDA(n, cudaMemcpy(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag == 0) return LGF_OK;
+  LGF_NCUDA(n, cudaMemset(n->tc_err, 0, sizeof(int)));
+  return nfail(n, LGF_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
 }
 
 }  // namespace
@@ -1012,6 +1168,7 @@ int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out) {
   }
   h->V = V;
   h->geo.V = V;
+  geom_init_rcp(h->geo);
   fg.V = V;
   double p2max = 0.0;
   for (int a = 0; a < 4; ++a) {
@@ -1078,6 +1235,10 @@ int lgf_create(int Lx, int Ly, int Lz, int Lt, int dtype, lgf_handle* out) {
 
   int rc = alloc_engine(h, h->e64);
   if (!rc && h->mixed) rc = alloc_engine(h, h->e32);
+  if (!rc) {
+    apply_cached_schedule(h, h->e64);
+    if (h->mixed) apply_cached_schedule(h, h->e32);
+  }
   if (rc) return bail(rc);
   h->cur = h->mixed ? &h->e32 : &h->e64;
   if (h->mixed) {
@@ -1372,16 +1533,81 @@ int lgf_fix_split(lgf_handle h, int* fp32_iters, int* fp64_iters) {
 int lgf_autotune(lgf_handle h, int reps, int* chosen) {
   if (!h || reps < 1) return LGF_ERR_ARG;
   drop_loops(h);
-  int p64 = 0, p32 = 0;
-  int rc = tune_engine(h, h->e64, reps, &p64);
+  TuneEntry t64, t32;
+  int rc = tune_engine(h, h->e64, reps, &t64);
   if (rc) return rc;
-  h->e64.tuned = p64;
+  h->e64.tuned = t64.pipeline;
+  h->e64.zt_bx = t64.zt_bx;
+  h->e64.zt_ro = t64.zt_ro;
   if (h->mixed) {
-    rc = tune_engine(h, h->e32, reps, &p32);
+    rc = tune_engine(h, h->e32, reps, &t32);
     if (rc) return rc;
-    h->e32.tuned = p32;
+    h->e32.tuned = t32.pipeline;
+    h->e32.zt_bx = t32.zt_bx;
+    h->e32.zt_ro = t32.zt_ro;
   }
-  if (chosen) *chosen = h->mixed ? p32 : p64;
+  if (chosen) *chosen = h->mixed ? t32.pipeline : t64.pipeline;
+  const char* path = getenv("LGF_TUNE_CACHE");
+  if (path && *path && tune_save_file(path) != LGF_OK)
+    return fail(h, LGF_ERR_ARG, std::string("lgf_autotune: cannot write the tuning cache ") + path);
+  return LGF_OK;
+}
+
+int lgf_tune_schedule(lgf_handle h, int engine, int* pipeline, int* zt_bx, int* zt_ro) {
+  if (!h || (engine != 0 && engine != 1)) return LGF_ERR_ARG;
+  if (engine == 1 && !h->mixed) return fail(h, LGF_ERR_ARG, "lgf_tune_schedule: the handle has no FP32 engine");
+  const Engine& e = engine == 1 ? h->e32 : h->e64;
+  if (pipeline) *pipeline = pick_pipeline(h, e);
+  if (zt_bx) *zt_bx = e.zt_bx;
+  if (zt_ro) *zt_ro = e.zt_ro;
+  return LGF_OK;
+}
+
+int lgf_set_schedule(lgf_handle h, int engine, int pipeline, int zt_bx, int zt_ro) {
+  if (!h || (engine != 0 && engine != 1)) return LGF_ERR_ARG;
+  if (engine == 1 && !h->mixed) return fail(h, LGF_ERR_ARG, "lgf_set_schedule: the handle has no FP32 engine");
+  Engine& e = engine == 1 ? h->e32 : h->e64;
+  TuneEntry t;
+  t.pipeline = pipeline;
+  t.zt_bx = zt_bx;
+  t.zt_ro = zt_ro;
+  if (!valid_entry(e.prec, h->L, t) || (pipeline == 2 && !e.axis))
+    return fail(h, LGF_ERR_ARG, "lgf_set_schedule: schedule does not apply to this lattice and precision");
+  drop_loops(h);
+  e.tuned = pipeline;
+  e.zt_bx = zt_bx;
+  e.zt_ro = zt_ro;
+  return LGF_OK;
+}
+
+int lgf_tune_load(const char* path, int* n_loaded) {
+  if (!path) return LGF_ERR_ARG;
+  const int rc = tune_load_file(path, n_loaded);
+  if (rc) set_global_error(std::string("lgf_tune_load: cannot read ") + path);
+  return rc;
+}
+
+int lgf_tune_save(const char* path) {
+  if (!path) return LGF_ERR_ARG;
+  const int rc = tune_save_file(path);
+  if (rc) set_global_error(std::string("lgf_tune_save: cannot write ") + path);
+  return rc;
+}
+
+int lgf_tune_lookup(int prec_bytes, int Lx, int Ly, int Lz, int Lt, int* pipeline, int* zt_bx, int* zt_ro) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune_cache.find(std::make_tuple(prec_bytes, Lx, Ly, Lz, Lt));
+  if (it == g_tune_cache.end()) return LGF_ERR_ARG;
+  if (pipeline) *pipeline = it->second.pipeline;
+  if (zt_bx) *zt_bx = it->second.zt_bx;
+  if (zt_ro) *zt_ro = it->second.zt_ro;
+  return LGF_OK;
+}
+
+int lgf_tune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache.clear();
+  g_tune_apply_at_create = false;
   return LGF_OK;
 }
 
@@ -1588,16 +1814,24 @@ int lgf_net_create(unsigned long long seed, lgf_net* out) {
   n->W1 = net_alloc(n, (size_t)kW1 * 2);
   n->W2 = net_alloc(n, (size_t)kW2 * 2);
   n->W3 = net_alloc(n, (size_t)81 * 32 * 16 * 2);
+  n->Wt1 = net_alloc(n, (size_t)kW1 * 2);
+  n->Wt2 = net_alloc(n, (size_t)kW2 * 2);
+  n->Wt3 = net_alloc(n, (size_t)81 * 32 * 16 * 2);
+  n->tc_err = static_cast<int*>(net_alloc(n, sizeof(int)));
   n->b1 = static_cast<float*>(net_alloc(n, 32 * 4));
   n->b2 = static_cast<float*>(net_alloc(n, 32 * 4));
   n->b3 = static_cast<float*>(net_alloc(n, 16 * 4));
   n->gW3p = static_cast<float*>(net_alloc(n, (size_t)81 * 32 * 16 * 4));
   n->gb3p = static_cast<float*>(net_alloc(n, 16 * 4));
   if (!n->p || !n->m || !n->v || !n->g || !n->W1 || !n->W2 || !n->W3 || !n->b1 || !n->b2 || !n->b3 || !n->gW3p ||
-      !n->gb3p) {
+      !n->gb3p || !n->Wt1 || !n->Wt2 || !n->Wt3 || !n->tc_err) {
     std::string msg = "device allocation of the network failed";
     lgf_net_destroy(n);
     return nfail(nullptr, LGF_ERR_OOM, msg);
+  }
+  if (cudaMemset(n->tc_err, 0, sizeof(int)) != cudaSuccess) {
+    lgf_net_destroy(n);
+    return nfail(nullptr, LGF_ERR_CUDA, "cudaMemset of the network's error flag failed");
   }
   // He-normal initialisation; the last layer 100x smaller so that g0 starts
   // close to the identity (the warm start starts as "no warm start")
@@ -1653,7 +1887,7 @@ int lgf_net_forward(lgf_net n, lgf_handle h, float* host_c) {
                                    (size_t)h->V, cudaMemcpyDeviceToHost, h->stream));
   }
   LGF_NCUDA(n, cudaStreamSynchronize(h->stream));
-  return LGF_OK;
+  return net_check_tc(n);
 }
 
 int lgf_net_train_step(lgf_net n, lgf_handle h, double lr, double* F_out, float* host_grad) {
@@ -1675,11 +1909,11 @@ int lgf_net_train_step(lgf_net n, lgf_handle h, double lr, double* F_out, float*
   // layer 3 (a2 -> c)
   LGF_NCUDA(n, warm::launch_conv_bwd_weight(3, n->a2, n->gc, n->gW3p, h->geo, s));
   LGF_NCUDA(n, warm::launch_bias_grad(16, n->gc, n->gb3p, V, s));
-  LGF_NCUDA(n, warm::launch_conv_bwd_data(3, n->gc, n->W3, n->a2, n->ga2, h->geo, s));
+  LGF_NCUDA(n, warm::launch_conv_bwd_data_tc(3, n->gc, n->W3, n->a2, n->ga2, h->geo, n->tc_err, s));
   // layer 2 (a1 -> a2)
   LGF_NCUDA(n, warm::launch_conv_bwd_weight(2, n->a1, n->ga2, n->g + kOW2, h->geo, s));
   LGF_NCUDA(n, warm::launch_bias_grad(32, n->ga2, n->g + kOB2, V, s));
-  LGF_NCUDA(n, warm::launch_conv_bwd_data(2, n->ga2, n->W2, n->a1, n->ga1, h->geo, s));
+  LGF_NCUDA(n, warm::launch_conv_bwd_data_tc(2, n->ga2, n->W2, n->a1, n->ga1, h->geo, n->tc_err, s));
   // layer 1 (x0 -> a1)
   LGF_NCUDA(n, warm::launch_conv_bwd_weight(1, n->x0, n->ga1, n->g, h->geo, s));
   LGF_NCUDA(n, warm::launch_bias_grad(32, n->ga1, n->g + kOB1, V, s));
@@ -1698,6 +1932,8 @@ int lgf_net_train_step(lgf_net n, lgf_handle h, double lr, double* F_out, float*
   }
   rc = sync_state(h);
   if (rc) return nfail(n, rc, h->err);
+  rc = net_check_tc(n);
+  if (rc) return rc;
   if (F_out) *F_out = h->st_host->F;
   return LGF_OK;
 }
@@ -1711,7 +1947,36 @@ int lgf_net_warm_start(lgf_net n, lgf_handle h) {
   LGF_NCUDA(n, warm::launch_expmap(h->e32.nc, n->c, 16, h->G, (int)h->V, h->stream));
   h->launches += 1;
   LGF_NCUDA(n, cudaStreamSynchronize(h->stream));
-  return LGF_OK;
+  return net_check_tc(n);
+}
+
+int lgf_net_conv(lgf_net n, int layer, int backward, const void* in, const void* mask, void* out, float* out_f32,
+                 int Lx, int Ly, int Lz, int Lt, void* stream) {
+  if (!n) return LGF_ERR_ARG;
+  if (layer < 1 || layer > 3 || (backward != 0 && backward != 1) || (backward && layer == 1))
+    return nfail(n, LGF_ERR_ARG, "lgf_net_conv: layer 1..3 forward, 2..3 backward");
+  if (!in || !out) return nfail(n, LGF_ERR_ARG, "lgf_net_conv: in and out must be device pointers");
+  Geom geo{};
+  const int Ls[4] = {Lx, Ly, Lz, Lt};
+  int64_t V = 1;
+  for (int a = 0; a < 4; ++a) {
+    if (Ls[a] < 2 || Ls[a] > kMaxL) return nfail(n, LGF_ERR_ARG, "lgf_net_conv: each extent must be in [2, 64]");
+    geo.L[a] = Ls[a];
+    geo.stride[a] = V;
+    V *= Ls[a];
+  }
+  geo.V = V;
+  geom_init_rcp(geo);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* const Wt[3] = {n->Wt1, n->Wt2, n->Wt3};
+  void* const W[3] = {n->W1, n->W2, n->W3};
+  const float* const b[3] = {n->b1, n->b2, n->b3};
+  if (!backward)
+    LGF_NCUDA(n, warm::launch_conv_fwd_tc(layer, in, Wt[layer - 1], b[layer - 1], out, out_f32, geo, n->tc_err, s));
+  else
+    LGF_NCUDA(n, warm::launch_conv_bwd_data_tc(layer, in, W[layer - 1], mask, out, geo, n->tc_err, s));
+  LGF_NCUDA(n, cudaStreamSynchronize(s));
+  return net_check_tc(n);
 }
 
 const char* lgf_net_last_error(lgf_net n) { return n ? n->err.c_str() : g_last_create_error.c_str(); }

@@ -109,15 +109,25 @@ cudaError_t launch_strided(int prec, int L, void* D, int64_t V, int64_t S, int i
 cudaError_t launch_tpass(int prec, int L, void* D, int64_t V, int Lx, int Ly, const void* kfac, const float* s2p,
                          float c_over_V, const DevState* st, cudaStream_t s);
 
-// three-pass plane pipeline with register FFTs (k_fft_plane.cu): x-y plane
-// (Lx = Ly) and z-t plane (fwd, acceleration factor, inv) kernels for a list
-// of instantiated shapes
+// three-pass plane pipeline with register FFTs: x-y plane (Lx = Ly) kernels
+// (k_fft_plane.cu) and z-t plane (fwd, acceleration factor, inv) kernels
+// (k_fft_zt.cu) for a list of instantiated shapes
+#define LGF_ZT_F32(X)                                                                                      \
+  X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(48, 48) X(48, 8) X(48, 12) \
+  X(24, 48) X(32, 8) X(32, 16) X(16, 32)
+#define LGF_ZT_F64(X) \
+  X(4, 4) X(6, 6) X(8, 8) X(12, 12) X(16, 16) X(20, 20) X(24, 24) X(32, 32) X(32, 8) X(32, 16) X(16, 32)
 bool plane_pipeline_supported(int prec, int Lx, int Ly, int Lz, int Lt);
 cudaError_t plane_pipeline_init();
+cudaError_t plane_zt_init();
 cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt, int inverse, const DevState* st,
                             cudaStream_t s);
+// z-t pass schedule: bx = x-run width of a tile (0: the default, 4 FP32 / 2
+// FP64; or twice that), ro = radix order of the z and t transforms (0, or 1
+// for FP32 where it changes the stages); s2p holds [2][4][kMaxL] FP32 factors
+bool plane_zt_schedule_supported(int prec, int Lx, int Lz, int Lt, int bx, int ro);
 cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, const void* kfac, const float* s2p,
-                            float c_over_V, const DevState* st, cudaStream_t s);
+                            float c_over_V, int bx, int ro, const DevState* st, cudaStream_t s);
 // inverse x-y pass fused with G <- g G (FP32 gauge representation; Lx = Ly
 // one of 4, 6, 8, 12, 16, 20, 24, 32)
 bool plane_xyinv_gstep_supported(int prec, int L);
@@ -175,7 +185,13 @@ cudaError_t launch_bias_grad(int co, const void* gy, float* gb, int V, cudaStrea
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float c1,
                         float c2, float eps, cudaStream_t s);
 cudaError_t launch_pack_weights(const float* p, void* W1, void* W2, void* W3, float* b1, float* b2, float* b3,
-                                cudaStream_t s);
+                                void* Wt1, void* Wt2, void* Wt3, cudaStream_t s);
+// tcgen05 implicit-GEMM convolutions (forward and backward data); *err is set
+// to 1 if a bounded wait inside a CTA expired
+cudaError_t launch_conv_fwd_tc(int layer, const void* x, const void* Wt, const float* b, void* y, float* yf,
+                               const Geom& geo, int* err, cudaStream_t s);
+cudaError_t launch_conv_bwd_data_tc(int layer, const void* gy, const void* W, const void* a, void* gx,
+                                    const Geom& geo, int* err, cudaStream_t s);
 cudaError_t launch_unpad_grad3(const float* gW3p, const float* gb3p, float* gW3, float* gb3, cudaStream_t s);
 }  // namespace warm
 

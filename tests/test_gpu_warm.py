@@ -143,30 +143,37 @@ def test_training_raises_F(lgf):
 
 
 def test_warm_start_cuts_iterations(lgf):
-    """What the trained network gains: trained on 16 configurations of 8^4
-    (8 epochs), it starts unseen 8^4 configurations at a higher F and the
-    warm-started fixes need fewer updates to theta < 1e-15 in total than the
-    plain fixes of the same inputs.  Every fix converges; the final F of each
-    pair is reported with whether the Gribov copy is the same (a different
-    copy is allowed: the plain method is the judge, through theta and F)."""
+    """What the trained network gains, on the recipe whose margin was
+    measured: trained on 2000 configurations of 16^4 (one epoch, Adam lr
+    1e-5, inputs from the GPU generator), it starts unseen 24^4
+    configurations at a higher F, and the warm-started fixes need fewer
+    updates to theta < 1e-15 in total than the plain fixes of the same
+    inputs (measured: 25 instead of 26 on each of 8 configurations).  Every
+    fix converges; the time of each arm (the warm one with its inference) is
+    reported, with whether the Gribov copy is the same (a different copy is
+    allowed: the plain method is the judge, through theta and F)."""
     import time
 
     import torch
-    dims = (8, 8, 8, 8)
-    train = [I.synthetic_config(dims, seed=100 + k, link_scale=0.5) for k in range(16)]
-    evals = [I.synthetic_config(dims, seed=200 + k, link_scale=0.5) for k in range(6)]
-    net = lgf.WarmStartNet(seed=5)
+    from lgf_inputs import torch_gen
+
+    def cfg(dims, seed):
+        return torch_gen.synthetic_config(dims, seed=seed, link_scale=0.5, gauge_scale=1.0, device="cuda")
+
+    net = lgf.WarmStartNet(seed=0)
     rows = []
     try:
+        with lgf.GaugeFixer((16, 16, 16, 16), "f32") as gf:
+            for k in range(2000):
+                gf.load_links(cfg((16, 16, 16, 16), 1000 + k))
+                net.train_step(gf, 1e-5)
+        dims = (24, 24, 24, 24)
         with lgf.GaugeFixer(dims, "f32") as gf:
-            for _ in range(8):
-                for U in train:
-                    gf.load_links(U)
-                    net.train_step(gf, 1e-5)
-        with lgf.GaugeFixer(dims, "f32") as gf:
-            gf.load_links(evals[0])
+            gf.load_links(cfg(dims, 4999))
             gf.fix(1e-15, 2000)  # builds the handle's loop graphs for both arms
-            for Ue in evals:
+            for k in range(4):
+                Ue = cfg(dims, 5000 + k)
+                F_in = O.functional(Ue.cpu().numpy())[0]
                 gf.load_links(Ue)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -177,17 +184,74 @@ def test_warm_start_cuts_iterations(lgf):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 net.warm_start(gf)
+                torch.cuda.synchronize()
+                t_inf = time.perf_counter() - t0
                 F_start = gf.functional()[0]
+                t0 = time.perf_counter()
                 it_warm, conv_w = gf.fix(1e-15, 2000)
-                t_warm = time.perf_counter() - t0
+                t_warm = time.perf_counter() - t0 + t_inf
                 F_warm, th = gf.functional()
                 assert conv_p and conv_w and th < 1e-15
-                assert F_start > O.functional(Ue)[0]
-                rows.append((it_plain, it_warm, t_plain, t_warm, F_plain, F_warm))
+                assert F_start > F_in + 0.1
+                rows.append((it_plain, it_warm, t_plain, t_warm, t_inf, F_plain, F_warm))
     finally:
         net.close()
-    for it_p, it_w, t_p, t_w, F_p, F_w in rows:
+    for it_p, it_w, t_p, t_w, t_i, F_p, F_w in rows:
         same = abs(F_w - F_p) < 1e-12 * abs(F_p)
-        print(f"\nwarm start on 8^4: iterations plain {it_p}, warm {it_w}; time plain {t_p * 1e3:.2f} ms, "
-              f"warm (with inference) {t_w * 1e3:.2f} ms; {'same' if same else 'different'} Gribov copy")
+        print(f"\nwarm start on 24^4: iterations plain {it_p}, warm {it_w}; time plain {t_p * 1e3:.2f} ms, "
+              f"warm {t_w * 1e3:.2f} ms (inference {t_i * 1e3:.2f} ms); "
+              f"{'same' if same else 'different'} Gribov copy")
     assert sum(r[1] for r in rows) < sum(r[0] for r in rows)
+
+
+@pytest.mark.parametrize("layer,backward", [(1, False), (2, False), (3, False), (2, True), (3, True)])
+def test_tensor_core_convolution_is_exact_on_dyadic_inputs(lgf, layer, backward):
+    """The tcgen05 implicit-GEMM convolutions, one layer at a time through
+    lgf_net_conv, element by element against the oracle's FP64 convolution.
+    Activations are multiples of 1/4 in [-1, 1] and weights multiples of 1/8
+    in [-3/8, 3/8] (both exact in BF16), biases multiples of 1/32: every
+    product and every partial sum is a multiple of 1/32 below 2^11 in
+    magnitude, so the FP32 accumulation is exact in any order and the BF16
+    rounding of the result (to nearest even on both sides) must agree bit for
+    bit.  The lattice (6, 4, 4, 6) has V = 576 sites: the last 128-site tile is
+    half empty.  In the backward case the padded output channels 8..15 of
+    layer 3 carry nonzero gradients that the zero padding must ignore."""
+    import torch
+    dims = (6, 4, 4, 6)
+    shp = I.lattice_shape(dims)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(40 + layer + 10 * int(backward))
+    net = lgf.WarmStartNet(seed=1)
+    try:
+        n1, n2, n3 = N1, N2, N3
+        p = np.concatenate([rng.integers(-3, 4, n1) / 8, rng.integers(-8, 9, 32) / 32,
+                            rng.integers(-3, 4, n2) / 8, rng.integers(-8, 9, 32) / 32,
+                            rng.integers(-3, 4, n3) / 8, rng.integers(-8, 9, 8) / 32]).astype(np.float32)
+        net.set_params(p)
+        (W1, b1), (W2, b2), (W3, b3) = unpack(p)
+        W, b = [(W1, b1), (W2, b2), (W3, b3)][layer - 1]
+        cin, cout = W.shape[1], W.shape[2]
+        if not backward:
+            x = rng.integers(-4, 5, (V, cin)) / 4
+            xt = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).cuda()
+            yf = torch.empty((V, 16), dtype=torch.float32, device="cuda") if layer == 3 else None
+            y = net.conv(layer, False, xt, dims, out_f32=yf).float().cpu().numpy()
+            ref = WO.conv(x.reshape(shp + (cin,)), W, b).reshape(V, cout)
+            if layer < 3:
+                ref = np.maximum(ref, 0.0)
+            assert np.array_equal(y[:, :cout], bf16(ref))
+            if layer == 3:
+                assert np.all(y[:, cout:] == 0)
+                assert np.array_equal(yf.cpu().numpy()[:, :cout], ref)
+        else:
+            nout = 16 if layer == 3 else 32
+            gy = rng.integers(-4, 5, (V, nout)) / 4
+            mask = rng.choice([-1.0, 0.0, 0.5, 1.0], (V, cin))
+            gyt = torch.tensor(gy, dtype=torch.float32).to(torch.bfloat16).cuda()
+            mt = torch.tensor(mask, dtype=torch.float32).to(torch.bfloat16).cuda()
+            gx = net.conv(layer, True, gyt, dims, mask=mt).float().cpu().numpy()
+            ref, _, _ = WO.conv_backward(np.zeros(shp + (cin,)), W, gy[:, :cout].reshape(shp + (cout,)))
+            ref = ref.reshape(V, cin) * (mask > 0)
+            assert np.array_equal(gx, bf16(ref))
+    finally:
+        net.close()
