@@ -426,7 +426,10 @@ def arm_single(lgf, torch, W, steps: int, warmup: int, params=(), Ud=None) -> di
     with lgf.GaugeFixer(dims, W["dtype"], stream=stream, alpha=W["alpha"]) as gf:
         for k, v in params:
             gf.set_param(k, v)
+        gf.load_links(Ud)
+        gf.autotune(reps=10)
         out = measure_handle(torch, gf, stream, Ud, W, steps, warmup, V, gauge_rep)
+        out["fft_schedule"] = list(gf.schedule())
     out["workload"] = W["desc"]
     return out
 
@@ -502,7 +505,7 @@ def batch_measure(lgf, torch, W, steps: int, warmup: int, lanes_arg: int = -1) -
             "gpu_launches": launches, "_window": (w0, w1)}
 
 
-def warm_measure(lgf, torch, W, ntr: int) -> dict:
+def warm_measure(lgf, torch, W, ntr: int, profile_range: bool = False) -> dict:
     """Train the warm-start network on the GPU, then fix unseen larger
     configurations with and without it."""
     import numpy as np
@@ -545,10 +548,14 @@ def warm_measure(lgf, torch, W, ntr: int) -> dict:
         Fp = ge.functional()[0]
         ge.load_links(u)
         torch.cuda.synchronize()
+        if profile_range:
+            torch.cuda.profiler.start()
         a = time.perf_counter()
         net.warm_start(ge)
         torch.cuda.synchronize()
         tw0 = time.perf_counter() - a
+        if profile_range:
+            torch.cuda.profiler.stop()
         Fw0 = ge.functional()[0]
         a = time.perf_counter()
         it_w, cw = ge.fix(W["tol"], W["max_iter"])
@@ -643,6 +650,13 @@ def run_ours(args, W):
         if args.tail_theta > 0:
             gf.set_param(2, args.tail_theta)  # LGF_TAIL_THETA
     gf.load_links(Ud)
+    schedule = None
+    if not args.no_autotune:
+        # the library's FFT schedule autotuner (pipeline, z-t tile width,
+        # radix order) on this shape, before anything is timed
+        gf.autotune(reps=10)
+        schedule = gf.schedule()
+        gf.load_links(Ud)
     smi = ClockSampler(gpu_id_for_smi(torch)) if rank == 0 else None
     try:
         gf.iterate(args.warmup)
@@ -653,10 +667,14 @@ def run_ours(args, W):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         w0 = time.time()
+        if args.profile_range:
+            torch.cuda.profiler.start()
         ev0.record(stream)
         gf.iterate(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        if args.profile_range:
+            torch.cuda.profiler.stop()
         w1 = time.time()
         barrier()
         ms = ev0.elapsed_time(ev1)
@@ -763,6 +781,8 @@ def run_ours(args, W):
         "dtype": "f32" if prec == 4 else "f64",
         "data": "synthetic (seeded SU(3) links behind a random gauge; stands in for thermalised ensembles)",
         "config": main_config(W, world, gauge_rep),
+        "fft_schedule": ({"autotuned": True, "pipeline": schedule[0], "zt_tile_width": schedule[1],
+                          "radix_order": schedule[2]} if schedule else {"autotuned": False}),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(ach / hbm_peak, 4) if ach else None,
                      "traffic": profile_traffic(dom, args.workload, gauge_rep),
@@ -899,7 +919,7 @@ def run_warm(args, W):
 
     torch.cuda.set_device(0)
     ntr = args.train_n if args.train_n else W["train_n"]
-    w = warm_measure(lgf, torch, W, ntr)
+    w = warm_measure(lgf, torch, W, ntr, args.profile_range)
     return {
         "metric": METRIC, "value": w["value"], "unit": METRIC, "n_gpus": 1,
         "steps": w["train_steps"], "warmup": 0, "ms_per_step": w["ms_per_train_step"],
@@ -949,6 +969,8 @@ def run_reference(args, W):
         "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": main_config(W, world, gauge_rep),
+        "fft_schedule": ({"autotuned": True, "pipeline": schedule[0], "zt_tile_width": schedule[1],
+                          "radix_order": schedule[2]} if schedule else {"autotuned": False}),
         "sample_lattice": list(dims),
         "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -968,6 +990,10 @@ def main():
     ap.add_argument("--train-n", type=int, default=0, help="warm-start workload: training configurations")
     ap.add_argument("--tail-theta", type=float, default=0.0, help="theta at which the FP32 phase hands over")
     ap.add_argument("--lanes", type=int, default=-1, help="batch workload: parallel graph lanes (0: one per member)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT schedule")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps (default workload) or the warm-start inferences (warm-start "
+                         "workload) with cudaProfilerStart/Stop, for ncu --profile-from-start off")
     ap.add_argument("--arms", default="all",
                     help="default workload: comparison arms to add, comma-separated from "
                          + ",".join(ARMS) + ", or 'all' / 'none'")

@@ -260,38 +260,52 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ x, co
 
 // ---------------------------------------------------------------------------
 // convolutions on the 5th-generation tensor cores (tcgen05): implicit GEMM
-//   D[s, n] = sum_tap sum_k A_tap[s, k] B_tap[n, k],  A_tap[s, k] = act[s + SIGN off(tap), k]
-// with M = 128 consecutive sites per CTA, N = the output channels and K = the
+//   D[m, n] = sum_tap sum_k A_tap[m, k] B_tap[n, k],  A_tap[m, k] = act[site(m) + SIGN off(tap), k]
+// with M = 128 output rows per CTA, N = the output channels and K = the
 // gathered channels of one tap (16 per instruction).  Forward: act = x,
 // B_tap = W^T (K-major copy [tap][out][in]), bias and ReLU in the epilogue.
 // Backward data: act = gy, SIGN = -1, B_tap = W[tap][in][out] (already
 // K-major in the output channels), the ReLU mask of the layer below in the
 // epilogue.
 //
-// Pipeline: kTcStages shared-memory stages, each holding one tap's A tile
-// (128 rows x K bf16) and B tile (N rows x K) in the no-swizzle K-major
-// canonical layout -- core matrices of 8 rows x 16 bytes, (row r, 16-byte
-// chunk c) at (r / 8) SBO + c 128 + (r % 8) 16 with SBO = 16 K bytes.  All 128
-// threads gather their own site's row with 16-byte cp.async copies, a tap
-// S - 1 ahead of the one being multiplied; one thread issues the K / 16 MMAs
-// of a tap into the FP32 accumulator in tensor memory (128 lanes x N
-// columns) and commits them to the stage's mbarrier, which frees the stage
-// for its next tap.  Epilogue: each warp reads its 32 lanes (sites) with
-// tcgen05.ld.  Every wait is bounded: on expiry the CTA records an error in
-// *err, stops issuing, waits (bounded) for its MMAs, frees its tensor memory
-// and returns.
+// Rows.  The M rows of a CTA are 128 consecutive rows of the lattice's
+// x-lines padded by one periodic halo row at each end (Lx + 2 rows per line:
+// x = Lx-1, 0, ..., Lx-1, 0); rows on a halo are computed and discarded.
+// The three taps that differ only in dx then read the same gathered rows one
+// row apart: for each of the 27 (dy, dz, dt) the CTA gathers one buffer of
+// 130 padded rows (its 128 and one on each side) at line offset SIGN (dy,
+// dz, dt), and the MMAs of dx = -1, 0, 1 start 16 bytes apart in it.  That is
+// a third of the gathering of one buffer per tap.
+//
+// Shared memory, per pipeline stage: the buffer and the three taps' B tiles,
+// each "chunk-major" K-major -- 16-byte chunk c of row r at c * ROWS * 16 +
+// r * 16 -- which is the no-swizzle canonical layout with SBO = 128 (the next
+// 8 rows) and LBO = ROWS * 16 (the next 8 channels).  A warp's 32 rows of one
+// chunk are 512 contiguous bytes, so the gathers write shared memory without
+// bank conflicts.
+//
+// Pipeline: kTcStages stages; all 128 threads gather (cp.async, L1-cached:
+// neighbouring groups gather overlapping rows), one thread issues the 3 K/16
+// MMAs of a group into the FP32 accumulator in tensor memory (128 lanes x N
+// columns) and commits them to the stage's mbarrier.  A group's MMAs are
+// issued before the previous group's stage is waited for and refilled, so
+// the tensor core always has work queued.  Epilogue: each warp reads its 32
+// lanes with tcgen05.ld.  Every wait is bounded: on expiry the CTA records an
+// error in *err, stops issuing, waits (bounded) for its MMAs, frees its
+// tensor memory and returns.
 // ---------------------------------------------------------------------------
 constexpr int kTcStages = 3;
 constexpr int kTcTmemCols = 32;
+constexpr int kTcBufRows = 136;  // 130 gathered rows, rounded up to whole 8-row groups
 constexpr unsigned kTcWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 bytes (the
-// next 16-byte chunk along K), SBO = the next 8-row group
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t sbo) {
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = bytes to the
+// next 16-byte chunk along K, sbo = bytes to the next 8-row group
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version of this architecture
   return d;
@@ -330,13 +344,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
+// 16-byte asynchronous copy global -> shared, cached in L1 (.ca): the rows a
+// CTA gathers for neighbouring groups overlap, and L1 serves the repeats
 __device__ __forceinline__ void cp_async16(uint32_t sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(gsrc) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(gsrc) : "memory");
 }
 
 template <int K, int N>
 constexpr int tc_stage_bytes() {
-  return (128 + N) * K * 2;
+  return (kTcBufRows + 3 * N) * K * 2;
+}
+
+__device__ __forceinline__ int wrap_add(int c, int d, int L) {
+  int v = c + d;
+  return v < 0 ? v + L : (v >= L ? v - L : v);
 }
 
 template <int K, int N, int SIGN, bool FWD>
@@ -345,27 +366,51 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
                                                  bf16* __restrict__ y, float* __restrict__ yf, const Geom geo,
                                                  bool relu, int* __restrict__ err) {
   static_assert(K % 16 == 0 && (N == 16 || N == 32), "tile shapes of this kernel");
-  constexpr int NCH = K / 8;           // 16-byte chunks per row
-  constexpr int SBO = NCH * 128;       // bytes per 8-row group
-  constexpr int A_BYTES = 128 * K * 2;
+  constexpr int NCH = K / 8;                         // 16-byte chunks per row
+  constexpr int A_LBO = kTcBufRows * 16;             // next chunk of the buffer
+  constexpr int A_BYTES = NCH * A_LBO;
+  constexpr int B_LBO = N * 16;                      // next chunk of a B tile
+  constexpr int B_TAP = NCH * B_LBO;
   constexpr int STAGE = tc_stage_bytes<K, N>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kTcStages + 1];
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
   const int t = threadIdx.x, w = t >> 5;
-  const int V = (int)geo.V;
-  const int s = blockIdx.x * 128 + t;
-  const bool valid = s < V;
-  int c[4] = {0, 0, 0, 0};
-  if (valid) site_coords_r(geo, s, c);
+  const int Lx = geo.L[0], Ly = geo.L[1], Lz = geo.L[2], Lt = geo.L[3];
+  const int LXP = Lx + 2;
+  const int lines = Ly * Lz * Lt;
+  const int PR = lines * LXP;              // padded rows
+  const int P0 = blockIdx.x * 128;
+  // this thread's output row
+  int s_out = -1;
+  {
+    const int P = P0 + t;
+    if (P < PR) {
+      const int l = P / LXP, xp = P - l * LXP;
+      if (xp >= 1 && xp <= Lx) s_out = (xp - 1) + Lx * l;
+    }
+  }
+  // this thread's buffer rows b = t and (t < 2) b = 128 + t: padded row
+  // P0 - 1 + b as (x, y, z, t) of its source line, or absent
+  int rx[2], ry[2], rz[2], rt[2];
+  bool rv[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int b = t + 128 * k;
+    const int P = P0 - 1 + b;
+    rv[k] = (k == 0 || b < 130) && P >= 0 && P < PR;
+    rx[k] = ry[k] = rz[k] = rt[k] = 0;
+    if (rv[k]) {
+      const int l = P / LXP, xp = P - l * LXP;
+      rx[k] = xp == 0 ? Lx - 1 : (xp == Lx + 1 ? 0 : xp - 1);
+      ry[k] = l % Ly;
+      const int l2 = l / Ly;
+      rz[k] = l2 % Lz;
+      rt[k] = l2 / Lz;
+    }
+  }
   const uint32_t sbase = smem_u32(smem_raw);
-  // rows past the end of the lattice stay zero in every stage
-  if (!valid)
-    for (int k = 0; k < kTcStages; ++k)
-      for (int ch = 0; ch < NCH; ++ch)
-        *reinterpret_cast<uint4*>(smem_raw + k * STAGE + (t >> 3) * SBO + ch * 128 + (t & 7) * 16) =
-            make_uint4(0, 0, 0, 0);
   if (t == 0) {
     for (int k = 0; k <= kTcStages; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[k])) : "memory");
@@ -383,71 +428,93 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  // gather tap `tap` into stage `tap % kTcStages`: this thread's row of A,
-  // and its share of the N x K tile of B
-  auto fill = [&](int tap) {
-    const uint32_t st = sbase + (tap % kTcStages) * STAGE;
-    if (valid) {
-      const int nb = tap_site(geo, c, tap, SIGN);
-      const bf16* src = act + (size_t)nb * K;
-      const uint32_t dst = st + (t >> 3) * SBO + (t & 7) * 16;
+  // gather group g = (dy, dz, dt) into stage g % kTcStages: this thread's
+  // buffer rows (zeros where a padded row lies outside the lattice) and its
+  // share of the three taps' N x K B tiles
+  auto fill = [&](int g) {
+    const uint32_t st = sbase + (g % kTcStages) * STAGE;
+    const int dy = SIGN * (g % 3 - 1), dz = SIGN * ((g / 3) % 3 - 1), dt = SIGN * (g / 9 - 1);
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) cp_async16(dst + ch * 128, src + ch * 8);
+    for (int k = 0; k < 2; ++k) {
+      const int b = t + 128 * k;
+      if (k == 1 && b >= 130) break;
+      const uint32_t dst = st + b * 16;
+      if (rv[k]) {
+        const int src = rx[k] + Lx * (wrap_add(ry[k], dy, Ly) + Ly * (wrap_add(rz[k], dz, Lz) + Lz * wrap_add(rt[k], dt, Lt)));
+        const bf16* p = act + (size_t)src * K;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) cp_async16(dst + c * A_LBO, p + c * 8);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+          asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(dst + c * A_LBO), "r"(0) : "memory");
+      }
     }
-    const bf16* wsrc = Wk + (size_t)tap * N * K;
-    for (int j = t; j < N * NCH; j += 128) {
-      const int n = j / NCH, ch = j % NCH;
-      cp_async16(st + A_BYTES + (n >> 3) * SBO + ch * 128 + (n & 7) * 16, wsrc + n * K + ch * 8);
+    const bf16* wsrc = Wk + (size_t)(3 * g) * N * K;
+    for (int j = t; j < 3 * N * NCH; j += 128) {
+      const int tp = j / (N * NCH), r = j % (N * NCH), n = r / NCH, c = r % NCH;
+      cp_async16(st + A_BYTES + tp * B_TAP + c * B_LBO + n * 16, wsrc + (tp * N + n) * K + c * 8);
     }
   };
 
   constexpr uint32_t idesc = tc_idesc<N>();
+  // every stage starts filled (groups 0 .. S-1, one copy group each); in the
+  // loop a group's MMAs are issued first, then the stage of the previous
+  // group is refilled S groups ahead once its MMAs have drained.  Copy
+  // groups: group g is copy group g, so it has landed when at most S - 2
+  // copy groups committed after it are pending.
 #pragma unroll 1
-  for (int tap = 0; tap < kTcStages - 1; ++tap) {
-    fill(tap);
+  for (int g = 0; g < kTcStages; ++g) {
+    fill(g);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  int issued = -1;  // last tap whose MMAs were issued
+  int issued = -1;  // last group whose MMAs were issued
 #pragma unroll 1
-  for (int tap = 0; tap < 81; ++tap) {
-    const int next = tap + kTcStages - 1;
-    if (next < 81) {
-      // the stage of `next` was last read by the MMAs of tap - 1
-      bool ok = true;
-      if (tap >= 1) ok = mbar_wait(&bars[(tap - 1) % kTcStages], (uint32_t)(((tap - 1) / kTcStages) & 1));
-      if (__syncthreads_or(!ok)) {
-        if (t == 0) atomicExch(err, 1);
-        break;
-      }
-      fill(next);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 1) : "memory");
+  for (int g = 0; g < 27; ++g) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 2) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (t == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = sbase + (tap % kTcStages) * STAGE;
+      const uint32_t st = sbase + (g % kTcStages) * STAGE;
 #pragma unroll
-      for (int q = 0; q < K / 16; ++q)
-        tc_mma(tmem, tc_desc(st + q * 256, SBO), tc_desc(st + A_BYTES + q * 256, SBO), idesc,
-               (tap > 0 || q > 0) ? 1u : 0u);
-      tc_commit(&bars[tap % kTcStages]);
+      for (int dxp = 0; dxp < 3; ++dxp) {
+        // output row m reads buffer row m + 1 + SIGN dx
+        const uint32_t a0 = st + (uint32_t)(1 + SIGN * (dxp - 1)) * 16;
+        const uint32_t b0 = st + A_BYTES + dxp * B_TAP;
+#pragma unroll
+        for (int q = 0; q < K / 16; ++q)
+          tc_mma(tmem, tc_desc(a0 + q * 2 * A_LBO, A_LBO, 128), tc_desc(b0 + q * 2 * B_LBO, B_LBO, 128), idesc,
+                 (g > 0 || dxp > 0 || q > 0) ? 1u : 0u);
+      }
+      tc_commit(&bars[g % kTcStages]);
     }
-    issued = tap;
+    issued = g;
+    if (g >= 1) {
+      const int next = g - 1 + kTcStages;
+      if (next < 27) {
+        // the stage of group g - 1 is free once its MMAs have completed
+        const bool ok = mbar_wait(&bars[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1));
+        if (__syncthreads_or(!ok)) {
+          if (t == 0) atomicExch(err, 1);
+          break;
+        }
+        fill(next);
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   // all MMAs issued so far have completed once the last commit's phase does
-  bool ok = true;
   if (t == 0 && issued >= 0) {
     tc_commit(&bars[kTcStages]);
-    ok = mbar_wait(&bars[kTcStages], 0u);
+    const bool ok = mbar_wait(&bars[kTcStages], 0u);
     if (!ok) atomicExch(err, 1);
-    stop = !ok || issued < 80;
+    stop = !ok || issued < 26;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!stop && issued == 80) {
+  if (!stop && issued == 26) {
     float acc[32];
     uint32_t r[32];
     const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16);
@@ -473,24 +540,25 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = __uint_as_float(r[j]);
-    if (valid) {
+    if (s_out >= 0) {
+      const int so = s_out;
       if constexpr (FWD) {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          float v = acc[j] + bias[j];
+          const float v = acc[j] + bias[j];
           acc[j] = relu ? fmaxf(v, 0.0f) : v;
         }
         if (yf != nullptr)
 #pragma unroll
           for (int j = 0; j < N; j += 4)
-            *reinterpret_cast<float4*>(yf + (size_t)s * N + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+            *reinterpret_cast<float4*>(yf + (size_t)so * N + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
       } else if (mask != nullptr) {
-        const bf16* mrow = mask + (size_t)s * N;
+        const bf16* mrow = mask + (size_t)so * N;
 #pragma unroll
         for (int j = 0; j < N; ++j)
           if (!(__bfloat162float(mrow[j]) > 0.0f)) acc[j] = 0.0f;
       }
-      bf16* out = y + (size_t)s * N;
+      bf16* out = y + (size_t)so * N;
 #pragma unroll
       for (int j = 0; j < N; j += 8) {
         uint4 q;
@@ -798,8 +866,13 @@ template <int K, int N, int SIGN, bool FWD>
 cudaError_t conv_tc_launch(const void* act, const void* Wk, const float* bias, const void* mask, void* y, float* yf,
                            const Geom& geo, bool relu, int* err, cudaStream_t s) {
   constexpr int smem = kTcStages * tc_stage_bytes<K, N>();
-  static_assert(smem <= 48 * 1024, "the stages fit the default dynamic shared memory cap");
-  const unsigned nb = (unsigned)((geo.V + 127) / 128);
+  static_assert(smem <= 227 * 1024, "the stages fit one CTA's shared memory");
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_conv_tc<K, N, SIGN, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (attr != cudaSuccess) return attr;
+  // 128 rows per CTA over the x-lines padded by one halo row at each end
+  const int64_t rows = geo.V / geo.L[0] * (geo.L[0] + 2);
+  const unsigned nb = (unsigned)((rows + 127) / 128);
   k_conv_tc<K, N, SIGN, FWD><<<nb, 128, smem, s>>>(static_cast<const bf16*>(act), static_cast<const bf16*>(Wk), bias,
                                                     static_cast<const bf16*>(mask), static_cast<bf16*>(y), yf, geo,
                                                     relu, err);

@@ -204,8 +204,9 @@ def test_warm_start_cuts_iterations(lgf):
     assert sum(r[1] for r in rows) < sum(r[0] for r in rows)
 
 
+@pytest.mark.parametrize("dims", [(6, 4, 3, 6), (16, 4, 2, 2)])
 @pytest.mark.parametrize("layer,backward", [(1, False), (2, False), (3, False), (2, True), (3, True)])
-def test_tensor_core_convolution_is_exact_on_dyadic_inputs(lgf, layer, backward):
+def test_tensor_core_convolution_is_exact_on_dyadic_inputs(lgf, layer, backward, dims):
     """The tcgen05 implicit-GEMM convolutions, one layer at a time through
     lgf_net_conv, element by element against the oracle's FP64 convolution.
     Activations are multiples of 1/4 in [-1, 1] and weights multiples of 1/8
@@ -213,11 +214,12 @@ def test_tensor_core_convolution_is_exact_on_dyadic_inputs(lgf, layer, backward)
     product and every partial sum is a multiple of 1/32 below 2^11 in
     magnitude, so the FP32 accumulation is exact in any order and the BF16
     rounding of the result (to nearest even on both sides) must agree bit for
-    bit.  The lattice (6, 4, 4, 6) has V = 576 sites: the last 128-site tile is
-    half empty.  In the backward case the padded output channels 8..15 of
-    layer 3 carry nonzero gradients that the zero padding must ignore."""
+    bit.  The kernels take 128 rows of x-lines padded by one periodic halo row
+    at each end: (6, 4, 3, 6) gives 72 lines of 8 rows, 4.5 tiles; (16, 4, 2,
+    2) 16 lines of 18 rows, 2.25 tiles, each tile spanning several lines.  In
+    the backward case the padded output channels 8..15 of layer 3 carry
+    nonzero gradients that the zero padding must ignore."""
     import torch
-    dims = (6, 4, 4, 6)
     shp = I.lattice_shape(dims)
     V = int(np.prod(dims))
     rng = np.random.default_rng(40 + layer + 10 * int(backward))
