@@ -208,56 +208,6 @@ __device__ __forceinline__ int tap_site(const Geom& geo, const int c[4], int tap
          geo.L[0] * (wrapc(c[1], d1, geo.L[1]) + geo.L[1] * (wrapc(c[2], d2, geo.L[2]) + geo.L[2] * wrapc(c[3], d3, geo.L[3])));
 }
 
-// y[s, o] = act(b[o] + sum_tap sum_i W[tap, i, o] x[s + off(tap), i]); one
-// warp per 16 consecutive sites (V is a multiple of 16), 4 warps per block.
-// Optionally also the FP32 result (yf, [V][COUT]).
-template <int CIN, int COUT, bool RELU>
-__global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ x, const bf16* __restrict__ W,
-                                                  const float* __restrict__ b, bf16* __restrict__ y,
-                                                  float* __restrict__ yf, const Geom geo) {
-  __shared__ __align__(32) bf16 sA[4][16 * 16];
-  __shared__ __align__(32) float sC[4][16 * COUT];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int V = (int)geo.V;
-  const int s0 = (blockIdx.x * 4 + warp) * 16;
-  if (s0 >= V) return;  // warp-uniform; only warp-level synchronisation below
-  const int row = lane >> 1, half = lane & 1;
-  const int s = s0 + row;
-  int c[4];
-  site_coords_i(geo.L, s, c);
-  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[COUT / 16];
-#pragma unroll
-  for (int n = 0; n < COUT / 16; ++n) wm::fill_fragment(acc[n], 0.0f);
-  for (int tap = 0; tap < 81; ++tap) {
-    const int nb = tap_site(geo, c, tap, +1);
-#pragma unroll
-    for (int k0 = 0; k0 < CIN; k0 += 16) {
-      *reinterpret_cast<uint4*>(&sA[warp][row * 16 + half * 8]) =
-          *reinterpret_cast<const uint4*>(x + (size_t)nb * CIN + k0 + half * 8);
-      __syncwarp();
-      wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> a;
-      wm::load_matrix_sync(a, &sA[warp][0], 16);
-#pragma unroll
-      for (int n = 0; n < COUT / 16; ++n) {
-        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> bm;
-        wm::load_matrix_sync(bm, W + ((size_t)tap * CIN + k0) * COUT + n * 16, COUT);
-        wm::mma_sync(acc[n], a, bm, acc[n]);
-      }
-      __syncwarp();
-    }
-  }
-#pragma unroll
-  for (int n = 0; n < COUT / 16; ++n) wm::store_matrix_sync(&sC[warp][n * 16], acc[n], COUT, wm::mem_row_major);
-  __syncwarp();
-#pragma unroll
-  for (int o = half * (COUT / 2); o < (half + 1) * (COUT / 2); ++o) {
-    float v = sC[warp][row * COUT + o] + b[o];
-    if (RELU) v = fmaxf(v, 0.0f);
-    y[(size_t)s * COUT + o] = __float2bfloat16_rn(v);
-    if (yf != nullptr) yf[(size_t)s * COUT + o] = v;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // convolutions on the 5th-generation tensor cores (tcgen05): implicit GEMM
 //   D[m, n] = sum_tap sum_k A_tap[m, k] B_tap[n, k],  A_tap[m, k] = act[site(m) + SIGN off(tap), k]
@@ -578,55 +528,6 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
 }
 
-// gx[s, i] = mask(s, i) * sum_tap sum_o W[tap, i, o] gy[s - off(tap), o], with
-// mask = (a[s, i] > 0) when a is given (the ReLU of the layer below).
-template <int CI, int CO>
-__global__ void __launch_bounds__(128) k_conv_bwd_data(const bf16* __restrict__ gy, const bf16* __restrict__ W,
-                                                       const bf16* __restrict__ a, bf16* __restrict__ gx,
-                                                       const Geom geo) {
-  __shared__ __align__(32) bf16 sA[4][16 * 16];
-  __shared__ __align__(32) float sC[4][16 * CI];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int V = (int)geo.V;
-  const int s0 = (blockIdx.x * 4 + warp) * 16;
-  if (s0 >= V) return;
-  const int row = lane >> 1, half = lane & 1;
-  const int s = s0 + row;
-  int c[4];
-  site_coords_i(geo.L, s, c);
-  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[CI / 16];
-#pragma unroll
-  for (int n = 0; n < CI / 16; ++n) wm::fill_fragment(acc[n], 0.0f);
-  for (int tap = 0; tap < 81; ++tap) {
-    const int nb = tap_site(geo, c, tap, -1);
-#pragma unroll
-    for (int k0 = 0; k0 < CO; k0 += 16) {
-      *reinterpret_cast<uint4*>(&sA[warp][row * 16 + half * 8]) =
-          *reinterpret_cast<const uint4*>(gy + (size_t)nb * CO + k0 + half * 8);
-      __syncwarp();
-      wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> am;
-      wm::load_matrix_sync(am, &sA[warp][0], 16);
-#pragma unroll
-      for (int n = 0; n < CI / 16; ++n) {
-        // B[k = o][n = i] = W[tap, i, o]: column-major with leading dimension CO
-        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::col_major> bm;
-        wm::load_matrix_sync(bm, W + ((size_t)tap * CI + n * 16) * CO + k0, CO);
-        wm::mma_sync(acc[n], am, bm, acc[n]);
-      }
-      __syncwarp();
-    }
-  }
-#pragma unroll
-  for (int n = 0; n < CI / 16; ++n) wm::store_matrix_sync(&sC[warp][n * 16], acc[n], CI, wm::mem_row_major);
-  __syncwarp();
-#pragma unroll
-  for (int i = half * (CI / 2); i < (half + 1) * (CI / 2); ++i) {
-    float v = sC[warp][row * CI + i];
-    if (a != nullptr && !(__bfloat162float(a[(size_t)s * CI + i]) > 0.0f)) v = 0.0f;
-    gx[(size_t)s * CI + i] = __float2bfloat16_rn(v);
-  }
-}
-
 // gW[tap, i, o] += sum_s x[s + off(tap), i] gy[s, o]: block (chunk group,
 // tap); each warp accumulates 16-site chunks on the tensor cores and adds its
 // tile to gW with FP32 atomics (so the sum order, and its last bits, vary).
@@ -787,38 +688,6 @@ cudaError_t launch_expmap(int nc, const float* c, int ldc, void* G, int V, cudaS
 
 cudaError_t launch_signal(const void* D, int V, float coef, void* gc, cudaStream_t s) {
   k_signal<<<nb128(V), 128, 0, s>>>(static_cast<const cx<float>*>(D), V, coef, static_cast<bf16*>(gc));
-  return cudaPeekAtLastError();
-}
-
-// layer 1: 48 -> 32 (ReLU), 2: 32 -> 32 (ReLU), 3: 32 -> 16 (8 used, FP32 copy)
-cudaError_t launch_conv_fwd(int layer, const void* x, const void* W, const float* b, void* y, float* yf,
-                            const Geom& geo, cudaStream_t s) {
-  const unsigned nb = (unsigned)((geo.V / 16 + 3) / 4);
-  const bf16* xp = static_cast<const bf16*>(x);
-  const bf16* Wp = static_cast<const bf16*>(W);
-  bf16* yp = static_cast<bf16*>(y);
-  if (layer == 1)
-    k_conv_fwd<kFeat, kHid, true><<<nb, 128, 0, s>>>(xp, Wp, b, yp, yf, geo);
-  else if (layer == 2)
-    k_conv_fwd<kHid, kHid, true><<<nb, 128, 0, s>>>(xp, Wp, b, yp, yf, geo);
-  else
-    k_conv_fwd<kHid, kOutPad, false><<<nb, 128, 0, s>>>(xp, Wp, b, yp, yf, geo);
-  return cudaPeekAtLastError();
-}
-
-// gradient with respect to the input of layer 3 (32 <- 16) or 2 (32 <- 32),
-// masked by the ReLU of the layer below (a)
-cudaError_t launch_conv_bwd_data(int layer, const void* gy, const void* W, const void* a, void* gx,
-                                 const Geom& geo, cudaStream_t s) {
-  const unsigned nb = (unsigned)((geo.V / 16 + 3) / 4);
-  const bf16* gyp = static_cast<const bf16*>(gy);
-  const bf16* Wp = static_cast<const bf16*>(W);
-  const bf16* ap = static_cast<const bf16*>(a);
-  bf16* gxp = static_cast<bf16*>(gx);
-  if (layer == 3)
-    k_conv_bwd_data<kHid, kOutPad><<<nb, 128, 0, s>>>(gyp, Wp, ap, gxp, geo);
-  else
-    k_conv_bwd_data<kHid, kHid><<<nb, 128, 0, s>>>(gyp, Wp, ap, gxp, geo);
   return cudaPeekAtLastError();
 }
 

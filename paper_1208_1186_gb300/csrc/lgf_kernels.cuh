@@ -175,10 +175,6 @@ constexpr int kParams = 81 * 48 * 32 + 32 + 81 * 32 * 32 + 32 + 81 * 32 * 8 + 8;
 cudaError_t launch_features(int nc, const void* U0, void* x, const Geom& geo, cudaStream_t s);
 cudaError_t launch_expmap(int nc, const float* c, int ldc, void* G, int V, cudaStream_t s);
 cudaError_t launch_signal(const void* D, int V, float coef, void* gc, cudaStream_t s);
-cudaError_t launch_conv_fwd(int layer, const void* x, const void* W, const float* b, void* y, float* yf,
-                            const Geom& geo, cudaStream_t s);
-cudaError_t launch_conv_bwd_data(int layer, const void* gy, const void* W, const void* a, void* gx,
-                                 const Geom& geo, cudaStream_t s);
 cudaError_t launch_conv_bwd_weight(int layer, const void* x, const void* gy, float* gW, const Geom& geo,
                                    cudaStream_t s);
 cudaError_t launch_bias_grad(int co, const void* gy, float* gb, int V, cudaStream_t s);
