@@ -18,6 +18,7 @@
 // pipeline).  The packed gradient crosses memory three times per iteration
 // instead of seven.
 #include "fft_reg.cuh"
+#include "lgf_df.cuh"
 #include "lgf_gstep.cuh"
 #include "lgf_kernels.cuh"
 
@@ -278,6 +279,58 @@ __global__ void __launch_bounds__(128) k_plane_xyinv_gstep(const cx<float>* __re
   }
 }
 
+// The double-float tail's inverse x-y pass fused with its gauge step
+// (tail_eta_site), as k_plane_xyinv_gstep fuses the FP32 phase's G update:
+// four warps inverse-transform the four fields of the CTA's planes, Delta~
+// stays in shared memory, and after one CTA barrier the 128 threads update
+// 1 + eta at the planes' sites.  The transforms are those of
+// k_plane_xy_warp, so the result is bit-identical to the unfused pass plus
+// k_tail_eta_step.
+template <int L>
+__global__ void __launch_bounds__(128) k_plane_xyinv_eta(const cx<float>* __restrict__ D, cx<float>* __restrict__ eh,
+                                                         cx<float>* __restrict__ el, int V, int nplanes, float h,
+                                                         const DevState* __restrict__ st) {
+  static_assert(L <= 32, "a warp holds at least one tile");
+  pdl_wait();
+  if (st != nullptr && st->done) return;
+  constexpr int GP = 32 / L, P = L + 1, N = L * L, TS = L * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tiles = reinterpret_cast<cx<float>*>(smem_raw);  // [field][plane of the CTA][y][x]
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / L, r = lane % L;
+  const int plane0 = blockIdx.x * GP;
+  const bool active = g < GP && plane0 + g < nplanes;
+  cx<float>* tile = tiles + (f * GP + (active ? g : 0)) * TS;
+  if (active) {  // inverse y-line r from global memory into column r
+    const cx<float>* src = D + ((int64_t)f * V + (int64_t)(plane0 + g) * N);
+    cx<float> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = src[p * L + r];
+    regfft::inverse<float, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[p * P + r] = v[p];
+  }
+  __syncwarp();
+  if (active) {  // inverse x-line r in row r
+    cx<float> v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = tile[r * P + p];
+    regfft::inverse<float, L>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p) tile[r * P + p] = v[p];
+  }
+  __syncthreads();
+  const int np = nplanes - plane0 < GP ? nplanes - plane0 : GP;
+  const int ns = np * N;
+  const int base = plane0 * N;
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+    const int gi = q / N, qq = q - gi * N;
+    const int o = gi * TS + (qq / L) * P + qq % L;
+    tail_eta_site(tiles[o], tiles[GP * TS + o], tiles[2 * GP * TS + o], tiles[3 * GP * TS + o], h, eh, el, V,
+                  base + q);
+  }
+}
+
 template <int L>
 constexpr size_t xyinv_gstep_smem() {
   return (size_t)4 * (L <= 32 ? 32 / L : 1) * L * (L + 1) * sizeof(cx<float>);
@@ -470,6 +523,7 @@ cudaError_t plane_pipeline_init() {
 #undef LGF_XYA32
 #undef LGF_XYA64
   if (e == cudaSuccess) e = plane_zt_init();
+  if (e == cudaSuccess) e = plane_xyinv_eta_init();
   return e;
 }
 
@@ -487,6 +541,47 @@ cudaError_t launch_plane_xy(int prec, int L, void* D, int64_t V, int Lz, int Lt,
 #undef LGF_XY32
 #undef LGF_XY64
   return cudaErrorInvalidValue;
+}
+
+bool plane_xyinv_eta_supported(int L) {
+  switch (L) {
+    case 4: case 6: case 8: case 12: case 16: case 20: case 24: case 32:
+      return kFuseXyinvGstep;
+    default:
+      return false;
+  }
+}
+
+cudaError_t plane_xyinv_eta_init() {
+  cudaError_t e = cudaSuccess;
+#define LGF_ETA_ATTR(L)                                                                           \
+  if (e == cudaSuccess)                                                                           \
+    e = cudaFuncSetAttribute(k_plane_xyinv_eta<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)xyinv_gstep_smem<L>());
+  LGF_ETA_ATTR(4) LGF_ETA_ATTR(6) LGF_ETA_ATTR(8) LGF_ETA_ATTR(12) LGF_ETA_ATTR(16) LGF_ETA_ATTR(20) LGF_ETA_ATTR(24)
+  LGF_ETA_ATTR(32)
+#undef LGF_ETA_ATTR
+  return e;
+}
+
+cudaError_t launch_plane_xyinv_eta(int L, const void* D, void* eta, int64_t V, int Lz, int Lt, double half_alpha,
+                                   const DevState* st, cudaStream_t s) {
+  const int nplanes = Lz * Lt;
+  const auto Dp = static_cast<const cx<float>*>(D);
+  auto e = static_cast<cx<float>*>(eta);
+  const float h = (float)half_alpha;
+#define LGF_ETA_L(N)                                                                                              \
+  case N: {                                                                                                       \
+    const unsigned nb = (unsigned)((nplanes + 32 / N - 1) / (32 / N));                                           \
+    return launch_pdl(k_plane_xyinv_eta<N>, nb, 128, xyinv_gstep_smem<N>(), s, Dp, e, e + 9 * V, (int)V, nplanes, \
+                      h, st);                                                                                     \
+  }
+  switch (L) {
+    LGF_ETA_L(4) LGF_ETA_L(6) LGF_ETA_L(8) LGF_ETA_L(12) LGF_ETA_L(16) LGF_ETA_L(20) LGF_ETA_L(24) LGF_ETA_L(32)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef LGF_ETA_L
 }
 
 bool plane_xyinv_gstep_supported(int prec, int L) {

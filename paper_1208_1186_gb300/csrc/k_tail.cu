@@ -575,12 +575,10 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_eta(const cx<float>* _
   grid_reduce_warp_totals(wf, (double)tsum, partial, st, normF, normT, mode);
 }
 
-// 1 + eta <- (1 + eps)(1 + eta), eps = X + X^2/2, eta in double-float (hi
-// planes, then lo planes): eta <- eta + X + (X^2/2 + eps eta_hi).  X, exactly
-// anti-Hermitian, enters by exact two-sums; only the small Hermitian terms
-// (|X|^2 ~ 1e-10) are rounded in FP32.  So 1 + eta stays unitary to O(|X|^3)
-// plus ~1e-17, where rounding X + X^2/2 as one FP32 sum would break unitarity
-// by 2^-24 |X| at every step.
+// 1 + eta <- (1 + eps)(1 + eta) at every site (tail_eta_site, lgf_df.cuh),
+// from the accelerated gradient in global memory; where the plane pipeline
+// applies, the same step is fused with the inverse x-y transform instead
+// (k_plane_xyinv_eta).
 __global__ void __launch_bounds__(128, 5) k_tail_eta_step(const cx<float>* __restrict__ D, cx<float>* __restrict__ eh,
                                                        cx<float>* __restrict__ el, int V, float h,
                                                        const DevState* __restrict__ st) {
@@ -588,46 +586,7 @@ __global__ void __launch_bounds__(128, 5) k_tail_eta_step(const cx<float>* __res
   if (st != nullptr && st->done) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const cx<float> c0 = ldg(D + s), c1 = ldg(D + V + s), c2 = ldg(D + 2 * V + s), c3 = ldg(D + 3 * V + s);
-  M3<float> X;
-  X.e[0][0] = mk<float>(0.f, h * c3.re);
-  X.e[1][1] = mk<float>(0.f, h * c3.im);
-  X.e[2][2] = mk<float>(0.f, -h * (c3.re + c3.im));
-  X.e[0][1] = scale(c0, h);
-  X.e[0][2] = scale(c1, h);
-  X.e[1][2] = scale(c2, h);
-  X.e[1][0] = mk<float>(-h * c0.re, h * c0.im);
-  X.e[2][0] = mk<float>(-h * c1.re, h * c1.im);
-  X.e[2][1] = mk<float>(-h * c2.re, h * c2.im);
-  M3<float> n;
-  cx<float> lo[9];  // all of eta's loads issued before any arithmetic
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    n.e[q / 3][q % 3] = eh[q * V + s];
-    lo[q] = el[q * V + s];
-  }
-  // small terms: X^2/2 + (X + X^2/2) eta_hi
-  M3<float> Y;
-  mm<float, 3>(Y, X, X);
-  M3<float> e = X;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      Y.e[i][j] = scale(Y.e[i][j], 0.5f);
-      e.e[i][j] = e.e[i][j] + Y.e[i][j];
-    }
-  mm_acc(Y, e, n);
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const int i = q / 3, j = q % 3;
-    df re = two_sum(n.e[i][j].re, X.e[i][j].re);
-    df im = two_sum(n.e[i][j].im, X.e[i][j].im);
-    re = fast_two_sum(re.h, __fadd_rn(re.l, __fadd_rn(lo[q].re, Y.e[i][j].re)));
-    im = fast_two_sum(im.h, __fadd_rn(im.l, __fadd_rn(lo[q].im, Y.e[i][j].im)));
-    eh[q * V + s] = mk<float>(re.h, im.h);
-    el[q * V + s] = mk<float>(re.l, im.l);
-  }
+  tail_eta_site(ldg(D + s), ldg(D + V + s), ldg(D + 2 * V + s), ldg(D + 3 * V + s), h, eh, el, V, s);
 }
 
 // U <- U' (the caller then clears eta): one thread per (site, direction), a

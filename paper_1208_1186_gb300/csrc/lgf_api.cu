@@ -465,6 +465,17 @@ int queue_iteration(lgf_handle h, Engine& e) {
     Engine& f = h->e32;
     LGF_LAUNCH(h, LGF_K_GRADIENT,
                launch_gradient_tail_eta(h->Udf, h->eta, h->tbase, f.D, h->partial, h->geo, h->st, 1, s));
+    if (pick_pipeline(h, f) == 3 && plane_xyinv_eta_supported(h->L[0])) {
+      // forward x-y, z-t, then the inverse x-y pass fused with the eta step
+      const int* L = h->L;
+      LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(f.prec, L[0], f.D, h->V, L[2], L[3], 0, h->st, s));
+      LGF_LAUNCH(h, LGF_K_FFT_ZT,
+                 launch_plane_zt(f.prec, L[0], L[1], L[2], L[3], f.D, f.kfac, f.s2p, f.c_over_V, f.zt_bx, f.zt_ro,
+                                 h->st, s));
+      LGF_LAUNCH(h, LGF_K_XY_GSTEP,
+                 launch_plane_xyinv_eta(L[0], f.D, h->eta, h->V, L[2], L[3], 0.5 * h->alpha, h->st, s));
+      return LGF_OK;
+    }
     int rc = queue_accelerate(h, f, h->st);
     if (rc) return rc;
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_tail_eta_step(f.D, h->eta, h->V, 0.5 * h->alpha, h->st, s));

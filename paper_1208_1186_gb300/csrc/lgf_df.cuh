@@ -213,4 +213,54 @@ __device__ __forceinline__ void tail_link_exact(const M3<float>& uh, const cx<fl
     }
 }
 
+// The tail's gauge step at site s: 1 + eta <- (1 + eps)(1 + eta), eps = X +
+// X^2/2, X = h Delta~ from the packed accelerated gradient (c0..c3), eta in
+// double-float (eh: hi planes, el: lo planes, 9 complex planes each):
+// eta <- eta + X + (X^2/2 + eps eta_hi).  X, exactly anti-Hermitian, enters by
+// exact two-sums; only the small Hermitian terms (|X|^2 ~ 1e-10) are rounded
+// in FP32.  So 1 + eta stays unitary to O(|X|^3) plus ~1e-17, where rounding
+// X + X^2/2 as one FP32 sum would break unitarity by 2^-24 |X| at every step.
+__device__ __forceinline__ void tail_eta_site(cx<float> c0, cx<float> c1, cx<float> c2, cx<float> c3, float h,
+                                              cx<float>* __restrict__ eh, cx<float>* __restrict__ el, int V, int s) {
+  M3<float> X;
+  X.e[0][0] = mk<float>(0.f, h * c3.re);
+  X.e[1][1] = mk<float>(0.f, h * c3.im);
+  X.e[2][2] = mk<float>(0.f, -h * (c3.re + c3.im));
+  X.e[0][1] = scale(c0, h);
+  X.e[0][2] = scale(c1, h);
+  X.e[1][2] = scale(c2, h);
+  X.e[1][0] = mk<float>(-h * c0.re, h * c0.im);
+  X.e[2][0] = mk<float>(-h * c1.re, h * c1.im);
+  X.e[2][1] = mk<float>(-h * c2.re, h * c2.im);
+  M3<float> n;
+  cx<float> lo[9];  // all of eta's loads issued before any arithmetic
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    n.e[q / 3][q % 3] = eh[q * V + s];
+    lo[q] = el[q * V + s];
+  }
+  // small terms: X^2/2 + (X + X^2/2) eta_hi
+  M3<float> Y;
+  mm<float, 3>(Y, X, X);
+  M3<float> e = X;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Y.e[i][j] = scale(Y.e[i][j], 0.5f);
+      e.e[i][j] = e.e[i][j] + Y.e[i][j];
+    }
+  mm_acc(Y, e, n);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const int i = q / 3, j = q % 3;
+    df re = two_sum(n.e[i][j].re, X.e[i][j].re);
+    df im = two_sum(n.e[i][j].im, X.e[i][j].im);
+    re = fast_two_sum(re.h, __fadd_rn(re.l, __fadd_rn(lo[q].re, Y.e[i][j].re)));
+    im = fast_two_sum(im.h, __fadd_rn(im.l, __fadd_rn(lo[q].im, Y.e[i][j].im)));
+    eh[q * V + s] = mk<float>(re.h, im.h);
+    el[q * V + s] = mk<float>(re.l, im.l);
+  }
+}
+
 }  // namespace lgf

@@ -131,6 +131,12 @@ cudaError_t launch_plane_zt(int prec, int Lx, int Ly, int Lz, int Lt, void* D, c
 // inverse x-y pass fused with G <- g G (FP32 gauge representation; Lx = Ly
 // one of 4, 6, 8, 12, 16, 20, 24, 32)
 bool plane_xyinv_gstep_supported(int prec, int L);
+// the double-float tail's inverse x-y pass fused with its eta step (FP32
+// packed gradient, Lx = Ly one of 4, 6, 8, 12, 16, 20, 24, 32)
+bool plane_xyinv_eta_supported(int L);
+cudaError_t plane_xyinv_eta_init();
+cudaError_t launch_plane_xyinv_eta(int L, const void* D, void* eta, int64_t V, int Lz, int Lt, double half_alpha,
+                                   const DevState* st, cudaStream_t s);
 cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int64_t V, int Lz, int Lt,
                                      double half_alpha, bool reunit_fp64, const DevState* st, cudaStream_t s);
 
