@@ -244,7 +244,7 @@ __device__ __forceinline__ int tap_site(const Geom& geo, const int c[4], int tap
 // error in *err, stops issuing, waits (bounded) for its MMAs, frees its
 // tensor memory and returns.
 // ---------------------------------------------------------------------------
-constexpr int kTcStages = 3;
+constexpr int kTcStages = 2;
 constexpr int kTcTmemCols = 32;
 constexpr int kTcBufRows = 136;  // 130 gathered rows, rounded up to whole 8-row groups
 constexpr unsigned kTcWaitLimit = 1u << 22;
