@@ -289,3 +289,32 @@ def test_oracle_matches_brute_force(dims):
         assert hist[0][0] == pytest.approx(Fb, rel=1e-13)
         assert hist[0][1] == pytest.approx(thb, rel=1e-12)
         assert BF.max_diff(links, Uo) < 1e-13
+
+
+def test_pack_delta_holds_the_eight_real_degrees_of_freedom():
+    """pack_delta (the 4-complex packing the GPU's gradient planes use): a
+    traceless anti-Hermitian matrix is X = i sum_a c_a lambda_a / 2, built here
+    from the Gell-Mann matrices with known c_a; its packed form must hold
+    X01, X02, X12 and Im X00 + i Im X11 (closed forms in the c_a checked too),
+    so a wrong index, sign or conjugate in the packing fails.  Unpacking the
+    4 numbers by the anti-Hermitian, traceless rules rebuilds X exactly."""
+    rng = np.random.default_rng(31)
+    lam = I.gell_mann()
+    c = rng.normal(size=(5, 8))
+    X = np.einsum("na,aij->nij", 0.5j * c, lam)
+    P = O.pack_delta(X)
+    assert P.shape == (5, 4)
+    for n in range(5):
+        x00, x11 = X[n, 0, 0].imag, X[n, 1, 1].imag
+        assert P[n, 0] == X[n, 0, 1] and P[n, 1] == X[n, 0, 2] and P[n, 2] == X[n, 1, 2]
+        assert P[n, 3] == x00 + 1j * x11
+        # closed forms of the entries from the coefficients
+        assert np.isclose(X[n, 0, 1], 0.5j * (c[n, 0] - 1j * c[n, 1]))
+        assert np.isclose(x00, 0.5 * (c[n, 2] + c[n, 7] / math.sqrt(3)))
+        # rebuild from the 4 numbers
+        R = np.zeros((3, 3), complex)
+        R[0, 1], R[0, 2], R[1, 2] = P[n, 0], P[n, 1], P[n, 2]
+        R[1, 0], R[2, 0], R[2, 1] = -np.conj(P[n, 0]), -np.conj(P[n, 1]), -np.conj(P[n, 2])
+        R[0, 0], R[1, 1] = 1j * P[n, 3].real, 1j * P[n, 3].imag
+        R[2, 2] = -1j * (P[n, 3].real + P[n, 3].imag)
+        assert np.allclose(R, X[n], atol=1e-15)
