@@ -434,7 +434,7 @@ def arm_single(lgf, torch, W, steps: int, warmup: int, params=(), Ud=None) -> di
     return out
 
 
-def batch_measure(lgf, torch, W, steps: int, warmup: int, lanes_arg: int = -1) -> dict:
+def batch_measure(lgf, torch, W, steps: int, warmup: int, lanes_arg: int = -1, fft_tune: bool = True) -> dict:
     """The batched workload (lgf_batch): site-iterations/s over all members,
     the time to fix all of them, and the step-level roofline."""
     import numpy as np
@@ -453,8 +453,9 @@ def batch_measure(lgf, torch, W, steps: int, warmup: int, lanes_arg: int = -1) -
             f.load_links(u)
         tuned = {}
         for f, s in zip(fixers, shapes):
-            ch = f.autotune(reps=5)
-            tuned.setdefault("x".join(map(str, s)), ch)
+            if fft_tune:
+                f.autotune(reps=5)
+            tuned.setdefault("x".join(map(str, s)), list(f.schedule()))
         Vtot = sum(int(np.prod(s)) for s in shapes)
         with lgf.GaugeBatch(fixers) as batch:
             lanes = lanes_arg
@@ -667,13 +668,13 @@ def run_ours(args, W):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         w0 = time.time()
-        if args.profile_range:
+        if args.profile_range == "steps":
             torch.cuda.profiler.start()
         ev0.record(stream)
         gf.iterate(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-        if args.profile_range:
+        if args.profile_range == "steps":
             torch.cuda.profiler.stop()
         w1 = time.time()
         barrier()
@@ -712,10 +713,18 @@ def run_ours(args, W):
         split = gf.fix_split()
         F, theta = gf.functional()
         # the same fix once more with per-kernel events, for the breakdown
+        # (host-queued iterations instead of the device-side graph loops, so
+        # that ncu, which cannot profile kernels inside graphs with conditional
+        # nodes, sees them: --profile-range fix brackets this fix)
         gf.load_links(Ud)
         torch.cuda.synchronize()
         gf.profile(True)
+        if args.profile_range == "fix":
+            torch.cuda.profiler.start()
         gf.fix(W["tol"], W["max_iter"])
+        if args.profile_range == "fix":
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         fix_prof = {k: round(v[0], 3) for k, v in gf.profile_read().items() if v[1]}
         fix_launches = {k: v[1] for k, v in gf.profile_read().items() if v[1]}
         gf.profile(False)
@@ -891,7 +900,7 @@ def run_batch(args, W):
     torch.cuda.set_device(0)
     smi = ClockSampler(gpu_id_for_smi(torch))
     try:
-        b = batch_measure(lgf, torch, W, args.steps, args.warmup, args.lanes)
+        b = batch_measure(lgf, torch, W, args.steps, args.warmup, args.lanes, not args.no_autotune)
     finally:
         smi.stop()
     w0, w1 = b.pop("_window")
@@ -919,7 +928,7 @@ def run_warm(args, W):
 
     torch.cuda.set_device(0)
     ntr = args.train_n if args.train_n else W["train_n"]
-    w = warm_measure(lgf, torch, W, ntr, args.profile_range)
+    w = warm_measure(lgf, torch, W, ntr, bool(args.profile_range))
     return {
         "metric": METRIC, "value": w["value"], "unit": METRIC, "n_gpus": 1,
         "steps": w["train_steps"], "warmup": 0, "ms_per_step": w["ms_per_train_step"],
@@ -990,10 +999,13 @@ def main():
     ap.add_argument("--train-n", type=int, default=0, help="warm-start workload: training configurations")
     ap.add_argument("--tail-theta", type=float, default=0.0, help="theta at which the FP32 phase hands over")
     ap.add_argument("--lanes", type=int, default=-1, help="batch workload: parallel graph lanes (0: one per member)")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT schedule")
-    ap.add_argument("--profile-range", action="store_true",
-                    help="bracket the timed steps (default workload) or the warm-start inferences (warm-start "
-                         "workload) with cudaProfilerStart/Stop, for ncu --profile-from-start off")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default FFT schedule (no lgf_autotune on the timed handles or batch members)")
+    ap.add_argument("--profile-range", choices=["", "steps", "fix"], default="", nargs="?", const="steps",
+                    help="bracket with cudaProfilerStart/Stop, for ncu --profile-from-start off: the timed steps "
+                         "(steps, the default of the bare flag) or the per-kernel-profiled (host-queued) fix to "
+                         "theta < tol (fix) of the single-lattice workloads, or the warm-start inferences of the "
+                         "warm-start workload")
     ap.add_argument("--arms", default="all",
                     help="default workload: comparison arms to add, comma-separated from "
                          + ",".join(ARMS) + ", or 'all' / 'none'")
