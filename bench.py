@@ -75,7 +75,7 @@ WORKLOADS["warmstart-f32"] = dict(
          "iterations and time to theta<1e-15 with and without the warm start")
 DEFAULT_WORKLOAD = "32^4-f32"
 KERNEL_SOURCES = {"update": "k_links.cu", "gradient": "k_links.cu", "build_g": "k_links.cu",
-                  "accumulate": "k_links.cu", "fft_xy": "k_fft_plane.cu", "fft_zt": "k_fft_plane.cu",
+                  "accumulate": "k_links.cu", "fft_xy": "k_fft_plane.cu", "fft_zt": "k_fft_zt.cu",
                   "fft_axis": "k_fft_axis.cu", "fft_t": "k_fft_axis.cu", "xy_gstep": "k_fft_plane.cu"}
 
 
@@ -268,17 +268,32 @@ def oracle_fix_iterations(case: str):
 
 # ---------------------------------------------------------------------------
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-COMMON_SOURCES = ("lgf_common.cuh", "lgf_reduce.cuh", "lgf_kernels.cuh", "fft_reg.cuh", "lgf_gstep.cuh")
+def include_closure(name: str) -> list:
+    """The translation unit `name` and every project header it includes
+    (#include "..."), transitively, in a fixed order."""
+    csrc = os.path.join(ROOT, "paper_1208_1186_gb300", "csrc")
+    seen, todo = [], [name]
+    while todo:
+        f = todo.pop(0)
+        if f in seen:
+            continue
+        seen.append(f)
+        for line in open(os.path.join(csrc, f)):
+            m = re.match(r'\s*#include\s+"([^"/]+)"', line)
+            if m and os.path.exists(os.path.join(csrc, m.group(1))):
+                todo.append(m.group(1))
+    return [seen[0]] + sorted(seen[1:])
 
 
 def kernel_source_hash(kernel: str, gauge_rep: bool) -> str | None:
-    """sha256 (16 hex) of the sources the kernel is compiled from."""
+    """sha256 (16 hex) of the sources the kernel is compiled from: its
+    translation unit and the project headers that unit includes."""
     name = "k_gauge_rep.cu" if (gauge_rep and kernel in ("gradient", "build_g")) else KERNEL_SOURCES.get(kernel)
     if name is None:
         return None
     h = hashlib.sha256()
     try:
-        for f in (name,) + COMMON_SOURCES:
+        for f in include_closure(name):
             h.update(open(os.path.join(ROOT, "paper_1208_1186_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
@@ -621,6 +636,28 @@ def oracle_arms(U_c2, U_c3, alpha: float) -> dict:
     return out
 
 
+def host_link_rates(torch, pinned_in, pinned_out, reps: int = 3) -> list:
+    """GB/s of one pinned host -> device and one device -> host copy of the
+    given buffers (best of reps, CUDA events on the current stream): the floor
+    under lgf_load_links and lgf_store_links, which move the same bytes."""
+    dev = torch.empty_like(pinned_in, device="cuda")
+    rates = []
+    for src, dst in ((pinned_in, dev), (dev, pinned_out)):
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+        rates.append(round(src.numel() * src.element_size() / (best * 1e-3) / 1e9, 1))
+    del dev
+    return rates
+
+
 def run_ours(args, W):
     import numpy as np
     import torch
@@ -754,6 +791,7 @@ def run_ours(args, W):
         _, _, e2e_warm_parts = e2e_pass()  # one untimed warm-up pass
         iters_e2e, e2e_local, e2e_parts = e2e_pass()
         e2e_s = max_over_ranks(e2e_local)
+        link = host_link_rates(torch, pinned, pinned_out)
     finally:
         if smi:
             smi.stop()
@@ -811,7 +849,11 @@ def run_ours(args, W):
                 "what": "lgf_load_links(pinned host) + lgf_fix(theta<tol) + lgf_store_links(pinned host)",
                 "parts": e2e_parts, "warmup_pass_parts": e2e_warm_parts,
                 "h2d_bytes_per_step": round(h2d / max(iters_e2e, 1), 1),
-                "d2h_bytes_per_step": round(d2h / max(iters_e2e, 1), 1)},
+                "d2h_bytes_per_step": round(d2h / max(iters_e2e, 1), 1),
+                "host_link": {"how": "plain pinned copies of the same link arrays (copy engine, CUDA events), "
+                                     "after the e2e passes",
+                              "h2d_gbs": link[0], "d2h_gbs": link[1],
+                              "load_store_floor_s": round(h2d / (link[0] * 1e9) + d2h / (link[1] * 1e9), 5)}},
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -281,7 +281,10 @@ int lgf_batch_autotune(lgf_batch b, int reps, int* lanes_out);
  * width of the z-t tiles (4 or 8 FP32 complex numbers, 2 or 4 FP64) and
  * the radix order of the z and t transforms (0: radix 4 first, 32 = 4 4 2;
  * 1: the same factors reversed, 32 = 2 4 4; FP32 only, where the stages
- * differ).  The paper (Sec. 2.2) transforms with cuFFT's fixed plans; this
+ * differ; 2: the pair split, FP32 lines of even length with one extent of
+ * 16 or more: two threads share each line, the first radix-2 stage runs
+ * across the pair and each thread transforms its half, which halves the
+ * registers per thread).  The paper (Sec. 2.2) transforms with cuFFT's fixed plans; this
  * search has no counterpart there.  Results are cached per (precision,
  * lattice shape) for the process; if the environment variable
  * LGF_TUNE_CACHE names a file, the cache is written there (JSON) after each
@@ -289,7 +292,9 @@ int lgf_batch_autotune(lgf_batch b, int reps, int* lanes_out);
  * iterates first (1 Stockham planes, 2 axis passes, 3 register planes).
  * Overwrites the gradient scratch only; the links are untouched.  Tile
  * widths give bit-identical results; radix orders round differently in
- * FP32 (the fix still ends at the same F to the FP64 tail's accuracy). */
+ * FP32 (the fix still ends at the same F to the FP64 tail's accuracy).
+ * Where an extent's pair-split stages equal those of order 1 (L = 8, 32),
+ * orders 1 and 2 give bit-identical results. */
 int lgf_autotune(lgf_handle h, int reps, int* chosen);
 
 /* The FFT schedule engine `engine` (0: the FP64 engine, 1: the FP32 engine of

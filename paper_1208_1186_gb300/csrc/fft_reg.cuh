@@ -280,5 +280,60 @@ __device__ __forceinline__ void inverse(cx<T>* a) {
   dit_inv_stages<T, L, L, RO>(a);
 }
 
+// ---------------------------------------------------------------------------
+// Pair-split transforms ("radix order 2"): a line of even length L shared by
+// two lanes l and l ^ 1 of a warp, half h = l & 1 holding elements
+// h L/2 ... h L/2 + L/2 - 1 in natural order.  The forward transform's first
+// stage is the radix-2 decimation-in-frequency butterfly between the halves,
+// done across the pair with shuffles; each lane then transforms its half
+// (length L/2, greedy radix order 0) in registers.  Afterwards element p of
+// half h holds frequency 2 digit_rev(L/2, p) + h.  The inverse undoes the
+// stages in reverse order and returns the halves in natural order.  For L = 8
+// and L = 32 the stage sequence (2, then 4s) is that of radix order 1, and
+// the results are bit-identical to it.  Both lanes of every pair must call
+// these (full-warp shuffles).
+
+constexpr int pair_freq(int L, int p, int h) { return 2 * digit_rev(L / 2, p, 0) + h; }
+
+constexpr bool pair_supported(int L) { return L % 2 == 0 && L >= 4 && supported(L / 2); }
+
+template <int L, int P, int HALF>
+struct MomentumSqPair {
+  static constexpr double s = turn_cs(pair_freq(L, P, HALF), 2 * L, 1);  // sin(pi k / L)
+  static constexpr double value = 4.0 * s * s;
+};
+
+template <class T>
+__device__ __forceinline__ cx<T> shfl_pair(cx<T> v) {
+  return mk<T>(__shfl_xor_sync(0xffffffffu, v.re, 1), __shfl_xor_sync(0xffffffffu, v.im, 1));
+}
+
+template <class T, int L>
+__device__ __forceinline__ void forward_pair(cx<T>* a, int h) {
+  constexpr int H = L / 2;
+  static_for<0, H>([&](auto nc) {
+    constexpr int n = decltype(nc)::value;
+    const cx<T> o = shfl_pair(a[n]);
+    // half 0: a_n + a_{n+H}; half 1: (a_n - a_{n+H}) W_L^n
+    const cx<T> sum = a[n] + o;
+    const cx<T> dif = mul_tw<T, L, n, false>(o - a[n]);
+    a[n] = h ? dif : sum;
+  });
+  dif_stages<T, H, H, 0>(a);
+}
+
+template <class T, int L>
+__device__ __forceinline__ void inverse_pair(cx<T>* a, int h) {
+  constexpr int H = L / 2;
+  dit_inv_stages<T, H, H, 0>(a);
+  static_for<0, H>([&](auto nc) {
+    constexpr int n = decltype(nc)::value;
+    // half 1 sends b_n conj(W_L^n); half 0 sends a_n
+    const cx<T> mine = h ? mul_tw<T, L, n, true>(a[n]) : a[n];
+    const cx<T> o = shfl_pair(mine);
+    a[n] = h ? o - mine : mine + o;
+  });
+}
+
 }  // namespace regfft
 }  // namespace lgf

@@ -58,7 +58,8 @@ struct Engine {
   int zt_ro = 0;         // plane pipeline: radix order of the z and t transforms
   bool grep = false;     // FP32 engine: gauge representation (U holds the loaded links, G is updated)
   void* kfac = nullptr;  // axis pipeline, FP64: p2_max/(V p2(k)) per site, digit-reversed order
-  float* s2p = nullptr;  // FP32: [2][4][kMaxL] 4 sin^2(pi k/L) at the digit-reversed positions of radix order 0, 1
+  float* s2p = nullptr;  // FP32: [3][4][kMaxL] 4 sin^2(pi k/L) at the digit-reversed positions of radix order 0, 1
+                         // and at the tile slots of order 2 (the pair split)
   float c_over_V = 0.f;  // p2_max / V
   size_t cbytes() const { return 2 * (size_t)prec; }
 };
@@ -253,7 +254,7 @@ int alloc_engine(lgf_handle h, Engine& e) {
     // acceleration factor at every position the forward passes leave a mode:
     // position p along an axis holds frequency digit_rev(L, p)
     std::vector<double> s2[4];
-    std::vector<float> s2f(2 * 4 * kMaxL, 0.0f);
+    std::vector<float> s2f(3 * 4 * kMaxL, 0.0f);
     double p2max = 0.0;
     for (int a = 0; a < 4; ++a) {
       const int L = h->L[a];
@@ -269,6 +270,12 @@ int alloc_engine(lgf_handle h, Engine& e) {
         const long double sk1 = sinl(3.14159265358979323846264338327950288L *
                                      (long double)regfft::digit_rev(L, p, 1) / (long double)L);
         s2f[4 * kMaxL + a * kMaxL + p] = (float)(4.0L * sk1 * sk1);
+        // the pair split: slot 2 q + half holds frequency pair_freq(L, q, half)
+        if (regfft::pair_supported(L)) {
+          const long double sk2 = sinl(3.14159265358979323846264338327950288L *
+                                       (long double)regfft::pair_freq(L, p >> 1, p & 1) / (long double)L);
+          s2f[2 * 4 * kMaxL + a * kMaxL + p] = (float)(4.0L * sk2 * sk2);
+        }
       }
       p2max += m;
     }
@@ -689,7 +696,7 @@ int tune_engine(lgf_handle h, Engine& e, int reps, TuneEntry* out) {
   if (e.plane) {
     const int b0 = e.prec == 4 ? 4 : 2;
     for (int bx : {0, 2 * b0})
-      for (int ro : {0, 1})
+      for (int ro : {0, 1, 2})
         if (plane_zt_schedule_supported(e.prec, h->L[0], h->L[2], h->L[3], bx, ro)) cands.push_back({3, bx, ro});
   }
   cudaEvent_t a, b;

@@ -7,6 +7,10 @@ autotuner may pick computes the same Fourier acceleration.
   differently in FP32: the accelerated gradient matches the oracle within
   the FP32 tolerance of the other parity tests, and a fix to theta < 1e-15
   ends at the oracle's F to 1e-12.
+- The pair split (radix order 2: two threads per line, the first radix-2
+  stage across the pair) has the stage sequence of the reversed order for
+  lines of 8 and 32, and gives bit-identical results there; elsewhere it is
+  a third factorisation, checked against the oracle like the reversed order.
 - lgf_autotune picks one of them; a cache file written under LGF_TUNE_CACHE
   and loaded back gives new handles of that shape the same schedule.
 """
@@ -72,6 +76,28 @@ def test_reversed_radix_order_matches_the_oracle(lgf, dims, bx):
     ref_fix = O.fix(U, 1e-15, 2000, ALPHA)
     dt, _, it, F, _ = run(lgf, dims, "f32", (3, bx, 1), U, 1)
     # FP32 forward + inverse FFT: error ~ eps log2 V of the largest entry
+    assert np.max(np.abs(dt - Dt_ref)) <= 4e-6 * np.max(np.abs(Dt_ref))
+    assert F == pytest.approx(ref_fix["F"], rel=1e-12)
+
+
+@pytest.mark.parametrize("bx", [0, 8])
+def test_pair_split_equals_the_reversed_order_for_lines_of_32_and_8(lgf, bx):
+    dims = (16, 16, 32, 8)
+    U = I.synthetic_config(dims, seed=14, link_scale=0.5)
+    ref = run(lgf, dims, "f32", (3, bx, 1), U, 5)
+    got = run(lgf, dims, "f32", (3, bx, 2), U, 5)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    assert got[2] == ref[2] and got[3] == ref[3] and np.array_equal(got[4], ref[4])
+
+
+@pytest.mark.parametrize("bx", [0, 8])
+def test_pair_split_matches_the_oracle(lgf, bx):
+    dims = (16, 16, 16, 16)
+    U = I.synthetic_config(dims, seed=15, link_scale=0.5)
+    parts = O.step_parts(U, ALPHA)
+    Dt_ref = O.pack_delta(parts["Delta_tilde"])
+    ref_fix = O.fix(U, 1e-15, 2000, ALPHA)
+    dt, _, it, F, _ = run(lgf, dims, "f32", (3, bx, 2), U, 1)
     assert np.max(np.abs(dt - Dt_ref)) <= 4e-6 * np.max(np.abs(Dt_ref))
     assert F == pytest.approx(ref_fix["F"], rel=1e-12)
 

@@ -3,8 +3,8 @@ GPU): lgf_tune_load takes the valid entries of a file into the process
 cache, lgf_tune_lookup reads them back, lgf_tune_save writes a file that is
 valid JSON and loads back to the same cache, and entries no engine could run
 (a tile width that does not divide Lx, a radix order where the stages would
-not change or in FP64, a pipeline the lattice does not support) are
-rejected."""
+not change or in FP64, a pair split without kernels for the lattice, a
+pipeline the lattice does not support) are rejected."""
 import ctypes
 import json
 
@@ -19,6 +19,7 @@ VALID = [
     (8, (32, 32, 32, 32), 3, 4, 0),   # FP64: widths 2 (default, 0) and 4
     (4, (16, 16, 16, 16), 2, 0, 0),   # per-axis passes
     (8, (10, 4, 6, 12), 1, 0, 0),     # Stockham planes
+    (4, (24, 24, 24, 24), 3, 0, 2),   # pair-split z and t transforms
 ]
 INVALID = [
     (4, (20, 20, 20, 20), 3, 8, 0),   # 8 does not divide Lx = 20
@@ -28,6 +29,8 @@ INVALID = [
     (4, (32, 32, 32, 32), 2, 4, 0),   # a tile width outside the plane pipeline
     (2, (32, 32, 32, 32), 1, 0, 0),   # no 2-byte precision
     (4, (32, 32, 32, 70), 1, 0, 0),   # extent beyond 64
+    (4, (8, 8, 8, 8), 3, 0, 2),       # no pair-split kernels for lines this short
+    (8, (16, 16, 16, 16), 3, 0, 2),   # the pair split is FP32 only
 ]
 
 
