@@ -87,6 +87,40 @@ def test_one_step_matches_oracle(lgf, dims, dtype, planes):
     np.testing.assert_allclose(U1, ref["U_next"], rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f32_r12"])
+@pytest.mark.parametrize("dims", STEP_DIMS)
+def test_fp32_step_matches_oracle(lgf, dims, dtype):
+    """One step of the FP32 engine (gauge representation, 18 or 12 reals)
+    against the FP64 oracle on the same shapes.  Tolerances: rounding the
+    input links to FP32 alone moves the oracle's Delta by ~3e-7 (|Delta| up
+    to ~14), its Delta~ by ~2e-8 of max |Delta~|, g by ~3e-8 and the next
+    links by ~6e-8; the FP32 products (27 MACs per product, ten products per
+    site) and the FP32 FFT (~eps log2 V) add about an order of magnitude.  The
+    bounds on Delta and Delta~ sit 10-50 times above that; F and theta carry
+    FP64 sums above the warp.  g = reunit(1 + (alpha/2) Delta~) moves by at
+    most alpha/2 times the error of Delta~ plus its own FP32 rounding, and the
+    next links g U g'^dag by twice that (the acceleration factor reaches
+    p2_max / (4 sin^2(pi/64)) ~ 1700 on 64-long lines, so there Delta~ and g
+    carry the largest absolute errors)."""
+    U = I.synthetic_config(dims, seed=3, link_scale=0.5)
+    ref = O.step_parts(U, ALPHA)
+    with lgf.GaugeFixer(dims, dtype) as gf:
+        gf.load_links(U)
+        out = gf.probe()
+        F, th = gf.functional()
+        gf.iterate(1)
+        U1 = gf.store_links()
+    d_ref, dt_ref = _packed(ref["Delta"]), _packed(ref["Delta_tilde"])
+    tol_dt = 4e-6 * np.max(np.abs(dt_ref))
+    tol_g = ALPHA / 2 * tol_dt + 1e-6
+    assert np.max(np.abs(out["delta"] - d_ref)) <= 2e-6 * np.max(np.abs(d_ref))
+    assert np.max(np.abs(out["delta_tilde"] - dt_ref)) <= tol_dt
+    np.testing.assert_allclose(out["g"], ref["g"], rtol=0, atol=tol_g)
+    assert F == pytest.approx(ref["F"], rel=2e-6)
+    assert th == pytest.approx(ref["theta"], rel=2e-5)
+    np.testing.assert_allclose(U1, ref["U_next"], rtol=0, atol=2 * tol_g + 1e-6)
+
+
 @pytest.mark.parametrize("n", [10, 50, 200])
 def test_iterate_matches_oracle_c1(lgf, n):
     """8^4 FP64, links scale 0.3 behind a gauge of scale 1.0, seed 0."""
