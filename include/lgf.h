@@ -385,6 +385,16 @@ int lgf_net_warm_start(lgf_net n, lgf_handle h);
 int lgf_net_conv(lgf_net n, int layer, int backward, const void* in, const void* mask, void* out, float* out_f32,
                  int Lx, int Ly, int Lz, int Lt, void* stream);
 
+/* Poll budget of the waits inside the tensor-core convolutions that wait for
+ * a pipeline stage's MMAs (default and upper bound 2^22 polls; polls < 0
+ * restores the default).  With a budget of 0 every such wait expires at
+ * once: each CTA records the error, stops issuing, waits for the MMAs it has
+ * issued with the full budget, frees its tensor memory and returns, and the
+ * call that ran the convolution returns LGF_ERR_TIMEOUT with its output
+ * unspecified.  This is how the expiry path of those bounded waits is tested
+ * without a fault; the context stays usable.  Synchronises the device. */
+int lgf_net_set_wait_budget(lgf_net n, long long polls);
+
 /* Text of the last error of a network call (NULL: of lgf_net_create). */
 const char* lgf_net_last_error(lgf_net n);
 

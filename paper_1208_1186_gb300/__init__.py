@@ -286,6 +286,12 @@ class WarmStartNet:
                                           *[int(d) for d in dims], ctypes.c_void_p(st)), "lgf_net_conv")
         return out
 
+    def set_wait_budget(self, polls: int):
+        """Poll budget of the convolutions' stage waits (lgf_net_set_wait_budget;
+        negative: the default)."""
+        self._check(self.lib.lgf_net_set_wait_budget(self.n, ctypes.c_longlong(int(polls))),
+                    "lgf_net_set_wait_budget")
+
     def warm_start(self, gf: "GaugeFixer"):
         self._check(self.lib.lgf_net_warm_start(self.n, gf.h), "lgf_net_warm_start")
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "lgf_net_warm_start": (ctypes.c_int, [_P, _P]),
     "lgf_net_last_error": (ctypes.c_char_p, [_P]),
     "lgf_net_conv": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P] + [ctypes.c_int] * 4 + [_P]),
+    "lgf_net_set_wait_budget": (ctypes.c_int, [_P, ctypes.c_longlong]),
 }
 LGF_NUM_KERNELS = 10
 

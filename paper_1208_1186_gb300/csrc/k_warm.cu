@@ -241,13 +241,14 @@ __device__ __forceinline__ int tap_site(const Geom& geo, const int c[4], int tap
 // issued before the previous group's stage is waited for and refilled, so
 // the tensor core always has work queued.  Epilogue: each warp reads its 32
 // lanes with tcgen05.ld.  Every wait is bounded: on expiry the CTA records an
-// error in *err, stops issuing, waits (bounded) for its MMAs, frees its
-// tensor memory and returns.
+// error in err[0], stops issuing, waits (bounded) for its MMAs, frees its
+// tensor memory and returns.  err[1] holds the poll budget of the stage
+// waits (kConvWaitPolls unless lgf_net_set_wait_budget changed it).
 // ---------------------------------------------------------------------------
 constexpr int kTcStages = 2;
 constexpr int kTcTmemCols = 32;
 constexpr int kTcBufRows = 136;  // 130 gathered rows, rounded up to whole 8-row groups
-constexpr unsigned kTcWaitLimit = 1u << 22;
+constexpr unsigned kTcWaitLimit = (unsigned)kConvWaitPolls;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -281,10 +282,11 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                : "memory");
 }
 
-// bounded wait for the phase of parity `parity` of an mbarrier; true if done
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait (at most `polls` polls) for the phase of parity `parity` of an
+// mbarrier; true if done
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned polls) {
   uint32_t done = 0;
-  for (unsigned it = 0; it < kTcWaitLimit && !done; ++it) {
+  for (unsigned it = 0; it < polls && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
@@ -377,6 +379,10 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  // the stage waits' poll budget (err[1]); the final wait for the MMAs always
+  // has the full budget, so that no MMA is in flight when the CTA frees its
+  // tensor memory
+  const unsigned stage_polls = (unsigned)err[1];
 
   // gather group g = (dy, dz, dt) into stage g % kTcStages: this thread's
   // buffer rows (zeros where a padded row lies outside the lattice) and its
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
       const int next = g - 1 + kTcStages;
       if (next < 27) {
         // the stage of group g - 1 is free once its MMAs have completed
-        const bool ok = mbar_wait(&bars[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1));
+        const bool ok = mbar_wait(&bars[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1), stage_polls);
         if (__syncthreads_or(!ok)) {
           if (t == 0) atomicExch(err, 1);
           break;
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   // all MMAs issued so far have completed once the last commit's phase does
   if (t == 0 && issued >= 0) {
     tc_commit(&bars[kTcStages]);
-    const bool ok = mbar_wait(&bars[kTcStages], 0u);
+    const bool ok = mbar_wait(&bars[kTcStages], 0u, kTcWaitLimit);
     if (!ok) atomicExch(err, 1);
     stop = !ok || issued < 26;
   }

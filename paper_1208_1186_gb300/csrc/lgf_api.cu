@@ -1022,7 +1022,8 @@ struct lgf_net_ctx {
   void* W2 = nullptr;
   void* W3 = nullptr;  // bf16, last layer 16 wide
   void *Wt1 = nullptr, *Wt2 = nullptr, *Wt3 = nullptr;  // the same K-major ([tap][out][in]) for the forward
-  int* tc_err = nullptr;  // set by a tensor-core convolution whose bounded wait expired
+  int* tc_err = nullptr;  // [0] set by a tensor-core convolution whose bounded wait expired,
+                          // [1] the poll budget of the convolutions' stage waits
   float* b1 = nullptr;
   float* b2 = nullptr;
   float* b3 = nullptr;
@@ -1835,7 +1836,7 @@ int lgf_net_create(unsigned long long seed, lgf_net* out) {
   n->Wt1 = net_alloc(n, (size_t)kW1 * 2);
   n->Wt2 = net_alloc(n, (size_t)kW2 * 2);
   n->Wt3 = net_alloc(n, (size_t)81 * 32 * 16 * 2);
-  n->tc_err = static_cast<int*>(net_alloc(n, sizeof(int)));
+  n->tc_err = static_cast<int*>(net_alloc(n, 2 * sizeof(int)));
   n->b1 = static_cast<float*>(net_alloc(n, 32 * 4));
   n->b2 = static_cast<float*>(net_alloc(n, 32 * 4));
   n->b3 = static_cast<float*>(net_alloc(n, 16 * 4));
@@ -1847,9 +1848,10 @@ int lgf_net_create(unsigned long long seed, lgf_net* out) {
     lgf_net_destroy(n);
     return nfail(nullptr, LGF_ERR_OOM, msg);
   }
-  if (cudaMemset(n->tc_err, 0, sizeof(int)) != cudaSuccess) {
+  const int err_init[2] = {0, warm::kConvWaitPolls};
+  if (cudaMemcpy(n->tc_err, err_init, sizeof err_init, cudaMemcpyHostToDevice) != cudaSuccess) {
     lgf_net_destroy(n);
-    return nfail(nullptr, LGF_ERR_CUDA, "cudaMemset of the network's error flag failed");
+    return nfail(nullptr, LGF_ERR_CUDA, "initialising the network's error flag failed");
   }
   // He-normal initialisation; the last layer 100x smaller so that g0 starts
   // close to the identity (the warm start starts as "no warm start")
@@ -1879,6 +1881,14 @@ int lgf_net_destroy(lgf_net n) {
 int lgf_net_get_params(lgf_net n, float* host) {
   if (!n || !host) return LGF_ERR_ARG;
   LGF_NCUDA(n, cudaMemcpy(host, n->p, (size_t)warm::kParams * 4, cudaMemcpyDeviceToHost));
+  return LGF_OK;
+}
+
+int lgf_net_set_wait_budget(lgf_net n, long long polls) {
+  if (!n) return LGF_ERR_ARG;
+  const int v = polls < 0 ? warm::kConvWaitPolls : (int)(polls < warm::kConvWaitPolls ? polls : warm::kConvWaitPolls);
+  LGF_NCUDA(n, cudaDeviceSynchronize());
+  LGF_NCUDA(n, cudaMemcpy(n->tc_err + 1, &v, sizeof v, cudaMemcpyHostToDevice));
   return LGF_OK;
 }
 

@@ -188,8 +188,10 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, flo
                         float c2, float eps, cudaStream_t s);
 cudaError_t launch_pack_weights(const float* p, void* W1, void* W2, void* W3, float* b1, float* b2, float* b3,
                                 void* Wt1, void* Wt2, void* Wt3, cudaStream_t s);
-// tcgen05 implicit-GEMM convolutions (forward and backward data); *err is set
-// to 1 if a bounded wait inside a CTA expired
+// tcgen05 implicit-GEMM convolutions (forward and backward data); err[0] is
+// set to 1 if a bounded wait inside a CTA expired; err[1] is the poll budget
+// of the stage waits (kConvWaitPolls by default)
+constexpr int kConvWaitPolls = 1 << 22;
 cudaError_t launch_conv_fwd_tc(int layer, const void* x, const void* Wt, const float* b, void* y, float* yf,
                                const Geom& geo, int* err, cudaStream_t s);
 cudaError_t launch_conv_bwd_data_tc(int layer, const void* gy, const void* W, const void* a, void* gx,

@@ -204,6 +204,34 @@ def test_warm_start_cuts_iterations(lgf):
     assert sum(r[1] for r in rows) < sum(r[0] for r in rows)
 
 
+@pytest.mark.parametrize("backward", [False, True])
+def test_expired_convolution_wait_is_reported_and_the_context_stays_usable(lgf, backward):
+    """The bounded waits of the tensor-core convolutions, made to expire
+    without a fault: with a stage-wait budget of 0 every CTA gives up its
+    first stage wait, drains the MMAs it issued, frees its tensor memory and
+    returns; the call reports LGF_ERR_TIMEOUT.  With the default budget back,
+    the same convolution on the same stream gives the result it gave before."""
+    import torch
+    from paper_1208_1186_gb300._lib import LGF_ERR_TIMEOUT
+    dims = (16, 8, 4, 6)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(7)
+    net = lgf.WarmStartNet(seed=3)
+    try:
+        x = torch.tensor(rng.integers(-4, 5, (V, 32)) / 4, dtype=torch.float32).to(torch.bfloat16).cuda()
+        layer = 2
+        before = net.conv(layer, backward, x, dims).cpu()
+        net.set_wait_budget(0)
+        with pytest.raises(lgf.LgfError) as e:
+            net.conv(layer, backward, x, dims)
+        assert e.value.status == LGF_ERR_TIMEOUT
+        net.set_wait_budget(-1)
+        after = net.conv(layer, backward, x, dims).cpu()
+        assert torch.equal(before, after)
+    finally:
+        net.close()
+
+
 @pytest.mark.parametrize("dims", [(6, 4, 3, 6), (16, 4, 2, 2)])
 @pytest.mark.parametrize("layer,backward", [(1, False), (2, False), (3, False), (2, True), (3, True)])
 def test_tensor_core_convolution_is_exact_on_dyadic_inputs(lgf, layer, backward, dims):
