@@ -963,7 +963,7 @@ def run_batch(args, W):
 
 
 def run_warm(args, W):
-    """C5 as its own bench line."""
+    """The warm-start workload as its own bench line."""
     import torch
 
     import paper_1208_1186_gb300 as lgf
@@ -1029,6 +1029,47 @@ def run_reference(args, W):
     }
 
 
+SWEEP_SHAPES = [((32, 32, 32, 32), "f32"), ((48, 48, 48, 8), "f32_r12"), ((48, 48, 48, 12), "f32_r12"),
+                ((24, 24, 24, 48), "f32"), ((32, 32, 32, 8), "f32"), ((16, 16, 16, 16), "f32"),
+                ((20, 20, 20, 20), "f32")]
+
+
+def schedule_sweep(iters: int = 50):
+    """z-t pass time per launch for each (tile width, radix order) the
+    register-plane pipeline supports on each shape (lgf_set_schedule, then
+    `iters` iterations with per-kernel CUDA events), and the autotuner's own
+    choice on the same handle."""
+    import torch
+    import paper_1208_1186_gb300 as lgf
+    from lgf_inputs import torch_gen
+    for dims, dtype in SWEEP_SHAPES:
+        Ud = torch_gen.synthetic_config(dims, seed=0, link_scale=0.5, gauge_scale=1.0, device="cuda")
+        st = torch.cuda.Stream()
+        gf = lgf.GaugeFixer(dims, dtype, stream=st)
+        res = {}
+        for bx in (0, 8):
+            for ro in (0, 1, 2):
+                try:
+                    gf.set_schedule(3, bx, ro)
+                except lgf.LgfError:
+                    continue  # not supported on this shape
+                gf.load_links(Ud)
+                gf.iterate(5)
+                torch.cuda.synchronize()
+                gf.profile(True)
+                gf.iterate(iters)
+                torch.cuda.synchronize()
+                k = gf.profile_read()
+                gf.profile(False)
+                res[f"width{bx or 4}_order{ro}"] = round(k["fft_zt"][0] / k["fft_zt"][1] * 1e3, 2)
+        gf.set_schedule(3, 0, 0)
+        gf.load_links(Ud)
+        gf.autotune(reps=10)
+        print(json.dumps({"lattice": list(dims), "storage": dtype, "zt_us_per_launch": res,
+                          "autotune": list(gf.schedule())}), flush=True)
+        gf.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1053,7 +1094,14 @@ def main():
                          + ",".join(ARMS) + ", or 'all' / 'none'")
     ap.add_argument("--link-update", type=int, default=0, choices=[0, 1],
                     help="FP32 storage: 0 gauge representation (default), 1 links updated in place")
+    ap.add_argument("--schedule-sweep", action="store_true",
+                    help="time the z-t pass (us per launch) under every register-plane FFT schedule on "
+                         "32^4, 48^3x8, 48^3x12, 24^3x48, 32^3x8, 16^4 and 20^4, print one JSON line per "
+                         "lattice and exit")
     args = ap.parse_args()
+    if args.schedule_sweep:
+        schedule_sweep()
+        return
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 steps (minimum)")
         args.warmup = 3

@@ -46,11 +46,13 @@ constexpr int zt_threads() {
 }
 
 // a thread holds a whole t line through the forward transform, the factor and
-// the inverse: up to 128 registers for FP32 lines up to 32 (4 CTAs of 128
-// threads per SM at BX = 4, 2 of 256 at BX = 8)
+// the inverse: FP32 lines up to 32 run 3 CTAs of 128 threads per SM at BX = 4
+// (up to 170 registers, no spills; 4 CTAs at 128 registers spilled 56 bytes
+// per thread and took 22.6 instead of 21.7 us at 32^4, 5 and 6 CTAs took
+// 23.9 and 28.9 us), 2 of 256 at BX = 8
 template <class T, int LZ, int LT, int BX>
 constexpr int zt_min_blocks() {
-  return (sizeof(T) == 4 && LZ <= 32 && LT <= 32) ? (BX <= 4 ? 4 : 2) : 1;
+  return (sizeof(T) == 4 && LZ <= 32 && LT <= 32) ? (BX <= 4 ? 3 : 2) : 1;
 }
 
 template <class T, int LZ, int LT, int BX>
