@@ -63,6 +63,57 @@ def test_null_handles_are_rejected(lib):
     assert lib.lgf_launch_count(None) == -1
 
 
+def test_every_handle_taking_entry_point_rejects_null(lib):
+    """Each call that takes a handle, batch or network checks it (and its
+    other arguments) before any device work: LGF_ERR_ARG, no crash."""
+    E = _lib.LGF_ERR_ARG
+    i = ctypes.c_int(0)
+    buf = (ctypes.c_double * 8)()
+    calls = {
+        "lgf_set_stream": (None, None),
+        "lgf_load_links": (None, buf),
+        "lgf_load_links_device": (None, buf),
+        "lgf_store_links": (None, buf),
+        "lgf_probe": (None, None, None, None),
+        "lgf_fix_split": (None, ctypes.byref(i), ctypes.byref(i)),
+        "lgf_autotune": (None, 3, None),
+        "lgf_tune_schedule": (None, 1, None, None, None),
+        "lgf_set_schedule": (None, 1, 3, 0, 0),
+        "lgf_history": (None, buf, 8, ctypes.byref(i)),
+        "lgf_profile": (None, 1),
+        "lgf_batch_destroy": (None,),
+        "lgf_batch_iterate": (None, 1),
+        "lgf_batch_fix": (None, 1e-12, 10, None, None),
+        "lgf_batch_autotune": (None, 3, None),
+        "lgf_batch_set_lanes": (None, 2),
+        "lgf_net_destroy": (None,),
+        "lgf_net_get_params": (None, buf),
+        "lgf_net_set_params": (None, buf),
+        "lgf_net_set_wait_budget": (None, 0),
+        "lgf_net_forward": (None, None, None),
+        "lgf_net_train_step": (None, None, 0.0, None, None),
+        "lgf_net_warm_start": (None, None),
+        "lgf_net_conv": (None, 1, 0, None, None, None, None, 8, 8, 8, 8, None),
+        "lgf_tune_load": (None, None),
+        "lgf_tune_save": (None,),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == E, name
+    # bad values with no handle needed
+    h = ctypes.c_void_p()
+    assert lib.lgf_create(8, 8, 8, 8, _lib.LGF_F64, None) == E
+    b = ctypes.c_void_p()
+    assert lib.lgf_batch_create(None, 1, ctypes.byref(b)) == E and not b.value
+    assert lib.lgf_batch_create(None, 1, None) == E
+    assert lib.lgf_net_create(ctypes.c_ulonglong(0), None) == E
+    out = (ctypes.c_double * 2)()
+    for dims, dt, links, o in [((1, 8, 8, 8), 0, buf, out), ((8, 8, 8, 65), 0, buf, out), ((8, 8, 8, 8), 7, buf, out),
+                               ((8, 8, 8, 8), 0, None, out), ((8, 8, 8, 8), 0, buf, None),
+                               ((64, 64, 64, 64), 0, buf, out)]:
+        assert lib.lgf_functional_noalloc(links, *dims, dt, o, None) == E, dims
+    assert not h.value
+
+
 def test_allocator_hooks_must_come_in_pairs(lib):
     alloc = _lib.ALLOC_FN(lambda n, d, s, u: None)
     assert lib.lgf_set_allocator(alloc, _lib.FREE_FN(), None) == _lib.LGF_ERR_ARG
