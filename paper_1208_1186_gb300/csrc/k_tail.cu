@@ -474,10 +474,13 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_eta(const cx<float>* _
   pdl_wait();
   if (queue_stopped(st, mode)) return;
   const int V = (int)geo.V;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  // a grid-stride loop over sites (2 CTAs per SM): each thread adds its
+  // sites' F terms in double-float and their theta terms in compensated
+  // FP32; the block and grid sums run once per CTA
   df fsum = {0.f, 0.f};
-  float tsum = 0.f;
-  if (s < V) {
+  float tsum = 0.f, tcomp = 0.f;
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
     int c[4];
     site_coords_i(geo.L, s, c);
     M3<float> Cc, T;  // the links' corrections; the pending factor of one product
@@ -559,12 +562,19 @@ __global__ void __launch_bounds__(256, 2) k_gradient_tail_eta(const cx<float>* _
     D[V + s] = d02;
     D[2 * V + s] = d12;
     D[3 * V + s] = mk<float>(i0, i1);
-    tsum = 2.f * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
+    const float ts = 2.f * (norm2(d01) + norm2(d02) + norm2(d12)) + i0 * i0 + i1 * i1 + i2 * i2;
+    {  // Kahan-compensated theta terms
+      const float y = ts - tcomp;
+      const float t = tsum + y;
+      tcomp = (t - tsum) - y;
+      tsum = t;
+    }
     const float2 f0 = __ldg(F0 + s);
     dacc fs = {f0.x, f0.y};
     dacc_add_f(fs, fc);
-    fsum = dacc_result(fs);
+    fsum = df_add(fsum, dacc_result(fs));
   }
+  tsum -= tcomp;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const df other = {__shfl_down_sync(0xffffffffu, fsum.h, o), __shfl_down_sync(0xffffffffu, fsum.l, o)};
@@ -659,10 +669,28 @@ cudaError_t launch_tail_base(const void* Udf, void* base, const Geom& geo, cudaS
   return cudaPeekAtLastError();
 }
 
+// the tail gradient's grid: 2 CTAs per SM (grid-stride), or one site per thread
+constexpr bool kTailGridStride = true;
+
+static int tail_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, m = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m <= 0)
+      return 1;
+    n = m;
+  }
+  return n;
+}
+
 cudaError_t launch_gradient_tail_eta(const void* Udf, const void* eta, const void* base, void* D32,
                                      double2* partial, const Geom& geo, DevState* st, int mode, cudaStream_t s) {
   auto D0 = static_cast<const cx<float>*>(base);
-  launch_pdl(k_gradient_tail_eta, (unsigned)((geo.V + 255) / 256), 256, 0, s, static_cast<const cx<float>*>(Udf),
+  const int64_t full = (geo.V + 255) / 256;
+  const int64_t cap = 2 * (int64_t)tail_sm_count();
+  const unsigned nb = (unsigned)(kTailGridStride && full > cap ? cap : full);
+  launch_pdl(k_gradient_tail_eta, nb, 256, 0, s, static_cast<const cx<float>*>(Udf),
              static_cast<const cx<float>*>(eta), D0, reinterpret_cast<const float2*>(D0 + 4 * geo.V),
              static_cast<cx<float>*>(D32), partial, geo, st, mode, 1.0 / (12.0 * (double)geo.V),
              1.0 / (3.0 * (double)geo.V));
