@@ -1020,8 +1020,6 @@ def run_reference(args, W):
         "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": main_config(W, world, gauge_rep),
-        "fft_schedule": ({"autotuned": True, "pipeline": schedule[0], "zt_tile_width": schedule[1],
-                          "radix_order": schedule[2]} if schedule else {"autotuned": False}),
         "sample_lattice": list(dims),
         "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": cores, "kind": "oracle",
                          "sample": sample},

@@ -68,3 +68,25 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = argparse.Namespace(steps=1, warmup=0)
     assert bench.run_reference(args, bench.WORKLOADS[bench.DEFAULT_WORKLOAD]) is None
+
+
+def test_reference_arm_line_on_rank_0(monkeypatch):
+    """On rank 0 the oracle arm prints one JSON line with the same metric and
+    config as the GPU arm, a cpu_baseline describing its sample and an e2e
+    equal to its value (the oracle's cost is stubbed: this checks the line,
+    not the oracle's speed)."""
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "time_oracle", lambda U, n, alpha, threads=1: 1e-6 * max(n, 1) * U.shape[0])
+    monkeypatch.setattr(bench, "host_cores", lambda: 4)
+    args = argparse.Namespace(steps=2, warmup=1)
+    W = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    line = bench.run_reference(args, W)
+    assert line is not None
+    json.dumps(line)  # serialisable
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert line["config"] == bench.main_config(W, 1, W["dtype"].startswith("f32"))
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 4
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["steps"] == 2 and line["warmup"] == 1
