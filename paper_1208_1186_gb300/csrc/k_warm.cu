@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   constexpr int STAGE = tc_stage_bytes<K, N>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kTcStages + 1];
+  __shared__ __align__(8) uint64_t bbars[kTcStages];  // a stage's B tiles have landed
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
   const int t = threadIdx.x, w = t >> 5;
@@ -366,6 +367,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   if (t == 0) {
     for (int k = 0; k <= kTcStages; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[k])) : "memory");
+    for (int k = 0; k < kTcStages; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbars[k])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
   }
@@ -384,6 +387,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   // tensor memory
   const unsigned stage_polls = (unsigned)err[1];
 
+  int b_issued = -1, b_waited = -1;  // thread 0: last group whose B copy was issued / waited for
+  bool b_fail = false;                // thread 0: a B wait expired (no more MMAs are issued)
   // gather group g = (dy, dz, dt) into stage g % kTcStages: this thread's
   // buffer rows (zeros where a padded row lies outside the lattice) and its
   // share of the three taps' N x K B tiles
@@ -406,10 +411,17 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
           asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(dst + c * A_LBO), "r"(0) : "memory");
       }
     }
-    const bf16* wsrc = Wk + (size_t)(3 * g) * N * K;
-    for (int j = t; j < 3 * N * NCH; j += 128) {
-      const int tp = j / (N * NCH), r = j % (N * NCH), n = r / NCH, c = r % NCH;
-      cp_async16(st + A_BYTES + tp * B_TAP + c * B_LBO + n * 16, wsrc + (tp * N + n) * K + c * 8);
+    // the three taps' B tiles: one bulk copy (the weights are stored in the
+    // tiles' shared-memory order), completing on the stage's B barrier
+    if (t == 0) {
+      constexpr uint32_t kBBytes = 3u * N * K * 2u;
+      const uint32_t bb = smem_u32(&bbars[g % kTcStages]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(kBBytes) : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       st + A_BYTES),
+                   "l"(Wk + (size_t)(3 * g) * N * K), "r"(kBBytes), "r"(bb)
+                   : "memory");
+      b_issued = g;
     }
   };
 
@@ -430,19 +442,30 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 2) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    // the group's B tiles (thread 0 issues the MMAs); a failed wait stops the CTA
     if (t == 0) {
+      if (!b_fail && !mbar_wait(&bbars[g % kTcStages], (uint32_t)((g / kTcStages) & 1), kTcWaitLimit)) {
+        b_fail = true;
+        atomicExch(err, 1);
+        stop = 1;
+      }
+      b_waited = g;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = sbase + (g % kTcStages) * STAGE;
+      if (!b_fail) {
 #pragma unroll
-      for (int dxp = 0; dxp < 3; ++dxp) {
-        // output row m reads buffer row m + 1 + SIGN dx
-        const uint32_t a0 = st + (uint32_t)(1 + SIGN * (dxp - 1)) * 16;
-        const uint32_t b0 = st + A_BYTES + dxp * B_TAP;
+        for (int dxp = 0; dxp < 3; ++dxp) {
+          // output row m reads buffer row m + 1 + SIGN dx
+          const uint32_t a0 = st + (uint32_t)(1 + SIGN * (dxp - 1)) * 16;
+          const uint32_t b0 = st + A_BYTES + dxp * B_TAP;
 #pragma unroll
-        for (int q = 0; q < K / 16; ++q)
-          tc_mma(tmem, tc_desc(a0 + q * 2 * A_LBO, A_LBO, 128), tc_desc(b0 + q * 2 * B_LBO, B_LBO, 128), idesc,
-                 (g > 0 || dxp > 0 || q > 0) ? 1u : 0u);
+          for (int q = 0; q < K / 16; ++q)
+            tc_mma(tmem, tc_desc(a0 + q * 2 * A_LBO, A_LBO, 128), tc_desc(b0 + q * 2 * B_LBO, B_LBO, 128), idesc,
+                   (g > 0 || dxp > 0 || q > 0) ? 1u : 0u);
+        }
       }
+      // committed even without MMAs (then it arrives at once), so that the
+      // stage wait below never waits for MMAs that were not issued
       tc_commit(&bars[g % kTcStages]);
     }
     issued = g;
@@ -451,7 +474,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
       if (next < 27) {
         // the stage of group g - 1 is free once its MMAs have completed
         const bool ok = mbar_wait(&bars[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1), stage_polls);
-        if (__syncthreads_or(!ok)) {
+        if (__syncthreads_or(!ok || b_fail)) {
           if (t == 0) atomicExch(err, 1);
           break;
         }
@@ -461,12 +484,17 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
+  if (t == 0) {
+    // B copies still in flight (after an early exit) land before the CTA ends
+    for (int gg = b_waited + 1; gg <= b_issued; ++gg)
+      (void)mbar_wait(&bbars[gg % kTcStages], (uint32_t)((gg / kTcStages) & 1), kTcWaitLimit);
+  }
   // all MMAs issued so far have completed once the last commit's phase does
   if (t == 0 && issued >= 0) {
     tc_commit(&bars[kTcStages]);
     const bool ok = mbar_wait(&bars[kTcStages], 0u, kTcWaitLimit);
     if (!ok) atomicExch(err, 1);
-    stop = !ok || issued < 26;
+    stop = stop || !ok || issued < 26;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -622,6 +650,15 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 // 16 outputs with zero columns.
 // (Wt*: the same weights K-major for the forward tensor-core convolution,
 // [tap][out][in])
+// Weight tile order of the tensor-core convolutions: for each tap, the N x K
+// tile (N rows of K input values) as K/8 chunks of 16 bytes, chunk-major:
+// element (tap, n, k) at ((tap K/8 + k/8) N + n) 8 + k % 8.  This is the
+// shared-memory order of a B tile, so the three taps of a group arrive by
+// one bulk copy.
+__device__ __forceinline__ int wtile_index(int tap, int n, int k, int N, int K) {
+  return ((tap * (K / 8) + k / 8) * N + n) * 8 + (k & 7);
+}
+
 __global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ W1, bf16* __restrict__ W2,
                                bf16* __restrict__ W3, float* __restrict__ b1, float* __restrict__ b2,
                                float* __restrict__ b3, bf16* __restrict__ Wt1, bf16* __restrict__ Wt2,
@@ -632,22 +669,22 @@ __global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ W
        i += gridDim.x * blockDim.x) {
     if (i < n1) {
       const bf16 v = __float2bfloat16_rn(p[i]);
-      W1[i] = v;
       const int tap = i / (kFeat * kHid), r = i % (kFeat * kHid), in = r / kHid, o = r % kHid;
-      Wt1[(tap * kHid + o) * kFeat + in] = v;
+      W1[wtile_index(tap, in, o, kFeat, kHid)] = v;
+      Wt1[wtile_index(tap, o, in, kHid, kFeat)] = v;
     } else if (i < n1 + n2) {
       const int j = i - n1;
       const bf16 v = __float2bfloat16_rn(p[o_W2 + j]);
-      W2[j] = v;
       const int tap = j / (kHid * kHid), r = j % (kHid * kHid), in = r / kHid, o = r % kHid;
-      Wt2[(tap * kHid + o) * kHid + in] = v;
+      W2[wtile_index(tap, in, o, kHid, kHid)] = v;
+      Wt2[wtile_index(tap, o, in, kHid, kHid)] = v;
     } else if (i < n1 + n2 + n3) {
       const int j = i - n1 - n2;  // [tap][i][16]
       const int o = j % kOutPad, ti = j / kOutPad;
       const bf16 v = __float2bfloat16_rn(o < kOut ? p[o_W3 + ti * kOut + o] : 0.f);
-      W3[j] = v;
       const int tap = ti / kHid, in = ti % kHid;
-      Wt3[(tap * kOutPad + o) * kHid + in] = v;
+      W3[wtile_index(tap, in, o, kHid, kOutPad)] = v;
+      Wt3[wtile_index(tap, o, in, kOutPad, kHid)] = v;
     } else {
       const int j = i - n1 - n2 - n3;
       if (j < kHid)
