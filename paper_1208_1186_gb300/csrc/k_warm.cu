@@ -5,8 +5,9 @@
 //
 // Network: three 3^4-tap periodic convolutions, 48 -> 32 -> 32 -> 8 channels,
 // ReLU after the first two; BF16 weights and activations, FP32 accumulation
-// on the tensor cores (warp-level mma on 16x16x16 BF16 tiles), FP32 master
-// weights and Adam moments.  Training signal: the loss is -F(U^{g0}) (the
+// on the tensor cores (the forward and backward-data convolutions as
+// tcgen05 implicit GEMMs, the weight gradient on warp-level 16x16x16 BF16
+// tiles), FP32 master weights and Adam moments.  Training signal: the loss is -F(U^{g0}) (the
 // method's own functional), whose derivative along left translations of
 // g0(x) is the projection of the transformed links' gradient Delta'(x) onto
 // the su(3) generators; Delta' comes from the gauge-representation gradient
@@ -218,36 +219,40 @@ __device__ __forceinline__ int tap_site(const Geom& geo, const int c[4], int tap
 // K-major in the output channels), the ReLU mask of the layer below in the
 // epilogue.
 //
-// Rows.  The M rows of a CTA are 128 consecutive rows of the lattice's
-// x-lines padded by one periodic halo row at each end (Lx + 2 rows per line:
-// x = Lx-1, 0, ..., Lx-1, 0); rows on a halo are computed and discarded.
-// The three taps that differ only in dx then read the same gathered rows one
-// row apart: for each of the 27 (dy, dz, dt) the CTA gathers one buffer of
-// 130 padded rows (its 128 and one on each side) at line offset SIGN (dy,
-// dz, dt), and the MMAs of dx = -1, 0, 1 start 16 bytes apart in it.  That is
-// a third of the gathering of one buffer per tap.
+// Rows.  The M rows of a CTA are 128 consecutive rows of the lattice laid
+// out with a periodic halo in x and y: each (z, t) plane is (Ly + 2) lines of
+// Lx + 2 rows (x = Lx-1, 0, ..., Lx-1, 0 along a line, the same wrap for the
+// lines in y); rows on a halo are computed and discarded.  For an output row
+// off the halo, the taps (dx, dy) read the rows dx + dy (Lx + 2) away, which
+// stay inside its own plane.  So the nine taps of one (dz, dt) read a single
+// window of gathered rows -- the CTA's 128 and Lx + 3 on each side -- at
+// start addresses that differ by whole rows: for each of the 9 (dz, dt) the
+// CTA gathers one window at plane offset SIGN (dz, dt) (each window row
+// mapped on its own, so windows may cross planes), and its 9 taps' MMAs start
+// (Lx + 3 + SIGN (dx + dy (Lx + 2))) rows into it.
 //
-// Shared memory, per pipeline stage: the buffer and the three taps' B tiles,
+// Shared memory, per pipeline stage: the window and the nine taps' B tiles,
 // each "chunk-major" K-major -- 16-byte chunk c of row r at c * ROWS * 16 +
 // r * 16 -- which is the no-swizzle canonical layout with SBO = 128 (the next
 // 8 rows) and LBO = ROWS * 16 (the next 8 channels).  A warp's 32 rows of one
 // chunk are 512 contiguous bytes, so the gathers write shared memory without
-// bank conflicts.
+// bank conflicts.  ROWS, and with it the stage size, follows Lx.
 //
 // Pipeline: kTcStages stages; all 128 threads gather (cp.async, L1-cached:
-// neighbouring groups gather overlapping rows), one thread issues the 3 K/16
-// MMAs of a group into the FP32 accumulator in tensor memory (128 lanes x N
-// columns) and commits them to the stage's mbarrier.  A group's MMAs are
-// issued before the previous group's stage is waited for and refilled, so
-// the tensor core always has work queued.  Epilogue: each warp reads its 32
-// lanes with tcgen05.ld.  Every wait is bounded: on expiry the CTA records an
-// error in err[0], stops issuing, waits (bounded) for its MMAs, frees its
-// tensor memory and returns.  err[1] holds the poll budget of the stage
-// waits (kConvWaitPolls unless lgf_net_set_wait_budget changed it).
+// neighbouring windows overlap), one thread copies the group's B tiles (one
+// bulk copy: the weights are stored in the tiles' order) and issues the
+// 9 K/16 MMAs of a group into the FP32 accumulator in tensor memory (128
+// lanes x N columns) and commits them to the stage's mbarrier.  A group's
+// MMAs are issued before the previous group's stage is waited for and
+// refilled, so the tensor core always has work queued.  Epilogue: each warp
+// reads its 32 lanes with tcgen05.ld.  Every wait is bounded: on expiry the
+// CTA records an error in err[0], stops issuing, waits (bounded) for its
+// MMAs, frees its tensor memory and returns.  err[1] holds the poll budget of
+// the stage waits (kConvWaitPolls unless lgf_net_set_wait_budget changed it).
 // ---------------------------------------------------------------------------
 constexpr int kTcStages = 2;
+constexpr int kTcGroups = 9;  // (dz, dt) windows per CTA
 constexpr int kTcTmemCols = 32;
-constexpr int kTcBufRows = 136;  // 130 gathered rows, rounded up to whole 8-row groups
 constexpr unsigned kTcWaitLimit = (unsigned)kConvWaitPolls;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -302,9 +307,13 @@ __device__ __forceinline__ void cp_async16(uint32_t sdst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(gsrc) : "memory");
 }
 
+// window rows of a CTA: its 128 and Lx + 3 on each side, rounded up to whole
+// 8-row groups
+__host__ __device__ constexpr int tc_window_rows(int Lx) { return (128 + 2 * (Lx + 3) + 7) & ~7; }
+
 template <int K, int N>
-constexpr int tc_stage_bytes() {
-  return (kTcBufRows + 3 * N) * K * 2;
+__host__ __device__ constexpr int tc_stage_bytes(int Lx) {
+  return (tc_window_rows(Lx) + 9 * N) * K * 2;
 }
 
 __device__ __forceinline__ int wrap_add(int c, int d, int L) {
@@ -319,11 +328,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
                                                  bool relu, int* __restrict__ err) {
   static_assert(K % 16 == 0 && (N == 16 || N == 32), "tile shapes of this kernel");
   constexpr int NCH = K / 8;                         // 16-byte chunks per row
-  constexpr int A_LBO = kTcBufRows * 16;             // next chunk of the buffer
-  constexpr int A_BYTES = NCH * A_LBO;
   constexpr int B_LBO = N * 16;                      // next chunk of a B tile
   constexpr int B_TAP = NCH * B_LBO;
-  constexpr int STAGE = tc_stage_bytes<K, N>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kTcStages + 1];
   __shared__ __align__(8) uint64_t bbars[kTcStages];  // a stage's B tiles have landed
@@ -331,36 +337,42 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   __shared__ int stop;
   const int t = threadIdx.x, w = t >> 5;
   const int Lx = geo.L[0], Ly = geo.L[1], Lz = geo.L[2], Lt = geo.L[3];
-  const int LXP = Lx + 2;
-  const int lines = Ly * Lz * Lt;
-  const int PR = lines * LXP;              // padded rows
+  const int LXP = Lx + 2, LYP = Ly + 2;
+  const int PLANE = LXP * LYP;             // padded rows of one (z, t) plane
+  const int PR = PLANE * Lz * Lt;          // padded rows
+  const int WR = 128 + 2 * (LXP + 1);      // window rows
+  const uint32_t A_LBO = (uint32_t)tc_window_rows(Lx) * 16;  // next chunk of the window
+  const uint32_t A_BYTES = NCH * A_LBO;
+  const uint32_t STAGE = (uint32_t)tc_stage_bytes<K, N>(Lx);
   const int P0 = blockIdx.x * 128;
   // this thread's output row
   int s_out = -1;
   {
     const int P = P0 + t;
     if (P < PR) {
-      const int l = P / LXP, xp = P - l * LXP;
-      if (xp >= 1 && xp <= Lx) s_out = (xp - 1) + Lx * l;
+      const int l = P / PLANE, r = P - l * PLANE;
+      const int yp = r / LXP, xp = r - yp * LXP;
+      if (xp >= 1 && xp <= Lx && yp >= 1 && yp <= Ly) s_out = (xp - 1) + Lx * ((yp - 1) + Ly * l);
     }
   }
-  // this thread's buffer rows b = t and (t < 2) b = 128 + t: padded row
-  // P0 - 1 + b as (x, y, z, t) of its source line, or absent
-  int rx[2], ry[2], rz[2], rt[2];
-  bool rv[2];
+  // this thread's window rows b = t + 128 k (b < WR; at most 3 for Lx <= 64):
+  // padded row P0 - LXP - 1 + b as (x, y, z, t) of its source site, or absent
+  constexpr int kRowsPerThread = 3;
+  int rx[kRowsPerThread], ry[kRowsPerThread], rz[kRowsPerThread], rt[kRowsPerThread];
+  bool rv[kRowsPerThread];
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kRowsPerThread; ++k) {
     const int b = t + 128 * k;
-    const int P = P0 - 1 + b;
-    rv[k] = (k == 0 || b < 130) && P >= 0 && P < PR;
+    const int P = P0 - LXP - 1 + b;
+    rv[k] = b < WR && P >= 0 && P < PR;
     rx[k] = ry[k] = rz[k] = rt[k] = 0;
     if (rv[k]) {
-      const int l = P / LXP, xp = P - l * LXP;
+      const int l = P / PLANE, r = P - l * PLANE;
+      const int yp = r / LXP, xp = r - yp * LXP;
       rx[k] = xp == 0 ? Lx - 1 : (xp == Lx + 1 ? 0 : xp - 1);
-      ry[k] = l % Ly;
-      const int l2 = l / Ly;
-      rz[k] = l2 % Lz;
-      rt[k] = l2 / Lz;
+      ry[k] = yp == 0 ? Ly - 1 : (yp == Ly + 1 ? 0 : yp - 1);
+      rz[k] = l % Lz;
+      rt[k] = l / Lz;
     }
   }
   const uint32_t sbase = smem_u32(smem_raw);
@@ -389,19 +401,19 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
 
   int b_issued = -1, b_waited = -1;  // thread 0: last group whose B copy was issued / waited for
   bool b_fail = false;                // thread 0: a B wait expired (no more MMAs are issued)
-  // gather group g = (dy, dz, dt) into stage g % kTcStages: this thread's
-  // buffer rows (zeros where a padded row lies outside the lattice) and its
-  // share of the three taps' N x K B tiles
+  // gather group g = (dz, dt) into stage g % kTcStages: this thread's window
+  // rows (zeros where a padded row lies outside the lattice) and, from thread
+  // 0, the nine taps' N x K B tiles
   auto fill = [&](int g) {
     const uint32_t st = sbase + (g % kTcStages) * STAGE;
-    const int dy = SIGN * (g % 3 - 1), dz = SIGN * ((g / 3) % 3 - 1), dt = SIGN * (g / 9 - 1);
+    const int dz = SIGN * (g % 3 - 1), dt = SIGN * (g / 3 - 1);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kRowsPerThread; ++k) {
       const int b = t + 128 * k;
-      if (k == 1 && b >= 130) break;
+      if (b >= WR) break;
       const uint32_t dst = st + b * 16;
       if (rv[k]) {
-        const int src = rx[k] + Lx * (wrap_add(ry[k], dy, Ly) + Ly * (wrap_add(rz[k], dz, Lz) + Lz * wrap_add(rt[k], dt, Lt)));
+        const int src = rx[k] + Lx * (ry[k] + Ly * (wrap_add(rz[k], dz, Lz) + Lz * wrap_add(rt[k], dt, Lt)));
         const bf16* p = act + (size_t)src * K;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) cp_async16(dst + c * A_LBO, p + c * 8);
@@ -411,15 +423,15 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
           asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(dst + c * A_LBO), "r"(0) : "memory");
       }
     }
-    // the three taps' B tiles: one bulk copy (the weights are stored in the
-    // tiles' shared-memory order), completing on the stage's B barrier
+    // the nine taps' B tiles (taps 9 g .. 9 g + 8, consecutive in the packed
+    // weights): one bulk copy, completing on the stage's B barrier
     if (t == 0) {
-      constexpr uint32_t kBBytes = 3u * N * K * 2u;
+      constexpr uint32_t kBBytes = 9u * N * K * 2u;
       const uint32_t bb = smem_u32(&bbars[g % kTcStages]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(kBBytes) : "memory");
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                        st + A_BYTES),
-                   "l"(Wk + (size_t)(3 * g) * N * K), "r"(kBBytes), "r"(bb)
+                   "l"(Wk + (size_t)(9 * g) * N * K), "r"(kBBytes), "r"(bb)
                    : "memory");
       b_issued = g;
     }
@@ -438,7 +450,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   }
   int issued = -1;  // last group whose MMAs were issued
 #pragma unroll 1
-  for (int g = 0; g < 27; ++g) {
+  for (int g = 0; g < kTcGroups; ++g) {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 2) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -453,15 +465,17 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = sbase + (g % kTcStages) * STAGE;
       if (!b_fail) {
-#pragma unroll
-        for (int dxp = 0; dxp < 3; ++dxp) {
-          // output row m reads buffer row m + 1 + SIGN dx
-          const uint32_t a0 = st + (uint32_t)(1 + SIGN * (dxp - 1)) * 16;
-          const uint32_t b0 = st + A_BYTES + dxp * B_TAP;
+#pragma unroll 1
+        for (int j = 0; j < 9; ++j) {
+          // tap (dx, dy) = SIGN (j % 3 - 1, j / 3 - 1): output row m reads
+          // window row m + LXP + 1 + SIGN (dx + dy LXP)
+          const int dx = SIGN * (j % 3 - 1), dy = SIGN * (j / 3 - 1);
+          const uint32_t a0 = st + (uint32_t)(LXP + 1 + dx + dy * LXP) * 16;
+          const uint32_t b0 = st + A_BYTES + j * B_TAP;
 #pragma unroll
           for (int q = 0; q < K / 16; ++q)
             tc_mma(tmem, tc_desc(a0 + q * 2 * A_LBO, A_LBO, 128), tc_desc(b0 + q * 2 * B_LBO, B_LBO, 128), idesc,
-                   (g > 0 || dxp > 0 || q > 0) ? 1u : 0u);
+                   (g > 0 || j > 0 || q > 0) ? 1u : 0u);
         }
       }
       // committed even without MMAs (then it arrives at once), so that the
@@ -471,7 +485,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
     issued = g;
     if (g >= 1) {
       const int next = g - 1 + kTcStages;
-      if (next < 27) {
+      if (next < kTcGroups) {
         // the stage of group g - 1 is free once its MMAs have completed
         const bool ok = mbar_wait(&bars[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1), stage_polls);
         if (__syncthreads_or(!ok || b_fail)) {
@@ -494,11 +508,11 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
     tc_commit(&bars[kTcStages]);
     const bool ok = mbar_wait(&bars[kTcStages], 0u, kTcWaitLimit);
     if (!ok) atomicExch(err, 1);
-    stop = stop || !ok || issued < 26;
+    stop = stop || !ok || issued < kTcGroups - 1;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!stop && issued == 26) {
+  if (!stop && issued == kTcGroups - 1) {
     float acc[32];
     uint32_t r[32];
     const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16);
@@ -777,13 +791,17 @@ namespace {
 template <int K, int N, int SIGN, bool FWD>
 cudaError_t conv_tc_launch(const void* act, const void* Wk, const float* bias, const void* mask, void* y, float* yf,
                            const Geom& geo, bool relu, int* err, cudaStream_t s) {
-  constexpr int smem = kTcStages * tc_stage_bytes<K, N>();
-  static_assert(smem <= 227 * 1024, "the stages fit one CTA's shared memory");
+  // the stages of the longest x extent fix the attribute once; a launch asks
+  // for its own extent's stages
+  constexpr int smem_max = kTcStages * tc_stage_bytes<K, N>(kMaxL);
+  static_assert(smem_max <= 227 * 1024, "the stages fit one CTA's shared memory");
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k_conv_tc<K, N, SIGN, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaFuncSetAttribute(k_conv_tc<K, N, SIGN, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (attr != cudaSuccess) return attr;
-  // 128 rows per CTA over the x-lines padded by one halo row at each end
-  const int64_t rows = geo.V / geo.L[0] * (geo.L[0] + 2);
+  if (geo.L[0] > kMaxL || geo.L[1] > kMaxL) return cudaErrorInvalidValue;
+  const int smem = kTcStages * tc_stage_bytes<K, N>(geo.L[0]);
+  // 128 rows per CTA over the (z, t) planes padded by a halo in x and y
+  const int64_t rows = (int64_t)(geo.L[0] + 2) * (geo.L[1] + 2) * geo.L[2] * geo.L[3];
   const unsigned nb = (unsigned)((rows + 127) / 128);
   k_conv_tc<K, N, SIGN, FWD><<<nb, 128, smem, s>>>(static_cast<const bf16*>(act), static_cast<const bf16*>(Wk), bias,
                                                     static_cast<const bf16*>(mask), static_cast<bf16*>(y), yf, geo,
