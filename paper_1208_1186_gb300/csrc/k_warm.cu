@@ -465,17 +465,21 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = sbase + (g % kTcStages) * STAGE;
       if (!b_fail) {
-#pragma unroll 1
+        // one descriptor per operand and group; each MMA adds its offset to
+        // the start-address field (address / 16 in the low 14 bits, which
+        // cannot carry: shared-memory addresses stay below 256 KB)
+        const uint64_t ad = tc_desc(st, A_LBO, 128), bd = tc_desc(st + A_BYTES, B_LBO, 128);
+        const uint32_t a_lbo16 = A_LBO >> 4;
+#pragma unroll
         for (int j = 0; j < 9; ++j) {
           // tap (dx, dy) = SIGN (j % 3 - 1, j / 3 - 1): output row m reads
           // window row m + LXP + 1 + SIGN (dx + dy LXP)
           const int dx = SIGN * (j % 3 - 1), dy = SIGN * (j / 3 - 1);
-          const uint32_t a0 = st + (uint32_t)(LXP + 1 + dx + dy * LXP) * 16;
-          const uint32_t b0 = st + A_BYTES + j * B_TAP;
+          const uint32_t arow = (uint32_t)(LXP + 1 + dx + dy * LXP);
 #pragma unroll
           for (int q = 0; q < K / 16; ++q)
-            tc_mma(tmem, tc_desc(a0 + q * 2 * A_LBO, A_LBO, 128), tc_desc(b0 + q * 2 * B_LBO, B_LBO, 128), idesc,
-                   (g > 0 || j > 0 || q > 0) ? 1u : 0u);
+            tc_mma(tmem, ad + (arow + (uint32_t)q * 2 * a_lbo16), bd + (uint32_t)((j * B_TAP + q * 2 * B_LBO) >> 4),
+                   idesc, (g > 0 || j > 0 || q > 0) ? 1u : 0u);
         }
       }
       // committed even without MMAs (then it arrives at once), so that the
