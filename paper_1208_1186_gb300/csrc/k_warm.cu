@@ -251,6 +251,7 @@ __device__ __forceinline__ int tap_site(const Geom& geo, const int c[4], int tap
 // the stage waits (kConvWaitPolls unless lgf_net_set_wait_budget changed it).
 // ---------------------------------------------------------------------------
 constexpr int kTcStages = 2;
+constexpr int kTcThreads = 160;  // four producer warps and the issuing warp
 constexpr int kTcGroups = 9;  // (dz, dt) windows per CTA
 constexpr int kTcTmemCols = 32;
 constexpr unsigned kTcWaitLimit = (unsigned)kConvWaitPolls;
@@ -301,6 +302,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
   return done != 0;
 }
 
+// the same, giving up early once another thread of the CTA has set *stop
+__device__ __forceinline__ bool mbar_wait_or_stop(uint64_t* bar, uint32_t parity, unsigned polls,
+                                                  const volatile int* stop) {
+  uint32_t done = 0;
+  for (unsigned it = 0; it < polls && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (!done && *stop) break;
+  }
+  return done != 0;
+}
+
 // 16-byte asynchronous copy global -> shared, cached in L1 (.ca): the rows a
 // CTA gathers for neighbouring groups overlap, and L1 serves the repeats
 __device__ __forceinline__ void cp_async16(uint32_t sdst, const void* gsrc) {
@@ -322,7 +338,7 @@ __device__ __forceinline__ int wrap_add(int c, int d, int L) {
 }
 
 template <int K, int N, int SIGN, bool FWD>
-__global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, const bf16* __restrict__ Wk,
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16* __restrict__ act, const bf16* __restrict__ Wk,
                                                  const float* __restrict__ bias, const bf16* __restrict__ mask,
                                                  bf16* __restrict__ y, float* __restrict__ yf, const Geom geo,
                                                  bool relu, int* __restrict__ err) {
@@ -331,11 +347,17 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   constexpr int B_LBO = N * 16;                      // next chunk of a B tile
   constexpr int B_TAP = NCH * B_LBO;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kTcStages + 1];
+  __shared__ __align__(8) uint64_t full[kTcStages];   // a stage's window has landed (128 producer arrivals)
+  __shared__ __align__(8) uint64_t empty[kTcStages];  // the MMAs reading a stage have completed
   __shared__ __align__(8) uint64_t bbars[kTcStages];  // a stage's B tiles have landed
+  __shared__ __align__(8) uint64_t done_bar;          // all MMAs have completed
   __shared__ uint32_t tmem_slot;
-  __shared__ int stop;
+  __shared__ int stop, last_issued;
   const int t = threadIdx.x, w = t >> 5;
+  // roles: threads 0-127 gather the windows and write the output rows; lane 0
+  // of warp 4 copies the B tiles and issues the MMAs
+  const bool producer = t < 128;
+  const bool issuer = t == 128;
   const int Lx = geo.L[0], Ly = geo.L[1], Lz = geo.L[2], Lt = geo.L[3];
   const int LXP = Lx + 2, LYP = Ly + 2;
   const int PLANE = LXP * LYP;             // padded rows of one (z, t) plane
@@ -347,7 +369,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   const int P0 = blockIdx.x * 128;
   // this thread's output row
   int s_out = -1;
-  {
+  if (producer) {
     const int P = P0 + t;
     if (P < PR) {
       const int l = P / PLANE, r = P - l * PLANE;
@@ -364,7 +386,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   for (int k = 0; k < kRowsPerThread; ++k) {
     const int b = t + 128 * k;
     const int P = P0 - LXP - 1 + b;
-    rv[k] = b < WR && P >= 0 && P < PR;
+    rv[k] = producer && b < WR && P >= 0 && P < PR;
     rx[k] = ry[k] = rz[k] = rt[k] = 0;
     if (rv[k]) {
       const int l = P / PLANE, r = P - l * PLANE;
@@ -377,12 +399,15 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   }
   const uint32_t sbase = smem_u32(smem_raw);
   if (t == 0) {
-    for (int k = 0; k <= kTcStages; ++k)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[k])) : "memory");
-    for (int k = 0; k < kTcStages; ++k)
+    for (int k = 0; k < kTcStages; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&full[k])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[k])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbars[k])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
+    last_issued = -1;
   }
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -399,11 +424,14 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
   // tensor memory
   const unsigned stage_polls = (unsigned)err[1];
 
-  int b_issued = -1, b_waited = -1;  // thread 0: last group whose B copy was issued / waited for
-  bool b_fail = false;                // thread 0: a B wait expired (no more MMAs are issued)
+  // a thread whose wait expired records the error and stops the CTA: every
+  // other wait of the CTA watches `stop` and gives up too
+  auto fail = [&]() {
+    atomicExch(err, 1);
+    *(volatile int*)&stop = 1;
+  };
   // gather group g = (dz, dt) into stage g % kTcStages: this thread's window
-  // rows (zeros where a padded row lies outside the lattice) and, from thread
-  // 0, the nine taps' N x K B tiles
+  // rows (zeros where a padded row lies outside the lattice)
   auto fill = [&](int g) {
     const uint32_t st = sbase + (g % kTcStages) * STAGE;
     const int dz = SIGN * (g % 3 - 1), dt = SIGN * (g / 3 - 1);
@@ -423,100 +451,105 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ act, c
           asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(dst + c * A_LBO), "r"(0) : "memory");
       }
     }
-    // the nine taps' B tiles (taps 9 g .. 9 g + 8, consecutive in the packed
-    // weights): one bulk copy, completing on the stage's B barrier
-    if (t == 0) {
-      constexpr uint32_t kBBytes = 9u * N * K * 2u;
-      const uint32_t bb = smem_u32(&bbars[g % kTcStages]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(kBBytes) : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       st + A_BYTES),
-                   "l"(Wk + (size_t)(9 * g) * N * K), "r"(kBBytes), "r"(bb)
-                   : "memory");
-      b_issued = g;
-    }
+  };
+  // (issuer) the nine taps' B tiles of group g -- taps 9 g .. 9 g + 8,
+  // consecutive in the packed weights -- into stage g % kTcStages by one
+  // bulk copy, completing on the stage's B barrier
+  int b_issued = -1, b_waited = -1;  // issuer: last group whose B copy was issued / waited for
+  auto fill_b = [&](int g) {
+    constexpr uint32_t kBBytes = 9u * N * K * 2u;
+    const uint32_t bb = smem_u32(&bbars[g % kTcStages]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(kBBytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sbase + (g % kTcStages) * STAGE + A_BYTES),
+                 "l"(Wk + (size_t)(9 * g) * N * K), "r"(kBBytes), "r"(bb)
+                 : "memory");
+    b_issued = g;
   };
 
-  constexpr uint32_t idesc = tc_idesc<N>();
-  // every stage starts filled (groups 0 .. S-1, one copy group each); in the
-  // loop a group's MMAs are issued first, then the stage of the previous
-  // group is refilled S groups ahead once its MMAs have drained.  Copy
-  // groups: group g is copy group g, so it has landed when at most S - 2
-  // copy groups committed after it are pending.
+  if (producer) {
+    // Each producer refills a stage once the MMAs of the group that read it
+    // have completed, waits for its own copies, makes its writes visible to
+    // the tensor core's (async) proxy and arrives on the stage's full
+    // barrier; it never waits for the issuing thread.
 #pragma unroll 1
-  for (int g = 0; g < kTcStages; ++g) {
-    fill(g);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
-  int issued = -1;  // last group whose MMAs were issued
-#pragma unroll 1
-  for (int g = 0; g < kTcGroups; ++g) {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 2) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    // the group's B tiles (thread 0 issues the MMAs); a failed wait stops the CTA
-    if (t == 0) {
-      if (!b_fail && !mbar_wait(&bbars[g % kTcStages], (uint32_t)((g / kTcStages) & 1), kTcWaitLimit)) {
-        b_fail = true;
-        atomicExch(err, 1);
-        stop = 1;
+    for (int g = 0; g < kTcGroups; ++g) {
+      if (g >= kTcStages &&
+          !mbar_wait_or_stop(&empty[g % kTcStages], (uint32_t)(((g - kTcStages) / kTcStages) & 1), stage_polls,
+                             &stop)) {
+        fail();
+        break;
       }
+      fill(g);
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[g % kTcStages])) : "memory");
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else if (issuer) {
+    constexpr uint32_t idesc = tc_idesc<N>();
+    // the B tiles of the first groups (their stages start free)
+    for (int g = 0; g < kTcStages; ++g) fill_b(g);
+    int issued = -1;
+#pragma unroll 1
+    for (int g = 0; g < kTcGroups; ++g) {
+      const uint32_t par = (uint32_t)((g / kTcStages) & 1);
+      if (!mbar_wait_or_stop(&full[g % kTcStages], par, stage_polls, &stop)) {
+        fail();
+        break;
+      }
+      const bool b_ok = mbar_wait(&bbars[g % kTcStages], par, kTcWaitLimit);
       b_waited = g;
+      if (!b_ok) {
+        fail();
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = sbase + (g % kTcStages) * STAGE;
-      if (!b_fail) {
-        // one descriptor per operand and group; each MMA adds its offset to
-        // the start-address field (address / 16 in the low 14 bits, which
-        // cannot carry: shared-memory addresses stay below 256 KB)
-        const uint64_t ad = tc_desc(st, A_LBO, 128), bd = tc_desc(st + A_BYTES, B_LBO, 128);
-        const uint32_t a_lbo16 = A_LBO >> 4;
+      // one descriptor per operand and group; each MMA adds its offset to
+      // the start-address field (address / 16 in the low 14 bits, which
+      // cannot carry: shared-memory addresses stay below 256 KB)
+      const uint64_t ad = tc_desc(st, A_LBO, 128), bd = tc_desc(st + A_BYTES, B_LBO, 128);
+      const uint32_t a_lbo16 = A_LBO >> 4;
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          // tap (dx, dy) = SIGN (j % 3 - 1, j / 3 - 1): output row m reads
-          // window row m + LXP + 1 + SIGN (dx + dy LXP)
-          const int dx = SIGN * (j % 3 - 1), dy = SIGN * (j / 3 - 1);
-          const uint32_t arow = (uint32_t)(LXP + 1 + dx + dy * LXP);
+      for (int j = 0; j < 9; ++j) {
+        // tap (dx, dy) = SIGN (j % 3 - 1, j / 3 - 1): output row m reads
+        // window row m + LXP + 1 + SIGN (dx + dy LXP)
+        const int dx = SIGN * (j % 3 - 1), dy = SIGN * (j / 3 - 1);
+        const uint32_t arow = (uint32_t)(LXP + 1 + dx + dy * LXP);
 #pragma unroll
-          for (int q = 0; q < K / 16; ++q)
-            tc_mma(tmem, ad + (arow + (uint32_t)q * 2 * a_lbo16), bd + (uint32_t)((j * B_TAP + q * 2 * B_LBO) >> 4),
-                   idesc, (g > 0 || j > 0 || q > 0) ? 1u : 0u);
-        }
+        for (int q = 0; q < K / 16; ++q)
+          tc_mma(tmem, ad + (arow + (uint32_t)q * 2 * a_lbo16), bd + (uint32_t)((j * B_TAP + q * 2 * B_LBO) >> 4),
+                 idesc, (g > 0 || j > 0 || q > 0) ? 1u : 0u);
       }
-      // committed even without MMAs (then it arrives at once), so that the
-      // stage wait below never waits for MMAs that were not issued
-      tc_commit(&bars[g % kTcStages]);
-    }
-    issued = g;
-    if (g >= 1) {
-      const int next = g - 1 + kTcStages;
-      if (next < kTcGroups) {
-        // the stage of group g - 1 is free once its MMAs have completed
-        const bool ok = mbar_wait(&bars[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1), stage_polls);
-        if (__syncthreads_or(!ok || b_fail)) {
-          if (t == 0) atomicExch(err, 1);
+      tc_commit(&empty[g % kTcStages]);
+      issued = g;
+      // group g + 1's B tiles go to the stage of group g - 1 once its MMAs
+      // (queued ahead of group g's) have completed
+      if (g >= 1 && g + 1 < kTcGroups) {
+        if (!mbar_wait_or_stop(&empty[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1), kTcWaitLimit,
+                               &stop)) {
+          fail();
           break;
         }
-        fill(next);
+        fill_b(g + 1);
       }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-  }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  if (t == 0) {
     // B copies still in flight (after an early exit) land before the CTA ends
     for (int gg = b_waited + 1; gg <= b_issued; ++gg)
       (void)mbar_wait(&bbars[gg % kTcStages], (uint32_t)((gg / kTcStages) & 1), kTcWaitLimit);
-  }
-  // all MMAs issued so far have completed once the last commit's phase does
-  if (t == 0 && issued >= 0) {
-    tc_commit(&bars[kTcStages]);
-    const bool ok = mbar_wait(&bars[kTcStages], 0u, kTcWaitLimit);
-    if (!ok) atomicExch(err, 1);
-    stop = stop || !ok || issued < kTcGroups - 1;
+    // all MMAs issued so far have completed once the last commit's phase does
+    if (issued >= 0) {
+      tc_commit(&done_bar);
+      if (!mbar_wait(&done_bar, 0u, kTcWaitLimit)) fail();
+    }
+    last_issued = issued;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!stop && issued == kTcGroups - 1) {
+  const int issued = last_issued;
+  if (producer && !stop && issued == kTcGroups - 1) {
     float acc[32];
     uint32_t r[32];
     const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16);
@@ -807,7 +840,7 @@ cudaError_t conv_tc_launch(const void* act, const void* Wk, const float* bias, c
   // 128 rows per CTA over the (z, t) planes padded by a halo in x and y
   const int64_t rows = (int64_t)(geo.L[0] + 2) * (geo.L[1] + 2) * geo.L[2] * geo.L[3];
   const unsigned nb = (unsigned)((rows + 127) / 128);
-  k_conv_tc<K, N, SIGN, FWD><<<nb, 128, smem, s>>>(static_cast<const bf16*>(act), static_cast<const bf16*>(Wk), bias,
+  k_conv_tc<K, N, SIGN, FWD><<<nb, kTcThreads, smem, s>>>(static_cast<const bf16*>(act), static_cast<const bf16*>(Wk), bias,
                                                     static_cast<const bf16*>(mask), static_cast<bf16*>(y), yf, geo,
                                                     relu, err);
   return cudaPeekAtLastError();
