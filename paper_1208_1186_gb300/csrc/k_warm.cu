@@ -525,15 +525,15 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16* __restrict__
       }
       tc_commit(&empty[g % kTcStages]);
       issued = g;
-      // group g + 1's B tiles go to the stage of group g - 1 once its MMAs
-      // (queued ahead of group g's) have completed
-      if (g >= 1 && g + 1 < kTcGroups) {
+      // the stage of group g - 1 takes group g - 1 + S's B tiles once its
+      // MMAs (queued ahead of group g's) have completed
+      if (g >= 1 && g - 1 + kTcStages < kTcGroups) {
         if (!mbar_wait_or_stop(&empty[(g - 1) % kTcStages], (uint32_t)(((g - 1) / kTcStages) & 1), kTcWaitLimit,
                                &stop)) {
           fail();
           break;
         }
-        fill_b(g + 1);
+        fill_b(g - 1 + kTcStages);
       }
     }
     // B copies still in flight (after an early exit) land before the CTA ends
