@@ -173,6 +173,29 @@ int lgf_iterate(lgf_handle h, int n);
  * iterations instead.  Both stop at the same update. */
 int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out);
 
+/* Fix an ensemble of n configurations in turn, streaming them through the
+ * device (paper Sec. 3.2: the string tension is measured on ensembles of
+ * configurations, each brought to Landau gauge on its own; Sec. 2.2: the
+ * host holds the lattice and the GPU fixes it).  host_in[k] (V*4*18 doubles,
+ * the layout above) is fixed as lgf_load_links + lgf_fix(theta_tol, max_iter)
+ * + lgf_store_links into host_out[k] would do, with bit-identical results.
+ * Configuration k runs on h0 for even k and h1 for odd k; the two handles
+ * must have the same lattice, dtype and device, and each should have its own
+ * stream (lgf_set_stream).  The copies go through each handle's device
+ * staging buffers on two streams of their own: while configuration k is
+ * being fixed, configuration k + 1 is copied in and k - 1 copied out, so the
+ * host link's transfers overlap the fixing.  host_in and host_out should be
+ * pinned (page-locked) for the copies to run asynchronously; the caller must
+ * leave every host_in[k] unchanged and read no host_out[k] until the call
+ * returns.  iters_out (may be NULL) receives n update counts.  Allocates two
+ * FP64 link buffers per handle on first use (kept until lgf_destroy).
+ * Returns LGF_OK, LGF_ERR_NOT_CONVERGED (every configuration is still fixed
+ * as far as max_iter allows and stored) or an error, whose message
+ * lgf_last_error(h0) gives; after an error the state of both handles and of
+ * the outputs not yet written is unspecified. */
+int lgf_fix_stream(lgf_handle h0, lgf_handle h1, int n, const double* const* host_in, double* const* host_out,
+                   double theta_tol, int max_iter, int* iters_out);
+
 /* F and theta of the current links (either pointer may be NULL): the gauge
  * functional the steepest descent of paper Sec. 1 maximises and its
  * convergence measure, normalised as at the top of this file, summed in a

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import LgfError
 
-__all__ = ["GaugeFixer", "GaugeBatch", "WarmStartNet", "LgfError"]
+__all__ = ["GaugeFixer", "GaugeBatch", "WarmStartNet", "LgfError", "fix_stream"]
 
 def _as_ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
@@ -169,6 +169,31 @@ class GaugeFixer:
             engine = 1 if self.dtype.startswith("f32") else 0
         _lib.check(self.lib.lgf_set_schedule(self.h, int(engine), int(pipeline), int(zt_bx), int(zt_ro)),
                    "lgf_set_schedule", self.h)
+
+
+def fix_stream(fixers, inputs, outputs, theta_tol: float, max_iter: int):
+    """Fix configurations inputs[k] into outputs[k] through two GaugeFixer
+    handles of one lattice and dtype (``lgf_fix_stream``): while one handle
+    fixes a configuration, the next is copied in and the previous copied out.
+    inputs/outputs: complex128 host arrays of the link layout, ideally in
+    pinned memory (e.g. views of ``torch.empty(..., pin_memory=True)``).
+    Returns (per-configuration update counts, all converged)."""
+    f0, f1 = fixers
+    n = len(inputs)
+    if len(outputs) != n:
+        raise ValueError("inputs and outputs differ in length")
+    for a in list(inputs) + list(outputs):
+        if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous \
+                or a.size != f0.V * 36:
+            raise ValueError(f"expected C-contiguous complex128 arrays of {f0.V * 36} entries")
+    ins = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in inputs])
+    outs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in outputs])
+    its = (ctypes.c_int * max(n, 1))()
+    st = f0.lib.lgf_fix_stream(f0.h, f1.h, n, ins, outs, float(theta_tol), int(max_iter), its)
+    if st == _lib.LGF_ERR_NOT_CONVERGED:
+        return list(its)[:n], False
+    _lib.check(st, "lgf_fix_stream", f0.h)
+    return list(its)[:n], True
 
 
 class GaugeBatch:

@@ -44,6 +44,7 @@ SIGNATURES = {
     "lgf_store_links": (ctypes.c_int, [_P, _P]),
     "lgf_iterate": (ctypes.c_int, [_P, ctypes.c_int]),
     "lgf_fix": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _IP]),
+    "lgf_fix_stream": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_int, _IP]),
     "lgf_functional": (ctypes.c_int, [_P, _DP, _DP]),
     "lgf_probe": (ctypes.c_int, [_P, _P, _P, _P]),
     "lgf_history": (ctypes.c_int, [_P, _P, ctypes.c_int, _IP]),

@@ -120,6 +120,7 @@ struct lgf_ctx {
   int hist_n = 0;
   double* staging = nullptr;  // device FP64 AoS link buffer (V*72 doubles), lazily
   size_t staging_bytes = 0;
+  double* staging_out = nullptr;  // second such buffer, for the results of lgf_fix_stream
   bool loaded = false;
   long long launches = 0;
   long long total_updates = 0;
@@ -1358,7 +1359,9 @@ int lgf_set_param(lgf_handle h, int key, double value) {
   }
 }
 
-static int load_from_device_aos(lgf_handle h, const double* aos) {
+// Queue the re-layout of device AoS links into the handle's storage on its
+// stream (no host synchronisation); the handle counts as loaded from here on.
+static int queue_load(lgf_handle h, const double* aos) {
   const int64_t V = h->V;
   // the FP32 engine's update mode is fixed at the load; loop bodies captured
   // for the other mode are dropped
@@ -1381,9 +1384,15 @@ static int load_from_device_aos(lgf_handle h, const double* aos) {
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
   }
-  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
   h->loaded = true;
   h->total_updates = 0;
+  return LGF_OK;
+}
+
+static int load_from_device_aos(lgf_handle h, const double* aos) {
+  int rc = queue_load(h, aos);
+  if (rc) return rc;
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
   return LGF_OK;
 }
 
@@ -1416,6 +1425,19 @@ int lgf_load_links_device(lgf_handle h, const double* dev_aos) {
   return load_from_device_aos(h, dev_aos);
 }
 
+// Queue the current links, as FP64 AoS, into dst (device memory, or host
+// memory the device writes directly) on the handle's stream.
+static int queue_store(lgf_handle h, double* dst) {
+  Engine& e = *h->cur;
+  if (&e == &h->e64 && h->df)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos_df(h->Udf, h->eta, h->geo, dst, h->stream));
+  else if (e.grep)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, dst, h->geo, h->stream));
+  else
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos(e.prec, e.nc, e.U, dst, h->V, h->stream));
+  return LGF_OK;
+}
+
 int lgf_store_links(lgf_handle h, double* host_aos) {
   if (!h || !host_aos) return LGF_ERR_ARG;
   if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
@@ -1424,14 +1446,8 @@ int lgf_store_links(lgf_handle h, double* host_aos) {
     int rc = ensure_staging(h);
     if (rc) return rc;
   }
-  double* dst = direct ? direct : h->staging;
-  Engine& e = *h->cur;
-  if (&e == &h->e64 && h->df)
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos_df(h->Udf, h->eta, h->geo, dst, h->stream));
-  else if (e.grep)
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_materialize(e.nc, e.U, h->G, dst, h->geo, h->stream));
-  else
-    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_aos(e.prec, e.nc, e.U, dst, h->V, h->stream));
+  int rc = queue_store(h, direct ? direct : h->staging);
+  if (rc) return rc;
   if (!direct)
     LGF_CUDA(h, cudaMemcpyAsync(host_aos, h->staging, (size_t)h->V * 72 * sizeof(double), cudaMemcpyDeviceToHost,
                                 h->stream));
@@ -1489,6 +1505,128 @@ int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out) {
     h->last_n32 += n2;
   if (iters_out) *iters_out = n1 + n2;
   return conv ? LGF_OK : fail(h, LGF_ERR_NOT_CONVERGED, "max_iter reached with theta >= tol");
+}
+
+// ---------------------------------------------------------------------------
+// streamed fixing of an ensemble (lgf_fix_stream)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Streams and events of one lgf_fix_stream call, released on every return
+// path after all the work queued on them has finished.
+struct StreamCtx {
+  cudaStream_t cin = nullptr, cout = nullptr;  // host -> device and device -> host copies
+  cudaEvent_t in_done[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+  lgf_handle H[2] = {nullptr, nullptr};
+  ~StreamCtx() {
+    if (cin) cudaStreamSynchronize(cin);
+    if (cout) cudaStreamSynchronize(cout);
+    for (lgf_handle h : H)
+      if (h) cudaStreamSynchronize(h->stream);
+    for (int s = 0; s < 2; ++s)
+      for (cudaEvent_t ev : {in_done[s], in_free[s], out_ready[s], out_free[s]})
+        if (ev) cudaEventDestroy(ev);
+    if (cin) cudaStreamDestroy(cin);
+    if (cout) cudaStreamDestroy(cout);
+  }
+  bool create() {
+    if (cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (int s = 0; s < 2; ++s)
+      for (cudaEvent_t* ev : {&in_done[s], &in_free[s], &out_ready[s], &out_free[s]})
+        if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+  }
+};
+
+int ensure_staging_out(lgf_handle h) {
+  if (h->staging_out) return LGF_OK;
+  h->staging_out = static_cast<double*>(dev_alloc(h, (size_t)h->V * 72 * sizeof(double)));
+  if (!h->staging_out) return fail(h, LGF_ERR_OOM, "device allocation of the result staging buffer failed");
+  return LGF_OK;
+}
+
+}  // namespace
+
+int lgf_fix_stream(lgf_handle h0, lgf_handle h1, int n, const double* const* host_in, double* const* host_out,
+                   double theta_tol, int max_iter, int* iters_out) {
+  if (!h0) return LGF_ERR_ARG;
+  if (!h1 || h1 == h0) return fail(h0, LGF_ERR_ARG, "lgf_fix_stream: needs two distinct handles");
+  if (n < 0 || max_iter < 0 || !(theta_tol > 0.0)) return fail(h0, LGF_ERR_ARG, "lgf_fix_stream: bad n, tol or max_iter");
+  if (n > 0 && (!host_in || !host_out)) return fail(h0, LGF_ERR_ARG, "lgf_fix_stream: null configuration array");
+  for (int a = 0; a < 4; ++a)
+    if (h0->L[a] != h1->L[a]) return fail(h0, LGF_ERR_ARG, "lgf_fix_stream: the handles' lattices differ");
+  if (h0->dtype != h1->dtype || h0->device != h1->device)
+    return fail(h0, LGF_ERR_ARG, "lgf_fix_stream: the handles' dtype or device differ");
+  for (int k = 0; k < n; ++k)
+    if (!host_in[k] || !host_out[k]) return fail(h0, LGF_ERR_ARG, "lgf_fix_stream: null configuration pointer");
+  if (n == 0) return LGF_OK;
+  const size_t bytes = (size_t)h0->V * 72 * sizeof(double);
+  StreamCtx c;
+  c.H[0] = h0;
+  c.H[1] = h1;
+  for (lgf_handle h : c.H) {
+    int rc = ensure_staging(h);
+    if (!rc) rc = ensure_staging_out(h);
+    if (rc) return fail(h0, rc, h->err);
+  }
+  if (!c.create()) return fail(h0, LGF_ERR_CUDA, "lgf_fix_stream: stream or event creation failed");
+  // Configuration k goes to handle k % 2.  Its input lands in that handle's
+  // staging buffer once the re-layout of configuration k - 2 has read it, and
+  // its re-layout is queued on that handle's stream before configuration
+  // k - 1 starts fixing on the other handle, so that it runs alongside that
+  // fix (after the store of configuration k - 2 in stream order).
+  auto queue_in = [&](int k) -> int {
+    const int s = k & 1;
+    lgf_handle h = c.H[s];
+    if (k >= 2) LGF_CUDA(h0, cudaStreamWaitEvent(c.cin, c.in_free[s], 0));
+    LGF_CUDA(h0, cudaMemcpyAsync(h->staging, host_in[k], bytes, cudaMemcpyHostToDevice, c.cin));
+    LGF_CUDA(h0, cudaEventRecord(c.in_done[s], c.cin));
+    return LGF_OK;
+  };
+  lgf_handle where = h0;  // the handle whose call failed (its message is reported through h0)
+  auto load_next = [&](int k) -> int {
+    const int s = k & 1;
+    lgf_handle h = c.H[s];
+    LGF_CUDA(h0, cudaStreamWaitEvent(h->stream, c.in_done[s], 0));
+    where = h;
+    int r = queue_load(h, h->staging);
+    if (r) return r;
+    where = h0;
+    LGF_CUDA(h0, cudaEventRecord(c.in_free[s], h->stream));
+    return k + 2 < n ? queue_in(k + 2) : LGF_OK;
+  };
+  int rc = queue_in(0);
+  if (!rc && n > 1) rc = queue_in(1);
+  if (!rc) rc = load_next(0);
+  if (rc) return where == h0 ? rc : fail(h0, rc, "lgf_fix_stream: " + where->err);
+  bool all_converged = true;
+  for (int k = 0; k < n && !rc; ++k) {
+    const int s = k & 1;
+    lgf_handle h = c.H[s];
+    if (k + 1 < n && (rc = load_next(k + 1)) != LGF_OK) break;
+    where = h;
+    int it = 0;
+    rc = lgf_fix(h, theta_tol, max_iter, &it);
+    if (iters_out) iters_out[k] = it;
+    if (rc == LGF_ERR_NOT_CONVERGED) {
+      all_converged = false;
+      rc = LGF_OK;
+    }
+    if (rc) break;
+    // the result buffer of this handle is free once configuration k - 2 is out
+    if (k >= 2) LGF_CUDA(h0, cudaStreamWaitEvent(h->stream, c.out_free[s], 0));
+    if ((rc = queue_store(h, h->staging_out)) != LGF_OK) break;
+    where = h0;
+    LGF_CUDA(h0, cudaEventRecord(c.out_ready[s], h->stream));
+    LGF_CUDA(h0, cudaStreamWaitEvent(c.cout, c.out_ready[s], 0));
+    LGF_CUDA(h0, cudaMemcpyAsync(host_out[k], h->staging_out, bytes, cudaMemcpyDeviceToHost, c.cout));
+    LGF_CUDA(h0, cudaEventRecord(c.out_free[s], c.cout));
+  }
+  if (rc) return where == h0 ? rc : fail(h0, rc, "lgf_fix_stream: " + where->err);
+  LGF_CUDA(h0, cudaStreamSynchronize(c.cout));
+  LGF_CUDA(h0, cudaStreamSynchronize(c.cin));
+  return all_converged ? LGF_OK : fail(h0, LGF_ERR_NOT_CONVERGED, "lgf_fix_stream: max_iter reached with theta >= tol");
 }
 
 int lgf_functional(lgf_handle h, double* F, double* theta) {
