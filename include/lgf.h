@@ -94,6 +94,27 @@ enum lgf_param {
                             as FP64, hi + lo); 2 the same tail on FP64 links;
                             1 always uses the plain FP64 iteration.  Values
                             other than 0, 1, 2 give LGF_ERR_ARG.              */
+  LGF_TRACK_G = 9,       /* FP64 handles, from the next load: 1 accumulates the
+                            gauge transformation G(x) <- reunitarised g(x) G(x)
+                            with every update, so that lgf_store_gauge can
+                            return it (one more SU(3) field in FP64 and one
+                            more kernel per iteration); 0 (default) does not.
+                            Mixed-precision handles always keep it (their FP32
+                            phase works on G); the parameter has no effect
+                            there.                                              */
+  LGF_EXP_ORDER = 8,     /* g from the accelerated gradient (paper Sec. 1, the
+                            cited steepest descent: g = exp(alpha/2 Delta~)):
+                            1 (default) reunitarised 1 + alpha/2 Delta~, the
+                            first-order form; 0 the reunitarised exact
+                            exponential, by a Taylor series with scaling and
+                            squaring (degree 16 in FP64, 9 in FP32 arithmetic).
+                            Both fix the same gauge.  With 0 the FP32 gauge
+                            step runs unfused from the inverse transform; the
+                            FP64 defect tail always uses 1 + eps, eps the
+                            exponential to second order, which equals the
+                            exact one to FP64 rounding at the tail's steps
+                            (|alpha/2 Delta~| < 1e-5).  Other values give
+                            LGF_ERR_ARG.                                        */
   LGF_LINK_UPDATE = 6    /* FP32 storage, from the next load: 0 (default) keeps
                             the loaded links and applies each update to the
                             accumulated gauge transformation G, forming
@@ -148,6 +169,20 @@ int lgf_load_links_device(lgf_handle h, const double* dev_aos);
  * storage rebuilds row 3 as conj(row1 x row2) (paper Sec. 2.2).  host_aos
  * is caller-owned; the call returns once it is written. */
 int lgf_store_links(lgf_handle h, double* host_aos);
+
+/* Copy out the gauge transformation G that the iterations since the last
+ * load have applied, as V*18 host doubles ([s][i][j] complex, row-major):
+ * the current links are G(x) U_mu(x) G(x+mu)^dagger of the loaded links U
+ * (paper Sec. 1: gauge fixing searches the gauge orbit of the configuration;
+ * G is the point of the orbit it reached, which fixes other fields to the
+ * same gauge).  FP64 handles need LGF_TRACK_G set before the load; mixed
+ * handles return G from their FP32 phase, or (1 + eta) G in FP64 after the
+ * default double-float tail.  Returns LGF_ERR_ARG when the handle does not
+ * hold it: an FP64 handle without LGF_TRACK_G, a mixed handle after an
+ * FP64-link tail (LGF_TAIL_MODE 1 or 2, or a hand-over above theta = 1e-8),
+ * or after lgf_probe on the double-float tail.  host_g is caller-owned; the
+ * call returns once it is written. */
+int lgf_store_gauge(lgf_handle h, double* host_g);
 
 /* Apply exactly n iterations (no convergence test).  Mixed-precision handles
  * iterate in their FP32 storage.  One iteration is one step of the paper's

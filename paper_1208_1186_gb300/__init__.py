@@ -93,6 +93,15 @@ class GaugeFixer:
         _lib.check(self.lib.lgf_store_links(self.h, _as_ptr(out)), "lgf_store_links", self.h)
         return out
 
+    def store_gauge(self, out: np.ndarray | None = None) -> np.ndarray:
+        """The gauge transformation G applied since the last load, complex128
+        (Lt, Lz, Ly, Lx, 3, 3): links = G(x) U_loaded G(x+mu)^dagger
+        (``lgf_store_gauge``; FP64 handles need LGF_TRACK_G before the load)."""
+        if out is None:
+            out = np.empty(self.shape + (3, 3), dtype=np.complex128)
+        _lib.check(self.lib.lgf_store_gauge(self.h, _as_ptr(out)), "lgf_store_gauge", self.h)
+        return out
+
     # -- the method -----------------------------------------------------------
     def iterate(self, n: int):
         _lib.check(self.lib.lgf_iterate(self.h, int(n)), "lgf_iterate", self.h)

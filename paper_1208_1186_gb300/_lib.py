@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "LGF_OK", -1: "LGF_ERR_ARG", -2: "LGF_ERR_CUDA", -3: "LGF_ERR
 
 LGF_ALPHA, LGF_CHECK_EVERY, LGF_TAIL_THETA, LGF_TAIL_MAX_FP32 = 0, 1, 2, 3
 LGF_REUNIT_FP64, LGF_FFT_PIPELINE, LGF_LINK_UPDATE, LGF_TAIL_MODE = 4, 5, 6, 7
+LGF_EXP_ORDER, LGF_TRACK_G = 8, 9
 
 # every symbol include/lgf.h declares: name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -42,6 +43,7 @@ SIGNATURES = {
     "lgf_load_links": (ctypes.c_int, [_P, _P]),
     "lgf_load_links_device": (ctypes.c_int, [_P, _P]),
     "lgf_store_links": (ctypes.c_int, [_P, _P]),
+    "lgf_store_gauge": (ctypes.c_int, [_P, _P]),
     "lgf_iterate": (ctypes.c_int, [_P, ctypes.c_int]),
     "lgf_fix": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _IP]),
     "lgf_fix_stream": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_int, _IP]),

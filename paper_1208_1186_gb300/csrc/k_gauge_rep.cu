@@ -16,7 +16,8 @@
 //                    sum_mu U_mu(x) = G(x) C,  sum_mu U_mu(x-mu) = B G(x)^dag,
 //                    A = B G^dag - G C, then Delta, F, theta as in k_gradient
 //                    (10 SU(3) products per site instead of 16).
-//   k_gstep          g = reunitarised (1 + alpha/2 Delta~), G <- reunitarised g G.
+//   k_gstep          g = reunitarised (1 + alpha/2 Delta~) (or the reunitarised exact
+//                    exponential), G <- reunitarised g G.
 //   k_materialize    G(x) U0_mu(x) G(x+mu)^dag as host-layout FP64 links.
 #include "lgf_gstep.cuh"
 #include "lgf_kernels.cuh"
@@ -131,14 +132,15 @@ __global__ void __launch_bounds__(kGrepThreads, 2) k_gradient_grep(const cx<T>* 
 
 // g from the accelerated gradient; G <- g G unless G is null; g stored if
 // g_out is not null.  RT: arithmetic of g, the product and both projections.
-template <class T, int NC, class RT>
+template <class T, int NC, class RT, bool EXACT>
 __global__ void __launch_bounds__(256) k_gstep(const cx<T>* __restrict__ D, cx<T>* G, cx<T>* __restrict__ g_out,
                                                int64_t V, double hd, const DevState* __restrict__ st) {
   pdl_wait();
   if (st != nullptr && st->done) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  gstep_site<T, NC, RT>(ldg(D + s), ldg(D + V + s), ldg(D + 2 * V + s), ldg(D + 3 * V + s), (RT)hd, G, g_out, V, s);
+  gstep_site<T, NC, RT>(ldg(D + s), ldg(D + V + s), ldg(D + 2 * V + s), ldg(D + 3 * V + s), (RT)hd, G, g_out, V, s,
+                        EXACT);
 }
 
 // one thread per (site, mu): the current link G(x) U0 G(x+mu)^dag in the host
@@ -209,24 +211,25 @@ cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D,
   return launch_pdl(k_gradient_grep<float, 6>, nb, kGrepThreads, 0, s, u, g, d, partial, geo, st, mode, nF, nT);
 }
 
-cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,
-                         const DevState* st, cudaStream_t s) {
+template <bool EXACT>
+static cudaError_t gstep_launch(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha,
+                                bool reunit_fp64, const DevState* st, cudaStream_t s) {
   const auto Dp = static_cast<const cx<float>*>(D);
   const auto Gp = static_cast<cx<float>*>(G);
   const auto gp = static_cast<cx<float>*>(g_out);
   const unsigned nb = nblocks(V, 256);
   if (nc == 9) {
-    if (reunit_fp64)
-      return launch_pdl(k_gstep<float, 9, double>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
-    else
-      return launch_pdl(k_gstep<float, 9, float>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
-  } else {
-    if (reunit_fp64)
-      return launch_pdl(k_gstep<float, 6, double>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
-    else
-      return launch_pdl(k_gstep<float, 6, float>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
+    if (reunit_fp64) return launch_pdl(k_gstep<float, 9, double, EXACT>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
+    return launch_pdl(k_gstep<float, 9, float, EXACT>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
   }
-  return cudaPeekAtLastError();
+  if (reunit_fp64) return launch_pdl(k_gstep<float, 6, double, EXACT>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
+  return launch_pdl(k_gstep<float, 6, float, EXACT>, nb, 256, 0, s, Dp, Gp, gp, V, half_alpha, st);
+}
+
+cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,
+                         bool exact, const DevState* st, cudaStream_t s) {
+  if (exact) return gstep_launch<true>(nc, D, G, g_out, V, half_alpha, reunit_fp64, st, s);
+  return gstep_launch<false>(nc, D, G, g_out, V, half_alpha, reunit_fp64, st, s);
 }
 
 cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s) {

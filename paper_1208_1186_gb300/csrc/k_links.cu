@@ -8,7 +8,8 @@
 //               warp shuffles.
 //               The last block to finish sums the partials in fixed order ->
 //               F, theta, and the stop decision of the iteration queue.
-//   k_build_g   g(x) = reunitarised (1 + alpha/2 Delta~(x)), FP64 arithmetic.
+//   k_build_g   g(x) = reunitarised (1 + alpha/2 Delta~(x)), or the reunitarised
+//               exact exponential exp(alpha/2 Delta~(x)), FP64 arithmetic.
 //   k_update    U_mu(x) <- g(x) U_mu(x) g(x+mu)^dag.
 //
 // Links of direction mu occupy NC complex planes of V elements:
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradient(const cx<T>* __restri
   grid_reduce<T>(fsum, tsum, partial, st, normF, normT, mode);
 }
 
-template <class T, int NC, class RT>
+template <class T, int NC, class RT, bool EXACT>
 __global__ void __launch_bounds__(256) k_build_g(const cx<T>* __restrict__ D, cx<T>* __restrict__ g, int64_t V,
                                                  double hd, const DevState* __restrict__ st) {
   pdl_wait();
@@ -90,14 +91,18 @@ __global__ void __launch_bounds__(256) k_build_g(const cx<T>* __restrict__ D, cx
   const cx<RT> c1 = cvt<RT>(ldg(D + V + s));
   const cx<RT> c2 = cvt<RT>(ldg(D + 2 * V + s));
   const cx<RT> c3 = cvt<RT>(ldg(D + 3 * V + s));
-  // rows 1-2 of 1 + h Delta~; Delta~10 = -conj(Delta~01), Delta~_ii = i Im
   M3<RT> m;
-  m.e[0][0] = mk<RT>(1, h * c3.re);
-  m.e[0][1] = scale(c0, h);
-  m.e[0][2] = scale(c1, h);
-  m.e[1][0] = mk<RT>(-h * c0.re, h * c0.im);
-  m.e[1][1] = mk<RT>(1, h * c3.im);
-  m.e[1][2] = scale(c2, h);
+  if constexpr (EXACT) {  // the exact exponential of h Delta~ (expm_taylor)
+    m = expm_taylor(unpack_ah(c0, c1, c2, c3, h));
+  } else {
+    // rows 1-2 of 1 + h Delta~; Delta~10 = -conj(Delta~01), Delta~_ii = i Im
+    m.e[0][0] = mk<RT>(1, h * c3.re);
+    m.e[0][1] = scale(c0, h);
+    m.e[0][2] = scale(c1, h);
+    m.e[1][0] = mk<RT>(-h * c0.re, h * c0.im);
+    m.e[1][1] = mk<RT>(1, h * c3.im);
+    m.e[1][2] = scale(c2, h);
+  }
   reunitarize(m);
 #pragma unroll
   for (int c = 0; c < NC; ++c) g[c * V + s] = cvt<T>(m.e[c / 3][c % 3]);
@@ -369,21 +374,28 @@ cudaError_t launch_gradient(int prec, int nc, const void* U, void* D, double2* p
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
-                           bool reunit_fp64, const DevState* st, cudaStream_t s) {
+template <bool EXACT>
+static cudaError_t build_g_launch(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
+                                  bool reunit_fp64, const DevState* st, cudaStream_t s) {
   if (prec == 4 && !reunit_fp64) {
     if (nc == 9)
-      launch_pdl(k_build_g<float, 9, float>, blocks_for(V, 256), 256, 0, s, static_cast<const cx<float>*>(D),
-                                                                   static_cast<cx<float>*>(g), V, half_alpha, st);
+      launch_pdl(k_build_g<float, 9, float, EXACT>, blocks_for(V, 256), 256, 0, s, static_cast<const cx<float>*>(D),
+                 static_cast<cx<float>*>(g), V, half_alpha, st);
     else
-      launch_pdl(k_build_g<float, 6, float>, blocks_for(V, 256), 256, 0, s, static_cast<const cx<float>*>(D),
-                                                                   static_cast<cx<float>*>(g), V, half_alpha, st);
+      launch_pdl(k_build_g<float, 6, float, EXACT>, blocks_for(V, 256), 256, 0, s, static_cast<const cx<float>*>(D),
+                 static_cast<cx<float>*>(g), V, half_alpha, st);
     return cudaPeekAtLastError();
   }
   LGF_DISPATCH(prec, nc,
-               (launch_pdl(k_build_g<T, NC, double>, blocks_for(V, 256), 256, 0, s, 
-                   static_cast<const cx<T>*>(D), static_cast<cx<T>*>(g), V, half_alpha, st)));
+               (launch_pdl(k_build_g<T, NC, double, EXACT>, blocks_for(V, 256), 256, 0, s,
+                           static_cast<const cx<T>*>(D), static_cast<cx<T>*>(g), V, half_alpha, st)));
   return cudaPeekAtLastError();
+}
+
+cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
+                           bool reunit_fp64, bool exact, const DevState* st, cudaStream_t s) {
+  if (exact) return build_g_launch<true>(prec, nc, D, g, V, half_alpha, reunit_fp64, st, s);
+  return build_g_launch<false>(prec, nc, D, g, V, half_alpha, reunit_fp64, st, s);
 }
 
 cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& geo, const DevState* st,

@@ -288,6 +288,30 @@ __global__ void __launch_bounds__(256) k_promote_df(const cx<float>* __restrict_
   }
 }
 
+// The gauge transformation that a double-float tail has applied to the
+// loaded links, (1 + eta)(Gh + Gl), as FP64 [s][3][3] complex: both factors
+// formed exactly in FP64 from their FP32 parts, the product in FP64.
+__global__ void __launch_bounds__(256) k_store_gauge_df(const cx<float>* __restrict__ gh,
+                                                        const cx<float>* __restrict__ gl,
+                                                        const cx<float>* __restrict__ eh,
+                                                        const cx<float>* __restrict__ el, double* __restrict__ out,
+                                                        int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  M3<double> E, Gd, R;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const cx<float> a = ldg(gh + q * V + s), b = ldg(gl + q * V + s);
+    const cx<float> c = ldg(eh + q * V + s), d = ldg(el + q * V + s);
+    Gd.e[q / 3][q % 3] = mk<double>((double)a.re + (double)b.re, (double)a.im + (double)b.im);
+    E.e[q / 3][q % 3] = mk<double>((q % 4 == 0 ? 1.0 : 0.0) + ((double)c.re + (double)d.re), (double)c.im + (double)d.im);
+  }
+  mm<double, 3>(R, E, Gd);
+  double2* o = reinterpret_cast<double2*>(out + (size_t)s * 18);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) o[q] = make_double2(R.e[q / 3][q % 3].re, R.e[q / 3][q % 3].im);
+}
+
 // U_mu(x) = g(x) U_loaded,mu(x) g(x+mu)^dag, one thread per (site, mu), with
 // g = Gh + Gl from k_promote_df and U = Uh + Ul the exact split of the FP64
 // input.  Row a of W = g U: Gh Uh by compensated dot products of exact FP32
@@ -646,6 +670,13 @@ __global__ void __launch_bounds__(256) k_df_to_fp64(const cx<float>* __restrict_
 }
 
 }  // namespace
+
+cudaError_t launch_store_gauge_df(const void* g_df, const void* eta, int64_t V, double* out, cudaStream_t s) {
+  auto g = static_cast<const cx<float>*>(g_df);
+  auto e = static_cast<const cx<float>*>(eta);
+  k_store_gauge_df<<<(unsigned)((V + 255) / 256), 256, 0, s>>>(g, g + 9 * V, e, e + 9 * V, out, (int)V);
+  return cudaPeekAtLastError();
+}
 
 cudaError_t launch_promote_df(const void* G32, void* g_df, int64_t V, cudaStream_t s) {
   auto h = static_cast<cx<float>*>(g_df);

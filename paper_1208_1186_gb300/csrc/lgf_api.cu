@@ -97,6 +97,10 @@ struct lgf_ctx {
   bool reunit_fp64 = false;   // FP32 storage: reunitarise g in FP64 arithmetic
   int fft_pipeline = 0;       // 0 auto, 1 Stockham planes, 2 axis passes, 3 register planes
   bool explicit_fp32 = false; // FP32 engine: update the links in place instead of G (from the next load)
+  int exp_order = 1;          // g from 1 + alpha/2 Delta~ (1) or from its exact exponential (0)
+  bool track_g = false;       // FP64 handles, from the next load: accumulate G <- g G (LGF_TRACK_G)
+  bool g64_track = false;     // ... in effect since the last load (G holds e64.nc FP64 planes)
+  bool g_valid = false;       // G (with the tail's Gh, Gl and eta) describes the current links
   int tail_mode = 0;          // defect-correction tail when the FP32 phase reached 1e-8, with links in
                               // double-float (0) or FP64 (2); 1: plain FP64
   bool defect = false;        // the FP64 engine runs the defect-correction tail
@@ -425,6 +429,7 @@ int queue_tail_start(lgf_handle h) {
     LGF_CUDA(h, cudaMemsetAsync(h->eta, 0, (size_t)18 * V * sizeof(float) * 2, h->stream));
     LGF_LAUNCH(h, LGF_K_OTHER, launch_tail_base(h->Udf, h->tbase, h->geo, h->stream));
   } else {
+    h->g_valid = false;  // the FP64 tails update the links without tracking their gauge transformation
     LGF_LAUNCH(h, LGF_K_OTHER, launch_promote_gauge(4, h->e32.nc, h->G, h->e64.g, V, h->stream));
     LGF_CUDA(h, cudaMemcpyAsync(h->e64.U, h->Uorig, (size_t)4 * 9 * V * 16, cudaMemcpyDeviceToDevice, h->stream));
     LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(8, 9, h->e64.U, h->e64.g, h->geo, nullptr, h->stream));
@@ -440,6 +445,7 @@ int queue_tail_start(lgf_handle h) {
 // eta to Udf and convert here first.
 int materialize_df(lgf_handle h) {
   if (!h->df || h->cur != &h->e64) return LGF_OK;
+  h->g_valid = false;  // later iterations run on the FP64 links
   LGF_LAUNCH(h, LGF_K_OTHER, launch_tail_apply_eta(h->Udf, h->eta, h->geo, h->stream));
   LGF_LAUNCH(h, LGF_K_OTHER, launch_df_to_fp64(h->Udf, h->e64.U, h->V, h->stream));
   h->df = false;
@@ -501,7 +507,8 @@ int queue_iteration(lgf_handle h, Engine& e) {
   }
   int rc = queue_gradient(h, e, 1);
   if (rc) return rc;
-  if (e.grep && pick_pipeline(h, e) == 3 && plane_xyinv_gstep_supported(e.prec, h->L[0])) {
+  const bool exact = h->exp_order == 0;
+  if (e.grep && !exact && pick_pipeline(h, e) == 3 && plane_xyinv_gstep_supported(e.prec, h->L[0])) {
     // forward x-y, z-t, then the inverse x-y fused with G <- g G
     const int* L = h->L;
     LGF_LAUNCH(h, LGF_K_FFT_XY, launch_plane_xy(e.prec, L[0], e.D, h->V, L[2], L[3], 0, h->st, s));
@@ -516,13 +523,13 @@ int queue_iteration(lgf_handle h, Engine& e) {
   if (rc) return rc;
   if (e.grep) {
     LGF_LAUNCH(h, LGF_K_BUILD_G,
-               launch_gstep(e.nc, e.D, h->G, nullptr, h->V, 0.5 * h->alpha, h->reunit_fp64, h->st, s));
+               launch_gstep(e.nc, e.D, h->G, nullptr, h->V, 0.5 * h->alpha, h->reunit_fp64, exact, h->st, s));
     return LGF_OK;
   }
   LGF_LAUNCH(h, LGF_K_BUILD_G,
-             launch_build_g(e.prec, e.nc, e.D, e.g, h->V, 0.5 * h->alpha, h->reunit_fp64, h->st, s));
+             launch_build_g(e.prec, e.nc, e.D, e.g, h->V, 0.5 * h->alpha, h->reunit_fp64, exact, h->st, s));
   LGF_LAUNCH(h, LGF_K_UPDATE, launch_update(e.prec, e.nc, e.U, e.g, h->geo, h->st, s));
-  if (h->mixed && &e == &h->e32)
+  if ((h->mixed && &e == &h->e32) || (!h->mixed && h->g64_track))
     LGF_LAUNCH(h, LGF_K_ACCUMULATE, launch_accumulate(e.prec, e.nc, h->G, e.g, h->V, h->st, s));
   return LGF_OK;
 }
@@ -1350,6 +1357,13 @@ int lgf_set_param(lgf_handle h, int key, double value) {
     case LGF_LINK_UPDATE:
       h->explicit_fp32 = value != 0.0;
       return LGF_OK;
+    case LGF_TRACK_G:
+      h->track_g = value != 0.0;
+      return LGF_OK;
+    case LGF_EXP_ORDER:
+      if (!(value == 0.0 || value == 1.0)) return fail(h, LGF_ERR_ARG, "exp order must be 0 or 1");
+      h->exp_order = (int)value;
+      return LGF_OK;
     case LGF_TAIL_MODE:
       if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(h, LGF_ERR_ARG, "tail mode must be 0, 1 or 2");
       h->tail_mode = (int)value;
@@ -1384,6 +1398,18 @@ static int queue_load(lgf_handle h, const double* aos) {
   } else {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_aos_to_soa(8, h->e64.nc, aos, h->e64.U, V, 4, h->stream));
   }
+  if (!h->mixed) {
+    // LGF_TRACK_G takes effect here; a change of it drops the captured loops
+    if (h->g64_track != h->track_g) drop_loops(h);
+    h->g64_track = false;
+    if (h->track_g) {
+      if (!h->G) h->G = dev_alloc(h, (size_t)h->e64.nc * V * 16);
+      if (!h->G) return fail(h, LGF_ERR_OOM, "device allocation of the tracked gauge transformation failed");
+      LGF_LAUNCH(h, LGF_K_OTHER, launch_set_identity(8, h->e64.nc, h->G, V, h->stream));
+      h->g64_track = true;
+    }
+  }
+  h->g_valid = h->mixed || h->g64_track;
   h->loaded = true;
   h->total_updates = 0;
   return LGF_OK;
@@ -1450,6 +1476,32 @@ int lgf_store_links(lgf_handle h, double* host_aos) {
   if (rc) return rc;
   if (!direct)
     LGF_CUDA(h, cudaMemcpyAsync(host_aos, h->staging, (size_t)h->V * 72 * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+  LGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+int lgf_store_gauge(lgf_handle h, double* host_g) {
+  if (!h || !host_g) return LGF_ERR_ARG;
+  if (!h->loaded) return fail(h, LGF_ERR_ARG, "no links loaded");
+  if (!h->g_valid)
+    return fail(h, LGF_ERR_ARG,
+                "the gauge transformation is not tracked (FP64 handles: set LGF_TRACK_G before the load; mixed "
+                "handles lose it in the FP64-link tails and after lgf_probe on the double-float tail)");
+  double* direct = host_direct(host_g);
+  if (!direct) {
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+  }
+  double* dst = direct ? direct : h->staging;
+  if (h->mixed && h->cur == &h->e64 && h->df)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_store_gauge_df(h->e64.g, h->eta, h->V, dst, h->stream));
+  else if (h->mixed)
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(4, h->e32.nc, h->G, dst, h->V, 1, h->stream));
+  else
+    LGF_LAUNCH(h, LGF_K_OTHER, launch_soa_to_aos(8, h->e64.nc, h->G, dst, h->V, 1, h->stream));
+  if (!direct)
+    LGF_CUDA(h, cudaMemcpyAsync(host_g, h->staging, (size_t)h->V * 18 * sizeof(double), cudaMemcpyDeviceToHost,
                                 h->stream));
   LGF_CUDA(h, cudaStreamSynchronize(h->stream));
   return LGF_OK;
@@ -1662,10 +1714,12 @@ int lgf_probe(lgf_handle h, double* delta_packed, double* delta_tilde_packed, do
   rc = queue_accelerate(h, e, nullptr);
   if (rc) return rc;
   if (e.grep)  // g only: G is left alone
-    LGF_LAUNCH(h, LGF_K_BUILD_G, launch_gstep(e.nc, e.D, nullptr, e.g, V, 0.5 * h->alpha, h->reunit_fp64, nullptr, s));
+    LGF_LAUNCH(h, LGF_K_BUILD_G, launch_gstep(e.nc, e.D, nullptr, e.g, V, 0.5 * h->alpha, h->reunit_fp64,
+                                              h->exp_order == 0, nullptr, s));
   else
     LGF_LAUNCH(h, LGF_K_BUILD_G,
-               launch_build_g(e.prec, e.nc, e.D, e.g, V, 0.5 * h->alpha, h->reunit_fp64, nullptr, s));
+               launch_build_g(e.prec, e.nc, e.D, e.g, V, 0.5 * h->alpha, h->reunit_fp64, h->exp_order == 0, nullptr,
+                              s));
   if (delta_tilde_packed) {
     LGF_LAUNCH(h, LGF_K_OTHER, launch_unpack_fields(e.prec, e.D, h->staging, V, s));
     LGF_CUDA(h, cudaMemcpyAsync(delta_tilde_packed, h->staging, (size_t)V * 8 * sizeof(double),

@@ -235,6 +235,76 @@ __device__ __forceinline__ void reunitarize(M3<T>& m) {
   complete_row3(m);
 }
 
+// exp(X) of a 3x3 complex matrix of moderate norm (here traceless
+// anti-Hermitian, |X| < ~2) by scaling and squaring with a Taylor polynomial
+// (Moler and Van Loan, "Nineteen dubious ways to compute the exponential of a
+// matrix", 2003, the Taylor method with scaling and squaring): Y = X / 2^q
+// with squared Frobenius norm <= 1/4, exp(Y) by Horner's rule on its Taylor
+// series to degree 16 (FP64; remainder below 0.5^17 / 17! ~ 2e-20) or 9
+// (FP32; ~6e-9), then q squarings.  At most 30 halvings, so a non-finite
+// input ends in a non-finite result instead of a long loop.
+template <class T>
+__device__ __forceinline__ M3<T> expm_taylor(const M3<T>& X) {
+  T n2 = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n2 += norm2(X.e[i][j]);
+  int q = 0;
+  T sc = 1;
+  while (n2 > (T)0.25 && q < 30) {
+    n2 *= (T)0.25;
+    sc *= (T)0.5;
+    ++q;
+  }
+  M3<T> Y, E;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Y.e[i][j] = scale(X.e[i][j], sc);
+      E.e[i][j] = mk<T>(i == j ? (T)1 : (T)0, 0);
+    }
+  constexpr int kDeg = sizeof(T) == 8 ? 16 : 9;
+#pragma unroll 1
+  for (int k = kDeg; k >= 1; --k) {  // E <- 1 + Y E / k
+    M3<T> t;
+    mm<T, 3>(t, Y, E);
+    const T inv = (T)1 / (T)k;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        E.e[i][j] = scale(t.e[i][j], inv);
+        if (i == j) E.e[i][j].re += (T)1;
+      }
+  }
+#pragma unroll 1
+  for (int r = 0; r < q; ++r) {
+    M3<T> t;
+    mm<T, 3>(t, E, E);
+    E = t;
+  }
+  return E;
+}
+
+// The whole traceless anti-Hermitian h Delta~ from its packed form c0..c3
+// (Delta~_01, Delta~_02, Delta~_12, Im Delta~_00 + i Im Delta~_11).
+template <class T>
+__device__ __forceinline__ M3<T> unpack_ah(cx<T> c0, cx<T> c1, cx<T> c2, cx<T> c3, T h) {
+  M3<T> X;
+  X.e[0][0] = mk<T>(0, h * c3.re);
+  X.e[1][1] = mk<T>(0, h * c3.im);
+  X.e[2][2] = mk<T>(0, -h * (c3.re + c3.im));
+  X.e[0][1] = scale(c0, h);
+  X.e[0][2] = scale(c1, h);
+  X.e[1][2] = scale(c2, h);
+  X.e[1][0] = mk<T>(-h * c0.re, h * c0.im);
+  X.e[2][0] = mk<T>(-h * c1.re, h * c1.im);
+  X.e[2][1] = mk<T>(-h * c2.re, h * c2.im);
+  return X;
+}
+
 // ---------------------------------------------------------------------------
 // lattice geometry, passed by value to every kernel
 // ---------------------------------------------------------------------------

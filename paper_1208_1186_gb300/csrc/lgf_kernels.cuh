@@ -70,8 +70,9 @@ cudaError_t launch_fft_xy(int prec, void* D, const FftGeom& fg, const void* tw, 
                           const DevState* st, cudaStream_t s);
 cudaError_t launch_fft_zt(int prec, void* D, const FftGeom& fg, const void* tw,
                           const double* sin2, const DevState* st, cudaStream_t s);
+// exact: g from the exact exponential of alpha/2 Delta~ instead of 1 + alpha/2 Delta~
 cudaError_t launch_build_g(int prec, int nc, const void* D, void* g, int64_t V, double half_alpha,
-                           bool reunit_fp64, const DevState* st, cudaStream_t s);
+                           bool reunit_fp64, bool exact, const DevState* st, cudaStream_t s);
 cudaError_t launch_update(int prec, int nc, void* U, const void* g, const Geom& geo,
                           const DevState* st, cudaStream_t s);
 // host [s][mu][3][3] complex128 layout (on the device) <-> SoA storage
@@ -145,12 +146,15 @@ cudaError_t launch_plane_xyinv_gstep(int L, int nc, const void* D, void* G, int6
 cudaError_t launch_gradient_grep(int nc, const void* U0, const void* G, void* D, double2* partial, const Geom& geo,
                                  DevState* st, int mode, cudaStream_t s);
 cudaError_t launch_gstep(int nc, const void* D, void* G, void* g_out, int64_t V, double half_alpha, bool reunit_fp64,
-                         const DevState* st, cudaStream_t s);
+                         bool exact, const DevState* st, cudaStream_t s);
 cudaError_t launch_materialize(int nc, const void* U0, const void* G, double* aos, const Geom& geo, cudaStream_t s);
 
 // FP64 tail by defect correction with double-float links (k_tail.cu): Udf
 // holds 36 V complex hi parts followed by 36 V complex lo parts
 // G (FP32, rows 0-1 used) -> Gh, Gl (2 x 9 FP32 complex planes), reunitarised in double-float
+// (1 + eta)(Gh + Gl) of a double-float tail as FP64 [s][3][3] complex (device
+// memory, or host memory the device writes directly)
+cudaError_t launch_store_gauge_df(const void* g_df, const void* eta, int64_t V, double* out, cudaStream_t s);
 cudaError_t launch_promote_df(const void* G32, void* g_df, int64_t V, cudaStream_t s);
 // Udf = Gh+Gl U_loaded (Gh+Gl)(x+mu)^dag in double-float (hi planes, then lo planes)
 cudaError_t launch_tail_start_df(const void* Uin64, const void* g_df, void* Udf, const Geom& geo, cudaStream_t s);

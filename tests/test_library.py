@@ -74,6 +74,7 @@ def test_every_handle_taking_entry_point_rejects_null(lib):
         "lgf_load_links": (None, buf),
         "lgf_load_links_device": (None, buf),
         "lgf_store_links": (None, buf),
+        "lgf_store_gauge": (None, buf),
         "lgf_fix_stream": (None, None, 2, None, None, 1e-12, 10, None),
         "lgf_probe": (None, None, None, None),
         "lgf_fix_split": (None, ctypes.byref(i), ctypes.byref(i)),
