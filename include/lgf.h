@@ -222,7 +222,9 @@ int lgf_fix(lgf_handle h, double theta_tol, int max_iter, int* iters_out);
  * host link's transfers overlap the fixing.  host_in and host_out should be
  * pinned (page-locked) for the copies to run asynchronously; the caller must
  * leave every host_in[k] unchanged and read no host_out[k] until the call
- * returns.  iters_out (may be NULL) receives n update counts.  Allocates two
+ * returns.  host_out[k] may be host_in[k] (fixing in place: configuration k
+ * is read before its result is written); no other output may overlap an
+ * input.  iters_out (may be NULL) receives n update counts.  Allocates two
  * FP64 link buffers per handle on first use (kept until lgf_destroy).
  * Returns LGF_OK, LGF_ERR_NOT_CONVERGED (every configuration is still fixed
  * as far as max_iter allows and stored) or an error, whose message
