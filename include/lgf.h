@@ -16,7 +16,8 @@
  *   theta     = 1/(3*V)   sum_x Tr Delta Delta^dagger           (convergence)
  *   Delta~    = FFT^-1[ p2_max / p2(k) * FFT[Delta] ], 0 at k = 0,
  *               p2(k) = sum_mu 4 sin^2(pi k_mu / L_mu)
- *   g(x)      = reunitarised (1 + alpha/2 Delta~(x))             (gauge step)
+ *   g(x)      = reunitarised (1 + alpha/2 Delta~(x))             (gauge step;
+ *               reunitarised exp(alpha/2 Delta~(x)) with LGF_EXP_ORDER = 0)
  *   U_mu(x)  <- g(x) U_mu(x) g(x + mu)^dagger                    (update)
  *
  * theta and F always describe the links *before* an update; an iteration is
